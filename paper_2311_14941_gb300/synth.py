@@ -251,11 +251,32 @@ def make_mechanism(seed: int, n_species: int, n_reactions: int, n_three_body: in
     req_set = set(required.values())
     for attempt in range(max_tries):
         rng = np.random.default_rng([seed, attempt])
-        pool = [c for c in cand_all if c not in req_set]
-        # prefer small compositions (real mechanisms are dominated by small species)
-        w = np.array([1.0 / (sum(c) ** 1.5) for c in pool])
-        pick = rng.choice(len(pool), size=n_species - len(req_set), replace=False, p=w / w.sum())
-        comps = list(dict.fromkeys(list(required.values()) + [pool[i] for i in pick]))
+        # grow composition families: every added species is a one-atom neighbour of one already present,
+        # preferring small compositions (real mechanisms are dominated by small species)
+        cand_set = set(cand_all)
+        have = list(dict.fromkeys(required.values()))
+        parent_of: Dict[Tuple[int, ...], Tuple[int, ...]] = {}
+        while len(have) < n_species:
+            base = have[int(rng.integers(len(have)))]
+            if base == required["N2"]:
+                continue
+            nbrs, wts = [], []
+            for e in range(n_el):
+                for dlt in (-1, 1):
+                    c = list(base)
+                    c[e] += dlt
+                    c = tuple(c)
+                    if c in cand_set and c not in have:
+                        nbrs.append(c)
+                        # H and O steps dominate (they are the ones a radical-pool reaction can take)
+                        wts.append((1.0 if elements[e] in ("H", "O") else 0.15) / (sum(c) ** 1.5))
+            if not nbrs:
+                continue
+            w_ = np.array(wts)
+            child = nbrs[rng.choice(len(nbrs), p=w_ / w_.sum())]
+            parent_of[child] = base
+            have.append(child)
+        comps = have
         assert len(comps) == n_species
         # shuffle species order (keeps the index order uncorrelated with roles)
         order = rng.permutation(n_species)
@@ -264,9 +285,15 @@ def make_mechanism(seed: int, n_species: int, n_reactions: int, n_three_body: in
         inert = index[required["N2"]]
         reactive = [i for i in range(n_species) if i != inert]
         sizes = np.array([sum(c) for c in comps])
+        # radical pool: the small H/O/C carriers first (H, O, OH, H2, O2, H2O, CO, CO2 when present),
+        # then the smallest remaining species
+        pool_names = [k for k in ("H", "O", "OH", "H2", "O2", "H2O", "CO", "CO2") if k in required]
         n_core = max(4, int(round(core_frac * n_species)))
-        rank = sorted(reactive, key=lambda i: (sizes[i], rng.uniform()))
-        core = set(rank[:n_core])
+        core_l = [index[required[k]] for k in pool_names][:max(n_core, 4)]
+        rank = sorted((i for i in reactive if i not in core_l and i != index[required["fuel"]]),
+                      key=lambda i: (sizes[i], rng.uniform()))
+        core_l += rank[: max(0, n_core - len(core_l))]
+        core = set(core_l)
         # formation enthalpies (J/mol) from a bond-energy model: atoms at their atomisation enthalpies
         # minus a random bond energy per bond; reference molecules O2, N2, H2 at zero, CO2/H2O/CO bound
         role_now = {k: index[v] for k, v in required.items()}
@@ -301,15 +328,44 @@ def make_mechanism(seed: int, n_species: int, n_reactions: int, n_three_body: in
                 for (b, c) in lst:
                     decomp.append((index[s], (b, c)))
 
+        # family-tree neighbours: parent/child and grandparent/grandchild links of the growth above
+        tree_nb: Dict[int, set] = {i: set() for i in range(n_species)}
+        for ch, pa in parent_of.items():
+            a, b = index[ch], index[pa]
+            tree_nb[a].add(b); tree_nb[b].add(a)
+        for ch, pa in parent_of.items():
+            if pa in parent_of:
+                a, g = index[ch], index[parent_of[pa]]
+                tree_nb[a].add(g); tree_nb[g].add(a)
+
+        def one_atom(a, b):
+            return b in tree_nb[a]
+
+        # Locality, as in real mechanisms: a species outside the radical pool reacts with pool species and
+        # turns into a neighbour that differs from it by one or two atoms (H-abstraction, O-addition, ...).
         def wt_exch(rx):
             (a, b), (c, d) = rx
-            lhs = (a in core) or (b in core)
-            rhs = (c in core) or (d in core)
-            return 1.0 if (lhs and rhs) else (0.3 if (lhs or rhs) else 0.05)
+            outside = [x for x in (a, b, c, d) if x not in core]
+            if not outside:
+                return 1.0
+            if len(outside) == 2:
+                x, y = outside
+                if ((x in (a, b)) != (y in (a, b))) and one_atom(x, y):
+                    return 1.0
+            return 1e-3
 
         def wt_dec(rx):
             a, (b, c) = rx
-            return 1.0 if (b in core or c in core) else 0.2
+            outside = [x for x in (a, b, c) if x not in core]
+            if not outside:
+                return 1.0
+            if len(outside) == 2 and a in outside:
+                other = b if b in outside else c
+                if one_atom(a, other):
+                    return 1.0
+            if outside == [a]:
+                return 0.5
+            return 1e-3
 
         if not exch or not decomp:
             continue
@@ -359,7 +415,8 @@ def make_mechanism(seed: int, n_species: int, n_reactions: int, n_three_body: in
                 chosen["elem"].append(it)
                 covered |= parts(it)
             elif d_opts and (room_tb or room_troe):
-                rx = d_opts[rng.integers(len(d_opts))]
+                w_ = np.array([wt_dec(rx) for rx in d_opts])
+                rx = d_opts[rng.choice(len(d_opts), p=w_ / w_.sum())]
                 exo = dhf[rx[0]] - dhf[rx[1][0]] - dhf[rx[1][1]] < 0.0
                 if room_troe and exo and (not room_tb or rng.uniform() < 0.5):
                     chosen["troe"].append(rx)
@@ -382,13 +439,18 @@ def make_mechanism(seed: int, n_species: int, n_reactions: int, n_three_body: in
                 continue
             rest = [it for it in pool_ if it not in chosen[key]]
             w_ = np.array([wfun(it) for it in rest]) if rest else np.zeros(0)
+            # distinct stoichiometries: only the local ones (weight >= 0.5) here
+            rest = [it for it in rest if wfun(it) >= 0.5] or rest
+            w_ = np.array([wfun(it) for it in rest]) if rest else np.zeros(0)
             take = min(need, len(rest))
             if take:
                 sel = rng.choice(len(rest), size=take, replace=False, p=w_ / w_.sum())
                 chosen[key] += [rest[i] for i in sel]
             need -= take
             if need > 0:
+                # further channels of the local pairs before any non-local stoichiometry
                 w_ = np.array([wfun(it) for it in pool_])
+                w_ = np.where(w_ >= 0.5, w_, w_ * 1e-3)
                 sel = rng.choice(len(pool_), size=need, replace=True, p=w_ / w_.sum())
                 chosen[key] += [pool_[i] for i in sel]
         break
@@ -515,7 +577,7 @@ def mechanism_methane_sized(seed: int = 53325, a_units: str = "cgs") -> MechDesc
 def mechanism_large(seed: int = 1501000, a_units: str = "cgs") -> MechDesc:
     """150 species (C, H, O, N), 1000 reversible reactions: 100 third-body, 60 Troe fall-off."""
     return make_mechanism(seed, 150, 1000, 100, 60, ["C", "H", "O", "N"], {"C": 4, "H": 10, "O": 4, "N": 2}, 10,
-                          fuel={"C": 1, "H": 4}, core_frac=0.06, name="large-150sp-1000rxn",
+                          fuel={"C": 1, "H": 4}, core_frac=0.04, name="large-150sp-1000rxn",
                           a_units=a_units)
 
 

@@ -1,0 +1,178 @@
+/*
+ * chem.h -- C ABI of the GB300 stiff-chemistry library.
+ *
+ * The method (Yang et al., "Development of a Chemistry Dynamic Load Balancing Solver with Sparse
+ * Analytical Jacobian Approach ...", Sec. 1 and Sec. 2.5): every CFD cell is an independent homogeneous
+ * gas-phase reactor whose species equations are advanced over the cell's flow time step by a stiff ODE
+ * solver driven by a sparse analytical Jacobian (SpeedCHEM-style), with the chemistry load balanced
+ * across workers (DLB) and per-cell time steps (LTS).  The paper names these techniques without
+ * formulas; this library implements them as:
+ *   - a constant-pressure adiabatic reactor, state y = (T, Y_1..Y_n);
+ *   - NASA-7 thermo, modified Arrhenius, third-body and Troe fall-off rates, reverse rates from Kc;
+ *   - an exact Jacobian J = S + u v^T whose sparse part S has a pattern fixed per mechanism (the rank-one
+ *     term is the constant-pressure density coupling, v_i = Wbar / W_i);
+ *   - the L-stable Rosenbrock method RODAS3 with a sparse LU whose fill-reducing ordering and symbolic
+ *     factorisation are fixed once per mechanism, one warp per cell.
+ *
+ * Conventions for every entry point below.
+ *   - Array arguments of the compute calls are DEVICE pointers (cudaMalloc / torch tensors on the
+ *     handle's device), FP64 unless stated, caller-owned, and must stay valid until the work queued on
+ *     `stream` completes.  Cell arrays are structure-of-arrays with leading dimension N: species k of
+ *     cell c is Y[k*N + c].
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls are asynchronous.
+ *   - Return value: CHEM_OK, or an error code for argument, launch or CUDA errors; chem_last_error()
+ *     returns the message of the last failure on the calling thread.  Per-cell numerical failures never
+ *     fail the call: they are reported in the per-cell status array.
+ *   - No call aborts, traps or prints.  A handle may be used from one host thread at a time.
+ *   - Units: SI (K, Pa, kg/mol, mol/m^3, J/mol, s).
+ */
+#ifndef CHEM_H_
+#define CHEM_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chem_handle_s* chem_handle;
+typedef struct CUstream_st* chem_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  CHEM_OK = 0,
+  CHEM_EINVAL = 1,       /* invalid argument or mechanism description */
+  CHEM_ENOMEM = 2,       /* device or host allocation failed */
+  CHEM_ECUDA = 3,        /* a CUDA runtime call failed */
+  CHEM_EUNSUPPORTED = 4  /* valid but outside this build's limits (e.g. shared memory per cell) */
+} chem_status;
+
+/* Per-cell status codes written by chem_integrate. */
+enum {
+  CHEM_CELL_OK = 0,
+  CHEM_CELL_MAXSTEPS = 1,  /* max_substeps attempts reached before t = dt */
+  CHEM_CELL_HMIN = 2,      /* step size fell below h_min */
+  CHEM_CELL_NONFINITE = 3, /* max_nonfinite consecutive attempts produced non-finite values */
+  CHEM_CELL_BADINPUT = 4,  /* T <= 0, p <= 0, dt < 0, non-finite input, or sum(Y/W) <= 0 */
+  CHEM_CELL_TIMEOUT = 5    /* the call's time budget ran out before this cell finished */
+};
+
+/* Mechanism description (host memory, copied by chem_create; the caller keeps ownership).
+   Reactions are reversible unless reversible[r] == 0.  rtype: 0 elementary, 1 third-body
+   (rate multiplied by [M]), 2 Troe fall-off (k = k_inf Pr/(1+Pr) F, no [M] multiplier).
+   Participants: CSR lists by reaction, species index and stoichiometric coefficient (1..3), at most 3
+   distinct species and total order 3 per side.  Efficiencies: CSR list by reaction of species whose
+   third-body efficiency differs from 1 (ignored for elementary reactions).  Arrhenius: k = A T^b
+   exp(-Ea/(Ru T)), A in SI units of the reaction's order; for Troe, A/b/Ea are the high-pressure limit
+   and low[3r..3r+2] = (A0, b0, Ea0) the low-pressure limit; troe[4r..4r+3] = (alpha, T3, T1, T2), with
+   T2 <= 0 meaning the T2 term is absent.  NASA-7: nasa_lo/nasa_hi [7n], low set used for T < T_mid[k].
+   comp (nullable): element counts [n*n_elements], enabling the element-balance check. */
+typedef struct {
+  int n_species;
+  int n_reactions;
+  int n_elements;
+  const double* W;         /* [n] molar masses, kg/mol, > 0 */
+  const double* nasa_lo;   /* [7n] */
+  const double* nasa_hi;   /* [7n] */
+  const double* T_mid;     /* [n] */
+  const int* comp;         /* [n*n_elements] or NULL */
+  const int* reac_ptr;     /* [R+1] */
+  const int* reac_sp;
+  const int* reac_nu;
+  const int* prod_ptr;     /* [R+1] */
+  const int* prod_sp;
+  const int* prod_nu;
+  const double* A;         /* [R] */
+  const double* b;         /* [R] */
+  const double* Ea;        /* [R] J/mol */
+  const int* rtype;        /* [R] */
+  const int* reversible;   /* [R] */
+  const int* eff_ptr;      /* [R+1] */
+  const int* eff_sp;
+  const double* eff_alpha;
+  const double* troe;      /* [4R] */
+  const double* low;       /* [3R] */
+} chem_mech_desc;
+
+/* Sizes of a compiled mechanism. */
+typedef struct {
+  int n_species;
+  int n_reactions;
+  int n_state;        /* m = n_species + 1 */
+  int nnz_S;          /* entries of the static Jacobian pattern (T row and column included) */
+  int nnz_LU;         /* entries of the factor after fill (fill-reducing ordering, T last) */
+  int lu_steps;       /* warp-wide steps of the precomputed elimination program */
+  int solve_steps;    /* warp-wide steps of one forward+backward solve */
+  int smem_per_cell;  /* bytes of shared memory one cell needs in the integrator */
+  int n_dslots;       /* per-reaction derivative slots used by the Jacobian */
+} chem_info_t;
+
+/* Options of chem_integrate (zero-initialise, then set; zero/negative fields take the defaults). */
+typedef struct {
+  double rtol;            /* default 1e-6 */
+  double atol;            /* default 1e-12 (applies to T too) */
+  double h_init;          /* default first step when h_io[c] <= 0: 1e-7 s */
+  double h_min;           /* default 1e-20 s */
+  double time_budget_s;   /* wall-clock budget of the call on the device; 0: none */
+  int max_substeps;       /* default 100000 attempts per cell */
+  int max_nonfinite;      /* default 10 consecutive non-finite attempts (each divides h by 10) */
+  int mode;               /* 0: plain one-warp-per-cell launch (reference form); 1: persistent
+                             work-queue kernel over cells sorted by their previous substep count */
+  int block_warps;        /* warps (cells in flight) per block; 0: automatic */
+  int chunk;              /* cells taken per queue pull in mode 1; 0: automatic */
+  int* naccept;           /* optional DEVICE array [N]: accepted steps per cell (NULL: not written) */
+  double* trace;          /* optional DEVICE array [trace_cap*N]: attempt i of cell c at trace[i*N + c],
+                             +h if accepted, -h if rejected, 0 after the last attempt (NULL: off) */
+  int trace_cap;          /* attempts recorded per cell */
+} chem_integrate_opts;
+
+/* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,
+   element balance when comp is given), reaction reordering by type, the static Jacobian pattern, a
+   minimum-degree ordering with T last, the symbolic LU and its warp elimination program, and upload of
+   all tables.  On success *out owns device memory until chem_destroy. */
+chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out);
+/* device == -1 compiles on the host only (no GPU needed): chem_info, chem_jacobian_pattern and
+   chem_export_plan work, compute calls return CHEM_EINVAL. */
+chem_status chem_destroy(chem_handle h);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char* chem_last_error(void);
+
+chem_status chem_info(chem_handle h, chem_info_t* info);
+
+/* The static pattern of S in natural state order (0 = T, 1 + k = Y_k), CSR, HOST arrays:
+   row_ptr [m+1], col_idx [nnz_S]. Entry e of chem_jacobian's S_vals is (row of e, col_idx[e]). */
+chem_status chem_jacobian_pattern(chem_handle h, int* row_ptr, int* col_idx);
+
+/* Host copy of a compiled plan, for inspection and CPU-side checks.  which:
+     0 elimination program, 1 substitution program: 4 ints per lane-op (kind, t, a, b), 32 per step,
+       t = 65535 marks an idle lane; kinds 0 reciprocal, 1 scale, 2 update (see the device code);
+     2 ordering: perm[p] = state index at factor position p (m ints);
+     3 factor pattern: row_ptr (m+1) then col (nnz_LU), factor positions;
+     4 factor slot sources: S entry (internal order) feeding each factor slot, -1 for fill (nnz_LU);
+     5 internal S entry -> CSR position of chem_jacobian_pattern (nnz_S).
+   With out == NULL only *count is written.  *count: number of ints. */
+chem_status chem_export_plan(chem_handle h, int which, int* out, int* count);
+
+/* Right-hand side of the reactor ODE for N cells:
+   dTdt [N] = -sum_k H_k w_k / (rho c_p), dYdt [n*N] = W_k w_k / rho, wdot [n*N] (nullable) = net molar
+   production rates w_k in mol/(m^3 s).  Inputs T [N], p [N], Y [n*N]. */
+chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, const double* Y,
+                       double* dTdt, double* dYdt, double* wdot, chem_stream stream);
+
+/* Exact Jacobian of chem_rates' right-hand side, J = S + u v^T, for N cells:
+   S_vals [nnz_S*N] (entry-major: entry e of cell c at S_vals[e*N + c], entries in the CSR order of
+   chem_jacobian_pattern), u [m*N], v [m*N] (v_0 = 0, v_{1+k} = Wbar / W_k). */
+chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p, const double* Y,
+                          double* S_vals, double* u, double* v, chem_stream stream);
+
+/* Advance N cells over their own step dt[c] with RODAS3 and error control.
+   In/out: T [N], Y [n*N]; h_io [N] (in: first step, <= 0 takes h_init; out: next proposed step);
+   nsub [N] (in: previous substep counts, the sort key of mode 1; out: attempts taken in this call);
+   status [N] (out: CHEM_CELL_*).  In: p [N], dt [N].  opts may be NULL (defaults).
+   Scratch for mode 1 (sorting and the queue) is held by the handle and grows on demand. */
+chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
+                           double* h_io, int* nsub, int* status, const chem_integrate_opts* opts,
+                           chem_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEM_H_ */

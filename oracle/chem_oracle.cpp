@@ -671,10 +671,11 @@ int oracle_replay_sens_cs(const OMech* m, double p, const double* y0, const doub
 }
 
 /* Batch driver over N cells (structure of arrays: Y[k*N + c]); OpenMP dynamic schedule over cells.
-   h_io: in initial step (<= 0: default), out last proposed step.  Returns the number of threads used. */
+   h_io: in initial step (<= 0: default), out last proposed step.  Optional trace [trace_cap*N]: attempt i
+   of cell c at trace[i*N + c], +h accepted, -h rejected, 0 after the last.  Returns the thread count. */
 int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, double* Y, const double* dt,
                            double rtol, double atol, int max_steps, double* h_io, int* nsub, int* nacc, int* status,
-                           int nthreads) {
+                           int nthreads, double* trace, int trace_cap) {
   Controls cc = make_controls(rtol, atol, max_steps);
   const int mm = m->n + 1;
   int used = 1;
@@ -693,7 +694,14 @@ int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, do
     for (int k = 0; k < m->n; ++k) y[1 + k] = Y[(size_t)k * N + c];
     double hout;
     int ns, na;
-    int st = integrate_cell(*m, p[c], y.data(), dt[c], cc, h_io ? h_io[c] : 0.0, &hout, &ns, &na, nullptr, nullptr);
+    std::vector<double> th;
+    std::vector<int> ta;
+    int st = integrate_cell(*m, p[c], y.data(), dt[c], cc, h_io ? h_io[c] : 0.0, &hout, &ns, &na,
+                            trace ? &th : nullptr, trace ? &ta : nullptr);
+    if (trace) {
+      for (int i = 0; i < trace_cap; ++i)
+        trace[(size_t)i * N + c] = i < (int)th.size() ? (ta[i] ? th[i] : -th[i]) : 0.0;
+    }
     T[c] = y[0];
     for (int k = 0; k < m->n; ++k) Y[(size_t)k * N + c] = y[1 + k];
     if (h_io) h_io[c] = hout;

@@ -49,7 +49,7 @@ def lib():
         L.oracle_replay_sens_cs.argtypes = [C.c_void_p, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_int,
                                             C.c_double, _dp]
         L.oracle_integrate_batch.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
-                                             C.c_int, _dp, _ip, _ip, _ip, C.c_int]
+                                             C.c_int, _dp, _ip, _ip, _ip, C.c_int, _dp, C.c_int]
         _lib = L
     return _lib
 
@@ -177,7 +177,8 @@ class Oracle:
             raise RuntimeError("singular iteration matrix in replay")
         return dy
 
-    def integrate_batch(self, T, p, Y, dt, rtol=1e-6, atol=1e-12, h_io=None, max_steps=100000, nthreads=0):
+    def integrate_batch(self, T, p, Y, dt, rtol=1e-6, atol=1e-12, h_io=None, max_steps=100000, nthreads=0,
+                        trace_cap=0):
         """Structure-of-arrays batch (Y[k, c]); returns a dict of new arrays and the thread count."""
         N = int(T.shape[0])
         T = np.array(T, dtype=np.float64)
@@ -186,6 +187,10 @@ class Oracle:
         dt = np.ascontiguousarray(dt, dtype=np.float64)
         h = np.zeros(N) if h_io is None else np.array(h_io, dtype=np.float64)
         ns = np.zeros(N, dtype=np.int32); na = np.zeros(N, dtype=np.int32); st = np.zeros(N, dtype=np.int32)
+        tr = np.zeros((trace_cap, N)) if trace_cap > 0 else None
         used = self.L.oracle_integrate_batch(self._p, N, _d(T), _d(p), _d(Yc), _d(dt), rtol, atol, max_steps,
-                                             _d(h), _i(ns), _i(na), _i(st), nthreads)
-        return dict(T=T, Y=Yc, h=h, nsub=ns, nacc=na, status=st, threads=used)
+                                             _d(h), _i(ns), _i(na), _i(st), nthreads, _d(tr), trace_cap)
+        out = dict(T=T, Y=Yc, h=h, nsub=ns, nacc=na, status=st, threads=used)
+        if tr is not None:
+            out["trace"] = tr
+        return out

@@ -1,0 +1,415 @@
+// capi.cu -- C ABI: handle life cycle, table upload, kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/chem.h"
+#include "compile.h"
+#include "device.cuh"
+
+using namespace chemgb;
+
+namespace {
+
+thread_local std::string g_err;
+
+chem_status fail(chem_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+chem_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(CHEM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct chem_handle_s {
+  int device = 0;
+  HostMech hm;
+  MechView view{};
+  void* blob = nullptr;
+  CellLayout L{};
+  int cell_bytes = 0;
+  int smem_optin = 0;
+  int num_sms = 0;
+  bool attr_set = false;
+  // scratch of the persistent mode (grows on demand)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+namespace {
+
+// Shared-memory layout of one cell (offsets in doubles).
+CellLayout make_layout(const HostMech& hm) {
+  CellLayout L{};
+  int o = 0;
+  const int m = hm.m, n = hm.n, R = hm.R;
+  auto take = [&](int cnt) { int at = o; o += cnt; return at; };
+  L.y = take(m); L.ytmp = take(m); L.f0 = take(m); L.U1 = take(m); L.U2 = take(m); L.U3 = take(m);
+  L.U4 = take(m); L.x = take(m); L.z = take(m); L.u = take(m); L.v = take(m);
+  L.C = take(n); L.hRT = take(n); L.eg = take(n); L.emg = take(n); L.cpR = take(n);
+  L.q = take(std::max(R, 1)); L.dqdT = take(std::max(R, 1));
+  L.S = take(hm.nnz_S);
+  // the derivative slots are dead once S is assembled; the factor reuses their space
+  const int lu_part = hm.nnz_LU + m;
+  const int reuse = std::max(lu_part, hm.n_dslot);
+  L.D = o;
+  L.LU = o;
+  L.dinv = o + hm.nnz_LU;
+  o += reuse;
+  int np = 1;
+  for (const HostGather* g : {&hm.g_omega, &hm.g_dtil, &hm.g_row, &hm.g_col}) np = std::max(np, g->n_partial);
+  L.part = take(2 * np);
+  L.misc = take(16);
+  L.total = o;
+  return L;
+}
+
+template <class T>
+size_t put(std::vector<char>& buf, const std::vector<T>& v) {
+  size_t off = align_up(buf.size(), 256);
+  buf.resize(off + v.size() * sizeof(T) + 8);
+  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+}  // namespace
+
+// =============================================================================================== kernels
+namespace chemgb {
+
+// Load one cell's state into y (lanes over state components).
+__device__ __forceinline__ void load_state(double* y, int m, int N, int c, const double* T, const double* Y, int lane) {
+  for (int i = lane; i < m; i += kWarp) y[i] = (i == 0) ? T[c] : Y[(size_t)(i - 1) * N + c];
+  __syncwarp();
+}
+
+// Block-cooperative coalesced load of the block's consecutive cells: adjacent threads read adjacent
+// cells of the same state row (structure of arrays), then each warp owns its cell's copy.
+__device__ __forceinline__ void load_tile(double* smem, const CellLayout& L, int m, int N, int c0, int wpb,
+                                          const double* T, const double* Y) {
+  const int total = wpb * m;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = idx / wpb, w = idx - row * wpb;
+    const int c = c0 + w;
+    if (c < N) smem[(size_t)w * L.total + L.y + row] = (row == 0) ? T[c] : Y[(size_t)(row - 1) * N + c];
+  }
+  __syncthreads();
+}
+
+__global__ void k_rates(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
+                        const double* __restrict__ Y, double* __restrict__ dTdt, double* __restrict__ dYdt,
+                        double* __restrict__ wdot) {
+  extern __shared__ double smem[];
+  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int c0 = blockIdx.x * wpb;
+  double* s = smem + (size_t)w * L.total;
+  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
+  const int c = c0 + w;
+  if (c >= N) return;
+  double* f = s + L.f0;
+  Scal sc = eval_f(M, s, L, s + L.y, p[c], f, lane);
+  for (int i = lane; i < M.m; i += kWarp) {
+    if (i == 0) dTdt[c] = f[0];
+    else dYdt[(size_t)(i - 1) * N + c] = f[i];
+  }
+  if (wdot) {
+    for (int k = lane; k < M.n; k += kWarp) wdot[(size_t)k * N + c] = f[1 + k] * sc.rho * __ldg(M.sp + (size_t)k * SP_STRIDE);
+  }
+}
+
+__global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
+                           const double* __restrict__ Y, double* __restrict__ Sv, double* __restrict__ u,
+                           double* __restrict__ v) {
+  extern __shared__ double smem[];
+  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int c0 = blockIdx.x * wpb;
+  double* s = smem + (size_t)w * L.total;
+  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
+  const int c = c0 + w;
+  if (c >= N) return;
+  eval_jac(M, s, L, s + L.y, p[c], lane);
+  for (int e = lane; e < M.nnz_S; e += kWarp) Sv[(size_t)__ldg(M.s_out + e) * N + c] = s[L.S + e];
+  for (int i = lane; i < M.m; i += kWarp) {
+    u[(size_t)i * N + c] = s[L.u + i];
+    v[(size_t)i * N + c] = s[L.v + i];
+  }
+}
+
+// Plain form: one warp per cell, cells in index order, one launch.
+__global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __restrict__ T, const double* __restrict__ p,
+                                  double* __restrict__ Y, const double* __restrict__ dt, double* __restrict__ h_io,
+                                  int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
+                                  IntOpts o) {
+  extern __shared__ double smem[];
+  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int c0 = blockIdx.x * wpb;
+  double* s = smem + (size_t)w * L.total;
+  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
+  const int c = c0 + w;
+  if (c >= N) return;
+  double h = h_io[c];
+  int ns = 0, na = 0, st = 0;
+  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, o, lane, c);
+  const double* y = s + L.y;
+  for (int i = lane; i < M.m; i += kWarp) {
+    if (i == 0) T[c] = y[0];
+    else Y[(size_t)(i - 1) * N + c] = y[i];
+  }
+  if (lane == 0) {
+    h_io[c] = h;
+    nsub[c] = ns;
+    status[c] = st;
+    if (nacc_out) nacc_out[c] = na;
+  }
+}
+
+}  // namespace chemgb
+
+// =============================================================================================== ABI
+namespace {
+
+chem_status check_handle(chem_handle h) {
+  if (!h) return fail(CHEM_EINVAL, "null handle");
+  if (h->device < 0) return fail(CHEM_EINVAL, "handle was compiled on the host only (device -1)");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return CHEM_OK;
+}
+
+chem_status set_attrs(chem_handle h) {
+  if (h->attr_set) return CHEM_OK;
+  const int bytes = h->smem_optin;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_integrate_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute");
+  h->attr_set = true;
+  return CHEM_OK;
+}
+
+int warps_per_block(const chem_handle h, int requested) {
+  int wpb = requested > 0 ? requested : 1;
+  while (wpb > 1 && wpb * h->cell_bytes > h->smem_optin) --wpb;
+  return wpb;
+}
+
+chem_status launch_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return CHEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* chem_last_error(void) { return g_err.c_str(); }
+
+chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out) {
+  g_err.clear();
+  if (!desc || !out) return fail(CHEM_EINVAL, "desc and out must not be NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = device == -1 ? cudaSuccess : cudaGetDeviceCount(&ndev);
+  const bool host_only = device == -1;
+  if (host_only) {
+    chem_handle h = new (std::nothrow) chem_handle_s();
+    if (!h) return fail(CHEM_ENOMEM, "host allocation failed");
+    h->device = -1;
+    std::string err;
+    chem_status st = compile_mechanism(*desc, h->hm, err);
+    if (st != CHEM_OK) { delete h; return fail(st, err); }
+    h->L = make_layout(h->hm);
+    h->cell_bytes = h->L.total * (int)sizeof(double);
+    *out = h;
+    return CHEM_OK;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(CHEM_EINVAL, "device index out of range");
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  chem_handle h = new (std::nothrow) chem_handle_s();
+  if (!h) return fail(CHEM_ENOMEM, "host allocation failed");
+  h->device = device;
+  std::string err;
+  chem_status st = compile_mechanism(*desc, h->hm, err);
+  if (st != CHEM_OK) { delete h; return fail(st, err); }
+  const HostMech& hm = h->hm;
+  h->L = make_layout(hm);
+  h->cell_bytes = h->L.total * (int)sizeof(double);
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDeviceProperties"); }
+  h->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  h->num_sms = prop.multiProcessorCount;
+  if (h->cell_bytes > h->smem_optin) {
+    delete h;
+    return fail(CHEM_EUNSUPPORTED, "mechanism needs " + std::to_string(h->L.total * 8) +
+                                       " bytes of shared memory per cell, more than the device allows");
+  }
+  // pack every table into one device allocation
+  std::vector<char> buf;
+  size_t o_sp = put(buf, hm.sp), o_rxd = put(buf, hm.rxd), o_rxi = put(buf, hm.rxi), o_esp = put(buf, hm.eff_sp),
+         o_eam = put(buf, hm.eff_am1), o_dsp = put(buf, hm.dslot_sp), o_dmask = put(buf, hm.dslot_mask),
+         o_dam = put(buf, hm.dslot_am1), o_er = put(buf, hm.entry_row), o_ec = put(buf, hm.entry_col),
+         o_ew = put(buf, hm.entry_wratio), o_lsrc = put(buf, hm.lu_src), o_ldiag = put(buf, hm.lu_diag),
+         o_lops = put(buf, hm.lu_ops), o_lkind = put(buf, hm.lu_kind), o_sops = put(buf, hm.sv_ops),
+         o_skind = put(buf, hm.sv_kind), o_sout = put(buf, hm.s_out);
+  size_t o_g[4][2];
+  const HostGather* gs[4] = {&hm.g_omega, &hm.g_dtil, &hm.g_row, &hm.g_col};
+  for (int i = 0; i < 4; ++i) { o_g[i][0] = put(buf, gs[i]->ops); o_g[i][1] = put(buf, gs[i]->comb); }
+  if ((e = cudaMalloc(&h->blob, buf.size())) != cudaSuccess) { delete h; return fail(CHEM_ENOMEM, "cudaMalloc of mechanism tables failed"); }
+  if ((e = cudaMemcpy(h->blob, buf.data(), buf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(h->blob);
+    delete h;
+    return cuda_fail(e, "cudaMemcpy of mechanism tables");
+  }
+  char* b = (char*)h->blob;
+  MechView& V = h->view;
+  V.n = hm.n; V.R = hm.R; V.m = hm.m; V.n_troe = hm.n_troe; V.n_tb = hm.n_tb; V.nY = hm.nY; V.nnz_S = hm.nnz_S;
+  V.nnz_LU = hm.nnz_LU; V.n_dslot = hm.n_dslot;
+  V.sp = (const double*)(b + o_sp); V.rxd = (const double*)(b + o_rxd); V.rxi = (const int*)(b + o_rxi);
+  V.eff_sp = (const int*)(b + o_esp); V.eff_am1 = (const double*)(b + o_eam);
+  V.dslot_sp = (const int*)(b + o_dsp); V.dslot_mask = (const int*)(b + o_dmask); V.dslot_am1 = (const double*)(b + o_dam);
+  V.entry_row = (const int*)(b + o_er); V.entry_col = (const int*)(b + o_ec); V.entry_wratio = (const double*)(b + o_ew);
+  V.lu_src = (const int*)(b + o_lsrc); V.lu_diag = (const int*)(b + o_ldiag);
+  V.lu_ops = (const ElimOp*)(b + o_lops); V.lu_kind = (const uint8_t*)(b + o_lkind); V.lu_steps = (int)hm.lu_kind.size();
+  V.sv_ops = (const ElimOp*)(b + o_sops); V.sv_kind = (const uint8_t*)(b + o_skind); V.sv_steps = (int)hm.sv_kind.size();
+  V.s_out = (const int*)(b + o_sout);
+  Gather* vg[4] = {&V.g_omega, &V.g_dtil, &V.g_row, &V.g_col};
+  for (int i = 0; i < 4; ++i) {
+    vg[i]->ops = (const GatherOp*)(b + o_g[i][0]);
+    vg[i]->steps = gs[i]->steps;
+    vg[i]->n_partial = gs[i]->n_partial;
+    vg[i]->comb = (const int*)(b + o_g[i][1]);
+    vg[i]->n_comb = (int)gs[i]->comb.size() / 3;
+  }
+  *out = h;
+  return CHEM_OK;
+}
+
+chem_status chem_destroy(chem_handle h) {
+  if (!h) return CHEM_OK;
+  if (h->device < 0) { delete h; return CHEM_OK; }
+  cudaSetDevice(h->device);
+  if (h->blob) cudaFree(h->blob);
+  if (h->scratch) cudaFree(h->scratch);
+  delete h;
+  return CHEM_OK;
+}
+
+chem_status chem_info(chem_handle h, chem_info_t* info) {
+  if (!h || !info) return fail(CHEM_EINVAL, "null argument");
+  info->n_species = h->hm.n;
+  info->n_reactions = h->hm.R;
+  info->n_state = h->hm.m;
+  info->nnz_S = h->hm.nnz_S;
+  info->nnz_LU = h->hm.nnz_LU;
+  info->lu_steps = (int)h->hm.lu_kind.size();
+  info->solve_steps = (int)h->hm.sv_kind.size();
+  info->smem_per_cell = h->cell_bytes;
+  info->n_dslots = h->hm.n_dslot;
+  return CHEM_OK;
+}
+
+chem_status chem_jacobian_pattern(chem_handle h, int* row_ptr, int* col_idx) {
+  if (!h || !row_ptr || !col_idx) return fail(CHEM_EINVAL, "null argument");
+  std::copy(h->hm.csr_ptr.begin(), h->hm.csr_ptr.end(), row_ptr);
+  std::copy(h->hm.csr_col.begin(), h->hm.csr_col.end(), col_idx);
+  return CHEM_OK;
+}
+
+chem_status chem_export_plan(chem_handle h, int which, int* out, int* count) {
+  if (!h || !count) return fail(CHEM_EINVAL, "null argument");
+  const HostMech& hm = h->hm;
+  std::vector<int> v;
+  auto prog = [&](const std::vector<ElimOp>& ops, const std::vector<uint8_t>& kinds) {
+    for (size_t st = 0; st < kinds.size(); ++st)
+      for (int l = 0; l < kWarp; ++l) {
+        const ElimOp& o = ops[st * kWarp + l];
+        v.push_back(kinds[st]); v.push_back(o.t); v.push_back(o.a); v.push_back(o.b);
+      }
+  };
+  switch (which) {
+    case 0: prog(hm.lu_ops, hm.lu_kind); break;
+    case 1: prog(hm.sv_ops, hm.sv_kind); break;
+    case 2: v = hm.perm; break;
+    case 3: v = hm.lu_rowptr; v.insert(v.end(), hm.lu_col.begin(), hm.lu_col.end()); break;
+    case 4: v = hm.lu_src; break;
+    case 5: v = hm.s_out; break;
+    default: return fail(CHEM_EINVAL, "unknown plan part");
+  }
+  if (out) std::copy(v.begin(), v.end(), out);
+  *count = (int)v.size();
+  return CHEM_OK;
+}
+
+chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, const double* Y, double* dTdt,
+                       double* dYdt, double* wdot, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N == 0) return CHEM_OK;
+  if (!T || !p || !Y || !dTdt || !dYdt) return fail(CHEM_EINVAL, "null array argument");
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  const int wpb = warps_per_block(h, 4);
+  k_rates<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view, h->L, N, T, p, Y,
+                                                                                           dTdt, dYdt, wdot);
+  return launch_check("chem_rates launch");
+}
+
+chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p, const double* Y, double* S_vals,
+                          double* u, double* v, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N == 0) return CHEM_OK;
+  if (!T || !p || !Y || !S_vals || !u || !v) return fail(CHEM_EINVAL, "null array argument");
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  const int wpb = warps_per_block(h, 4);
+  k_jacobian<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view, h->L, N, T, p,
+                                                                                              Y, S_vals, u, v);
+  return launch_check("chem_jacobian launch");
+}
+
+chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
+                           double* h_io, int* nsub, int* status, const chem_integrate_opts* opts, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N == 0) return CHEM_OK;
+  if (!T || !p || !Y || !dt || !h_io || !nsub || !status) return fail(CHEM_EINVAL, "null array argument");
+  chem_integrate_opts o{};
+  if (opts) o = *opts;
+  IntOpts io;
+  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
+  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
+  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
+  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
+  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
+  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
+  io.deadline_ns = 0;
+  io.trace = o.trace;
+  io.trace_cap = o.trace ? o.trace_cap : 0;
+  io.N = N;
+  if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
+  if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
+    return fail(CHEM_EINVAL, "non-finite option");
+  if (o.mode != 0) return fail(CHEM_EUNSUPPORTED, "only mode 0 (plain) is available in this build");
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  if (o.time_budget_s > 0.0) return fail(CHEM_EUNSUPPORTED, "time_budget_s is not available in this build");
+  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
+  k_integrate_plain<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(
+      h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, io);
+  return launch_check("chem_integrate launch");
+}
+
+}  // extern "C"

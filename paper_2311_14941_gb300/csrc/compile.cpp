@@ -1,0 +1,543 @@
+// compile.cpp -- host mechanism compiler.
+//
+// The paper's chemistry library gets its speed from three mechanism-level preparations (Sec. 2.5):
+// internal sparse management of mechanism quantities, a sparse analytical Jacobian, and (for the stiff
+// solver) sparse linear algebra.  Here all of that is decided once, on the host, when a handle is
+// created:
+//   1. validation and reordering of reactions by type (Troe, third-body, elementary) so that warp lanes
+//      working on consecutive reactions take the same branch;
+//   2. the static pattern of the sparse Jacobian part S (T row and column, species couplings through
+//      shared reactions and listed collision efficiencies);
+//   3. a minimum-degree ordering of the species block with T last, the symbolic LU (fill) of
+//      I/(h gamma) - S in that order, and DAG-scheduled warp programs for the numeric factorisation and
+//      the two triangular solves;
+//   4. load-balanced warp "gather" programs for every sparse reduction of the rate and Jacobian
+//      evaluation (production rates, Jacobian entries, row and column sums).
+#include "compile.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <numeric>
+#include <set>
+
+namespace chemgb {
+namespace {
+
+bool fin(double x) { return std::isfinite(x); }
+
+// ------------------------------------------------------------------------ gather programs
+// groups[g] = list of (a, b) terms summed into output g.  Terms are dealt to the 32 lanes so that the
+// longest lane is as short as possible: a group longer than the per-lane target is split into pieces
+// whose partial sums are combined afterwards; pieces go to lanes largest first (LPT).
+bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, HostGather& G, std::string& err) {
+  G = HostGather();
+  long total = 0;
+  for (auto& g : groups) total += std::max<size_t>(g.size(), 1);
+  if (groups.empty()) return true;
+  const long cap = std::max<long>(1, (total + kWarp - 1) / kWarp);
+  struct Piece { int g; int first; int count; int partial; };
+  std::vector<Piece> pieces;
+  int n_partial = 0;
+  for (size_t g = 0; g < groups.size(); ++g) {
+    const int L = (int)groups[g].size();
+    if (L <= cap) {
+      pieces.push_back({(int)g, 0, L, -1});
+    } else {
+      const int np = (int)((L + cap - 1) / cap);
+      const int per = (L + np - 1) / np;
+      G.comb.push_back((int)g);
+      G.comb.push_back(n_partial);
+      G.comb.push_back(np);
+      for (int p = 0; p < np; ++p) {
+        int f = p * per, c = std::min(per, L - f);
+        pieces.push_back({(int)g, f, c, n_partial++});
+      }
+    }
+  }
+  G.n_partial = n_partial;
+  std::vector<int> order(pieces.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return std::max(pieces[x].count, 1) > std::max(pieces[y].count, 1); });
+  std::vector<std::vector<int>> lane(kWarp);
+  std::vector<long> load(kWarp, 0);
+  for (int pi : order) {
+    int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lane[l].push_back(pi);
+    load[l] += std::max(pieces[pi].count, 1);
+  }
+  G.steps = (int)*std::max_element(load.begin(), load.end());
+  G.ops.assign((size_t)G.steps * kWarp, GatherOp{0, 0, DST_NONE, 1});
+  for (int l = 0; l < kWarp; ++l) {
+    int s = 0;
+    for (int pi : lane[l]) {
+      const Piece& P = pieces[pi];
+      const auto& terms = groups[P.g];
+      const int cnt = std::max(P.count, 1);
+      for (int t = 0; t < cnt; ++t, ++s) {
+        GatherOp op{0, 0, DST_NONE, 1};
+        if (P.count > 0) {
+          auto ab = terms[P.first + t];
+          if (ab.first < 0 || ab.first > 0xFFFF || ab.second < -32768 || ab.second > 0xFFFF) {
+            err = "mechanism too large for 16-bit program indices";
+            return false;
+          }
+          op.a = (uint16_t)ab.first;
+          op.b = (uint16_t)(ab.second & 0xFFFF);
+          op.flags = 0;
+        }
+        if (t == cnt - 1) {
+          int dst = P.partial >= 0 ? (PARTIAL_BIT | P.partial) : P.g;
+          if (P.partial < 0 && P.g >= PARTIAL_BIT) { err = "too many gather outputs"; return false; }
+          op.dst = (uint16_t)dst;
+        }
+        G.ops[(size_t)s * kWarp + l] = op;
+      }
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------------ DAG list scheduler
+struct DagOp {
+  int kind;
+  int target;      // location written (distinct within a step)
+  ElimOp enc;
+  std::vector<int> succ;
+  int npred = 0;
+  int prio = 0;
+};
+
+// Steps of one kind, at most 32 ops, distinct targets; ops become ready when all predecessors are done.
+// Priority = longest path to the end of the DAG (critical path first).
+bool schedule(std::vector<DagOp>& ops, std::vector<ElimOp>& out, std::vector<uint8_t>& kinds, std::string& err) {
+  const int N = (int)ops.size();
+  std::vector<int> indeg(N, 0), topo;
+  topo.reserve(N);
+  for (auto& o : ops) for (int s : o.succ) indeg[s]++;
+  for (int i = 0; i < N; ++i) ops[i].npred = indeg[i];
+  std::vector<int> q;
+  for (int i = 0; i < N; ++i) if (indeg[i] == 0) q.push_back(i);
+  for (size_t h = 0; h < q.size(); ++h) {
+    int v = q[h];
+    topo.push_back(v);
+    for (int s : ops[v].succ) if (--indeg[s] == 0) q.push_back(s);
+  }
+  if ((int)topo.size() != N) { err = "internal error: cyclic elimination DAG"; return false; }
+  for (int i = N - 1; i >= 0; --i) {
+    int v = topo[i];
+    int best = 0;
+    for (int s : ops[v].succ) best = std::max(best, ops[s].prio);
+    ops[v].prio = best + 1;
+  }
+  std::vector<char> done(N, 0);
+  std::vector<int> ready;
+  for (int i = 0; i < N; ++i) if (ops[i].npred == 0) ready.push_back(i);
+  int remaining = N;
+  out.clear();
+  kinds.clear();
+  std::vector<int> newly;
+  while (remaining > 0) {
+    if (ready.empty()) { err = "internal error: scheduler stalled"; return false; }
+    std::stable_sort(ready.begin(), ready.end(), [&](int a, int b) {
+      if (ops[a].prio != ops[b].prio) return ops[a].prio > ops[b].prio;
+      return a < b;
+    });
+    const int K = ops[ready[0]].kind;
+    std::vector<int> step;
+    std::set<int> used;
+    std::vector<int> keep;
+    for (int v : ready) {
+      if ((int)step.size() < kWarp && ops[v].kind == K && !used.count(ops[v].target)) {
+        step.push_back(v);
+        used.insert(ops[v].target);
+      } else {
+        keep.push_back(v);
+      }
+    }
+    for (int l = 0; l < kWarp; ++l) {
+      if (l < (int)step.size()) out.push_back(ops[step[l]].enc);
+      else out.push_back(ElimOp{OP_IDLE, 0, 0, 0});
+    }
+    kinds.push_back((uint8_t)K);
+    newly.clear();
+    for (int v : step) {
+      done[v] = 1;
+      --remaining;
+      for (int s : ops[v].succ) if (--ops[s].npred == 0) newly.push_back(s);
+    }
+    ready = keep;
+    ready.insert(ready.end(), newly.begin(), newly.end());
+  }
+  return true;
+}
+
+// exact minimum-degree ordering on the elimination graph; `last` is eliminated last
+std::vector<int> min_degree_order(int m, const std::vector<std::vector<char>>& adj0, int last) {
+  std::vector<std::vector<char>> adj = adj0;
+  std::vector<char> alive(m, 1);
+  std::vector<int> order;
+  for (int step = 0; step < m - 1; ++step) {
+    int best = -1, bdeg = 1 << 30;
+    for (int v = 0; v < m; ++v) {
+      if (!alive[v] || v == last) continue;
+      int d = 0;
+      for (int u = 0; u < m; ++u) d += (alive[u] && adj[v][u]) ? 1 : 0;
+      if (d < bdeg) { bdeg = d; best = v; }
+    }
+    std::vector<int> nb;
+    for (int u = 0; u < m; ++u) if (alive[u] && adj[best][u]) nb.push_back(u);
+    for (int a : nb)
+      for (int b : nb)
+        if (a != b) adj[a][b] = 1;
+    alive[best] = 0;
+    order.push_back(best);
+  }
+  order.push_back(last);
+  return order;
+}
+
+}  // namespace
+
+chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string& err) {
+  hm = HostMech();
+  const int n = d.n_species, R = d.n_reactions;
+  if (n < 1 || R < 0) { err = "n_species must be >= 1 and n_reactions >= 0"; return CHEM_EINVAL; }
+  if (!d.W || !d.nasa_lo || !d.nasa_hi || !d.T_mid) { err = "species arrays must not be NULL"; return CHEM_EINVAL; }
+  if (R > 0 && (!d.reac_ptr || !d.reac_sp || !d.reac_nu || !d.prod_ptr || !d.prod_sp || !d.prod_nu || !d.A || !d.b ||
+                !d.Ea || !d.rtype || !d.reversible || !d.eff_ptr || !d.troe || !d.low)) {
+    err = "reaction arrays must not be NULL";
+    return CHEM_EINVAL;
+  }
+  for (int k = 0; k < n; ++k) {
+    if (!(d.W[k] > 0.0) || !fin(d.W[k])) { err = "molar mass of species " + std::to_string(k) + " must be positive"; return CHEM_EINVAL; }
+    if (!(d.T_mid[k] > 0.0) || !fin(d.T_mid[k])) { err = "T_mid of species " + std::to_string(k) + " must be positive"; return CHEM_EINVAL; }
+    for (int i = 0; i < 7; ++i)
+      if (!fin(d.nasa_lo[7 * k + i]) || !fin(d.nasa_hi[7 * k + i])) { err = "non-finite NASA-7 coefficient"; return CHEM_EINVAL; }
+  }
+  // ---- reactions: validate and expand
+  struct Rx {
+    int type, rev;
+    std::vector<int> ro, po;      // occurrences
+    std::vector<std::pair<int, double>> eff;
+    double A, b, Ea, A0, b0, Ea0, alpha, T3, T1, T2;
+  };
+  std::vector<Rx> rx(R);
+  for (int r = 0; r < R; ++r) {
+    Rx& x = rx[r];
+    x.type = d.rtype[r];
+    x.rev = d.reversible[r];
+    if (x.type < 0 || x.type > 2) { err = "reaction " + std::to_string(r) + ": type must be 0, 1 or 2"; return CHEM_EINVAL; }
+    if (x.rev != 0 && x.rev != 1) { err = "reaction " + std::to_string(r) + ": reversible must be 0 or 1"; return CHEM_EINVAL; }
+    for (int side = 0; side < 2; ++side) {
+      const int* ptr = side ? d.prod_ptr : d.reac_ptr;
+      const int* sp = side ? d.prod_sp : d.reac_sp;
+      const int* nu = side ? d.prod_nu : d.reac_nu;
+      if (ptr[r + 1] < ptr[r]) { err = "reaction " + std::to_string(r) + ": bad participant pointers"; return CHEM_EINVAL; }
+      std::vector<int>& occ = side ? x.po : x.ro;
+      std::set<int> seen;
+      for (int i = ptr[r]; i < ptr[r + 1]; ++i) {
+        if (sp[i] < 0 || sp[i] >= n) { err = "reaction " + std::to_string(r) + ": species index out of range"; return CHEM_EINVAL; }
+        if (nu[i] < 1 || nu[i] > 3) { err = "reaction " + std::to_string(r) + ": coefficients must be 1..3"; return CHEM_EINVAL; }
+        if (seen.count(sp[i])) { err = "reaction " + std::to_string(r) + ": species listed twice on one side"; return CHEM_EINVAL; }
+        seen.insert(sp[i]);
+        for (int c = 0; c < nu[i]; ++c) occ.push_back(sp[i]);
+      }
+      if (occ.empty()) { err = "reaction " + std::to_string(r) + ": empty side"; return CHEM_EINVAL; }
+      if (occ.size() > 3) { err = "reaction " + std::to_string(r) + ": order above 3 on one side"; return CHEM_EUNSUPPORTED; }
+    }
+    x.A = d.A[r]; x.b = d.b[r]; x.Ea = d.Ea[r];
+    if (!(x.A > 0.0) || !fin(x.A) || !fin(x.b) || !fin(x.Ea)) { err = "reaction " + std::to_string(r) + ": Arrhenius parameters must be finite with A > 0"; return CHEM_EINVAL; }
+    if (x.type != 0) {
+      if (d.eff_ptr[r + 1] < d.eff_ptr[r]) { err = "reaction " + std::to_string(r) + ": bad efficiency pointers"; return CHEM_EINVAL; }
+      std::set<int> seen;
+      for (int i = d.eff_ptr[r]; i < d.eff_ptr[r + 1]; ++i) {
+        int s = d.eff_sp[i];
+        double a = d.eff_alpha[i];
+        if (s < 0 || s >= n || seen.count(s)) { err = "reaction " + std::to_string(r) + ": bad efficiency species"; return CHEM_EINVAL; }
+        if (!(a >= 0.0) || !fin(a)) { err = "reaction " + std::to_string(r) + ": efficiency must be finite and >= 0"; return CHEM_EINVAL; }
+        seen.insert(s);
+        if (a != 1.0) x.eff.push_back({s, a});
+      }
+    }
+    x.A0 = x.b0 = x.Ea0 = x.alpha = x.T3 = x.T1 = x.T2 = 0.0;
+    if (x.type == 2) {
+      x.alpha = d.troe[4 * r]; x.T3 = d.troe[4 * r + 1]; x.T1 = d.troe[4 * r + 2]; x.T2 = d.troe[4 * r + 3];
+      x.A0 = d.low[3 * r]; x.b0 = d.low[3 * r + 1]; x.Ea0 = d.low[3 * r + 2];
+      if (!fin(x.alpha) || !(x.T3 > 0.0) || !(x.T1 > 0.0) || !fin(x.T2) || !(x.A0 > 0.0) || !fin(x.A0) || !fin(x.b0) || !fin(x.Ea0)) {
+        err = "reaction " + std::to_string(r) + ": invalid Troe parameters";
+        return CHEM_EINVAL;
+      }
+    }
+    if (d.comp && d.n_elements > 0) {
+      for (int e = 0; e < d.n_elements; ++e) {
+        long bal = 0;
+        for (int s : x.ro) bal -= d.comp[s * d.n_elements + e];
+        for (int s : x.po) bal += d.comp[s * d.n_elements + e];
+        if (bal != 0) { err = "reaction " + std::to_string(r) + " is not element balanced"; return CHEM_EINVAL; }
+      }
+    }
+  }
+  // ---- reorder: Troe, third-body, elementary (stable)
+  hm.n = n; hm.R = R; hm.m = n + 1;
+  const int m = n + 1;
+  for (int t : {2, 1, 0})
+    for (int r = 0; r < R; ++r) if (rx[r].type == t) hm.rx_order.push_back(r);
+  for (int r = 0; r < R; ++r) { if (rx[r].type == 2) hm.n_troe++; if (rx[r].type == 1) hm.n_tb++; }
+
+  // ---- species table
+  hm.sp.assign((size_t)n * SP_STRIDE, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double* s = &hm.sp[(size_t)k * SP_STRIDE];
+    s[0] = 1.0 / d.W[k]; s[1] = d.W[k]; s[2] = d.T_mid[k];
+    for (int rg = 0; rg < 2; ++rg) {
+      const double* a = rg ? &d.nasa_hi[7 * k] : &d.nasa_lo[7 * k];
+      double* c = s + 4 + rg * SP_RANGE;
+      for (int i = 0; i < 5; ++i) c[i] = a[i];
+      c[5] = a[1] / 2.0; c[6] = a[2] / 3.0; c[7] = a[3] / 4.0; c[8] = a[4] / 5.0;
+      c[9] = -a[1] / 2.0; c[10] = -a[2] / 6.0; c[11] = -a[3] / 12.0; c[12] = -a[4] / 20.0;
+      c[13] = a[5]; c[14] = a[6];
+      c[15] = 2.0 * a[2]; c[16] = 3.0 * a[3]; c[17] = 4.0 * a[4];
+    }
+  }
+  // ---- reaction tables, derivative slots
+  hm.rxd.assign((size_t)R * RX_D, 0.0);
+  hm.rxi.assign((size_t)R * RX_I, -1);
+  std::vector<std::vector<int>> net(R, std::vector<int>());   // per compiled reaction: (species, nu) pairs
+  std::vector<std::map<int, int>> netmap(R);
+  std::vector<std::vector<int>> slots_sp(R);
+  for (int r = 0; r < R; ++r) {
+    const Rx& x = rx[hm.rx_order[r]];
+    double* D = &hm.rxd[(size_t)r * RX_D];
+    D[0] = std::log(x.A); D[1] = x.b; D[2] = x.Ea / kRu;
+    if (x.type == 2) {
+      D[3] = std::log(x.A0); D[4] = x.b0; D[5] = x.Ea0 / kRu;
+      D[6] = 1.0 - x.alpha; D[7] = x.alpha; D[8] = 1.0 / x.T3; D[9] = 1.0 / x.T1; D[10] = x.T2 > 0.0 ? x.T2 : 0.0;
+    }
+    int* I = &hm.rxi[(size_t)r * RX_I];
+    I[0] = x.type; I[1] = x.rev; I[2] = (int)x.ro.size(); I[3] = (int)x.po.size();
+    for (size_t i = 0; i < x.ro.size(); ++i) I[4 + i] = x.ro[i];
+    for (size_t i = 0; i < x.po.size(); ++i) I[7 + i] = x.po[i];
+    I[10] = (int)x.po.size() - (int)x.ro.size();
+    I[11] = (int)hm.eff_sp.size();
+    I[12] = (int)x.eff.size();
+    for (auto& e : x.eff) { hm.eff_sp.push_back(e.first); hm.eff_am1.push_back(e.second - 1.0); }
+    for (int s : x.ro) netmap[r][s] -= 1;
+    for (int s : x.po) netmap[r][s] += 1;
+    // distinct column species: reactants, products, listed colliders
+    std::vector<int> cols;
+    auto addc = [&](int s) { if (std::find(cols.begin(), cols.end(), s) == cols.end()) cols.push_back(s); };
+    for (int s : x.ro) addc(s);
+    for (int s : x.po) addc(s);
+    if (x.type != 0) for (auto& e : x.eff) addc(e.first);
+    I[13] = hm.n_dslot;
+    I[14] = (int)cols.size();
+    for (int s : cols) {
+      int mask = 0;
+      for (size_t i = 0; i < x.ro.size(); ++i) if (x.ro[i] == s) mask |= 1 << i;
+      for (size_t i = 0; i < x.po.size(); ++i) if (x.po[i] == s) mask |= 1 << (3 + i);
+      double am1 = 0.0;
+      if (x.type != 0) for (auto& e : x.eff) if (e.first == s) am1 = e.second - 1.0;
+      hm.dslot_sp.push_back(s);
+      hm.dslot_mask.push_back(mask);
+      hm.dslot_am1.push_back(am1);
+      hm.n_dslot++;
+    }
+    slots_sp[r] = cols;
+  }
+  if (R > 0xFFFF || hm.n_dslot > 0xFFFF) { err = "mechanism too large for 16-bit program indices"; return CHEM_EUNSUPPORTED; }
+
+  // ---- S pattern, Y block (species k row, species j column)
+  std::vector<std::vector<char>> Yp(n, std::vector<char>(n, 0));
+  for (int k = 0; k < n; ++k) Yp[k][k] = 1;
+  for (int r = 0; r < R; ++r)
+    for (auto& kv : netmap[r]) {
+      if (kv.second == 0) continue;
+      for (int j : slots_sp[r]) Yp[kv.first][j] = 1;
+    }
+  std::vector<std::vector<int>> eidx(n, std::vector<int>(n, -1));
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      if (Yp[k][j]) {
+        eidx[k][j] = hm.nY++;
+        hm.entry_row.push_back(k);
+        hm.entry_col.push_back(j);
+        hm.entry_wratio.push_back(d.W[k] / d.W[j]);
+      }
+  hm.nnz_S = hm.nY + n + m;
+  if (hm.nnz_S > 0xFFFF) { err = "Jacobian pattern too large for 16-bit program indices"; return CHEM_EUNSUPPORTED; }
+  // state-index pattern: s_index(row, col) -> internal S index
+  auto s_index = [&](int row, int col) -> int {
+    if (row == 0) return hm.nY + n + col;          // T row (col 0 = TT)
+    if (col == 0) return hm.nY + (row - 1);        // T column
+    return eidx[row - 1][col - 1];
+  };
+  // natural CSR order for output
+  hm.csr_ptr.assign(m + 1, 0);
+  hm.s_out.assign(hm.nnz_S, -1);
+  {
+    int pos = 0;
+    for (int row = 0; row < m; ++row) {
+      hm.csr_ptr[row] = pos;
+      for (int col = 0; col < m; ++col) {
+        int e = (row == 0 || col == 0) ? s_index(row, col) : eidx[row - 1][col - 1];
+        if (e < 0) continue;
+        hm.csr_col.push_back(col);
+        hm.s_out[e] = pos++;
+      }
+    }
+    hm.csr_ptr[m] = pos;
+    if (pos != hm.nnz_S) { err = "internal error: pattern size mismatch"; return CHEM_EINVAL; }
+  }
+
+  // ---- gather programs
+  {
+    std::vector<std::vector<std::pair<int, int>>> gw(n), gd(hm.nY), gr(n), gc(n);
+    for (int r = 0; r < R; ++r)
+      for (auto& kv : netmap[r])
+        if (kv.second != 0) gw[kv.first].push_back({r, kv.second});
+    for (int r = 0; r < R; ++r) {
+      const int base = hm.rxi[(size_t)r * RX_I + 13];
+      for (auto& kv : netmap[r]) {
+        if (kv.second == 0) continue;
+        for (size_t c = 0; c < slots_sp[r].size(); ++c) {
+          int e = eidx[kv.first][slots_sp[r][c]];
+          gd[e].push_back({base + (int)c, kv.second});
+        }
+      }
+    }
+    for (int e = 0; e < hm.nY; ++e) {
+      gr[hm.entry_row[e]].push_back({e, hm.entry_col[e]});
+      gc[hm.entry_col[e]].push_back({e, hm.entry_row[e]});
+    }
+    if (!build_gather(gw, hm.g_omega, err) || !build_gather(gd, hm.g_dtil, err) || !build_gather(gr, hm.g_row, err) ||
+        !build_gather(gc, hm.g_col, err))
+      return CHEM_EUNSUPPORTED;
+  }
+
+  // ---- ordering (minimum degree, T last) and symbolic LU
+  std::vector<std::vector<char>> full(m, std::vector<char>(m, 0));
+  for (int row = 0; row < m; ++row)
+    for (int col = 0; col < m; ++col) {
+      bool in = (row == 0 || col == 0) ? true : Yp[row - 1][col - 1];
+      full[row][col] = in;
+    }
+  std::vector<std::vector<char>> sym(m, std::vector<char>(m, 0));
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b)
+      if (a != b && (full[a][b] || full[b][a])) sym[a][b] = 1;
+  hm.perm = min_degree_order(m, sym, 0);
+  hm.iperm.assign(m, 0);
+  for (int p = 0; p < m; ++p) hm.iperm[hm.perm[p]] = p;
+  std::vector<std::vector<char>> F(m, std::vector<char>(m, 0));
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q) F[p][q] = full[hm.perm[p]][hm.perm[q]];
+  for (int p = 0; p < m; ++p) F[p][p] = 1;
+  for (int k = 0; k < m; ++k)
+    for (int i = k + 1; i < m; ++i) {
+      if (!F[i][k]) continue;
+      for (int j = k + 1; j < m; ++j) if (F[k][j]) F[i][j] = 1;
+    }
+  std::vector<std::vector<int>> slot(m, std::vector<int>(m, -1));
+  hm.lu_rowptr.assign(m + 1, 0);
+  for (int p = 0; p < m; ++p) {
+    hm.lu_rowptr[p] = hm.nnz_LU;
+    for (int q = 0; q < m; ++q)
+      if (F[p][q]) { slot[p][q] = hm.nnz_LU++; hm.lu_col.push_back(q); }
+  }
+  hm.lu_rowptr[m] = hm.nnz_LU;
+  if (hm.nnz_LU > 0xFFFE) { err = "factor too large for 16-bit program indices"; return CHEM_EUNSUPPORTED; }
+  hm.lu_src.assign(hm.nnz_LU, -1);
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q)
+      if (slot[p][q] >= 0 && full[hm.perm[p]][hm.perm[q]]) hm.lu_src[slot[p][q]] = s_index(hm.perm[p], hm.perm[q]);
+  hm.lu_diag.assign(m, 0);
+  for (int s = 0; s < m; ++s) hm.lu_diag[s] = slot[hm.iperm[s]][hm.iperm[s]];
+
+  // ---- elimination program
+  {
+    std::vector<DagOp> ops;
+    std::vector<std::vector<int>> upd_to(hm.nnz_LU);   // UPDATE ops writing each slot
+    std::vector<int> recip(m), scale_of(hm.nnz_LU, -1);
+    for (int k = 0; k < m; ++k) {
+      recip[k] = (int)ops.size();
+      ops.push_back(DagOp{K_RECIP, 1 << 20 | k, ElimOp{(uint16_t)k, (uint16_t)slot[k][k], 0, 0}, {}});
+      for (int i = k + 1; i < m; ++i) {
+        if (slot[i][k] < 0) continue;
+        scale_of[slot[i][k]] = (int)ops.size();
+        ops.push_back(DagOp{K_SCALE, slot[i][k], ElimOp{(uint16_t)slot[i][k], (uint16_t)k, 0, 0}, {}});
+      }
+      for (int i = k + 1; i < m; ++i) {
+        if (slot[i][k] < 0) continue;
+        for (int j = k + 1; j < m; ++j) {
+          if (slot[k][j] < 0) continue;
+          int t = slot[i][j];
+          upd_to[t].push_back((int)ops.size());
+          ops.push_back(DagOp{K_UPDATE, t, ElimOp{(uint16_t)t, (uint16_t)slot[i][k], (uint16_t)slot[k][j], 0}, {}});
+          hm.lu_flops += 1;
+        }
+      }
+    }
+    // edges
+    for (int k = 0; k < m; ++k) {
+      for (int u : upd_to[slot[k][k]]) ops[u].succ.push_back(recip[k]);
+      for (int i = k + 1; i < m; ++i) {
+        if (slot[i][k] < 0) continue;
+        int sc = scale_of[slot[i][k]];
+        ops[recip[k]].succ.push_back(sc);
+        for (int u : upd_to[slot[i][k]]) ops[u].succ.push_back(sc);
+      }
+    }
+    for (size_t v = 0; v < ops.size(); ++v) {
+      if (ops[v].kind != K_UPDATE) continue;
+      int a = ops[v].enc.a, b = ops[v].enc.b;
+      ops[scale_of[a]].succ.push_back((int)v);
+      for (int u : upd_to[b]) ops[u].succ.push_back((int)v);
+    }
+    if (!schedule(ops, hm.lu_ops, hm.lu_kind, err)) return CHEM_EINVAL;
+  }
+  // ---- substitution program (forward with unit L, backward with U and 1/diag), state-order indices
+  {
+    std::vector<DagOp> ops;
+    std::vector<std::vector<int>> fw_w(m), fw_r(m), bw_w(m);
+    std::vector<int> sc(m);
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < p; ++q)
+        if (slot[p][q] >= 0) {
+          int id = (int)ops.size();
+          ops.push_back(DagOp{K_UPDATE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)slot[p][q], (uint16_t)hm.perm[q], 0}, {}});
+          fw_w[p].push_back(id);
+          fw_r[q].push_back(id);
+        }
+    for (int p = 0; p < m; ++p) {
+      sc[p] = (int)ops.size();
+      ops.push_back(DagOp{K_SCALE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)p, 0, 0}, {}});
+    }
+    std::vector<std::pair<int, int>> bw;   // (op id, q)
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q)
+        if (slot[p][q] >= 0) {
+          int id = (int)ops.size();
+          ops.push_back(DagOp{K_UPDATE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)slot[p][q], (uint16_t)hm.perm[q], 0}, {}});
+          bw_w[p].push_back(id);
+          bw.push_back({id, q});
+        }
+    for (int p = 0; p < m; ++p) {
+      for (int w : fw_w[p]) for (int r : fw_r[p]) ops[w].succ.push_back(r);     // RAW forward
+      for (int w : fw_w[p]) ops[w].succ.push_back(sc[p]);
+      for (int r : fw_r[p]) ops[r].succ.push_back(sc[p]);                       // WAR before scaling
+      for (int w : bw_w[p]) {
+        for (int f : fw_w[p]) ops[f].succ.push_back(w);                         // backward after forward
+        for (int r : fw_r[p]) ops[r].succ.push_back(w);                         // WAR
+        ops[w].succ.push_back(sc[p]);
+      }
+    }
+    for (auto& pr : bw) ops[sc[pr.second]].succ.push_back(pr.first);           // RAW backward
+    if (!schedule(ops, hm.sv_ops, hm.sv_kind, err)) return CHEM_EINVAL;
+  }
+  return CHEM_OK;
+}
+
+}  // namespace chemgb

@@ -1,0 +1,36 @@
+// compile.h -- host mechanism compiler: description -> tables and warp programs.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/chem.h"
+#include "mech.h"
+
+namespace chemgb {
+
+struct HostGather {
+  std::vector<GatherOp> ops;
+  int steps = 0;
+  int n_partial = 0;
+  std::vector<int> comb;   // triples
+};
+
+struct HostMech {
+  int n = 0, R = 0, m = 0, n_troe = 0, n_tb = 0, nY = 0, nnz_S = 0, nnz_LU = 0, n_dslot = 0;
+  std::vector<int> rx_order;           // compiled reaction index -> description index
+  std::vector<double> sp, rxd, eff_am1, dslot_am1, entry_wratio;
+  std::vector<int> rxi, eff_sp, dslot_sp, dslot_mask, entry_row, entry_col;
+  HostGather g_omega, g_dtil, g_row, g_col;
+  std::vector<int> perm, iperm;        // LU position -> state index, and back
+  std::vector<int> lu_src, lu_diag, s_out;
+  std::vector<int> lu_rowptr, lu_col;  // factor pattern, CSR in LU (permuted) order
+  std::vector<ElimOp> lu_ops, sv_ops;
+  std::vector<uint8_t> lu_kind, sv_kind;
+  std::vector<int> csr_ptr, csr_col;   // S pattern in natural state order
+  long long lu_flops = 0;              // multiply-adds of one factorisation (algorithmic)
+};
+
+// Validates and compiles; returns CHEM_OK or an error code with a message in err.
+chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string& err);
+
+}  // namespace chemgb

@@ -1,0 +1,111 @@
+// mech.h -- layout of a compiled mechanism, shared by the host compiler and the device kernels.
+//
+// All tables live in one device allocation; MechView carries typed pointers into it and is passed to
+// kernels by value.  Index fields of the warp programs are 16 bits wide, which bounds reactions,
+// derivative slots and factor entries to 65535 (chem_create reports CHEM_EUNSUPPORTED beyond).
+#pragma once
+#include <cstdint>
+
+namespace chemgb {
+
+constexpr double kRu = 8.314462618;   // J/(mol K)
+constexpr double kP0 = 101325.0;      // Pa, standard state of Kc
+constexpr int kWarp = 32;
+
+// ---- species table: SP_STRIDE doubles per species
+//   [0] 1/W  [1] W  [2] T_mid  [3] unused
+//   [4 .. 4+RANGE)   low range, [4+RANGE .. 4+2 RANGE) high range, each:
+//   a0 a1 a2 a3 a4 | h1..h4 = a1/2 a2/3 a3/4 a4/5 | g1..g4 = -a1/2 -a2/6 -a3/12 -a4/20 | a5 a6 |
+//   d2 d3 d4 = 2a2 3a3 4a4
+// so cp/R = a0 + T(a1 + T(a2 + T(a3 + T a4))), h/RT = a0 + T(h1 + ...) + a5/T,
+// g = h/RT - s/R = a0 (1 - ln T) + T(g1 + T(g2 + T(g3 + T g4))) + a5/T - a6,
+// d(cp/R)/dT = a1 + T(d2 + T(d3 + T d4)).
+constexpr int SP_RANGE = 18;
+constexpr int SP_STRIDE = 4 + 2 * SP_RANGE;
+
+// ---- reaction tables (reactions ordered: Troe, then third-body, then elementary)
+// doubles, RX_D per reaction:
+//   [0] ln A  [1] b  [2] Ea/Ru  [3] ln A0  [4] b0  [5] Ea0/Ru  [6] 1-alpha  [7] alpha  [8] 1/T3  [9] 1/T1
+//   [10] T2 (0: absent)  [11] unused
+constexpr int RX_D = 12;
+// ints, RX_I per reaction:
+//   [0] type (0 elementary, 1 third-body, 2 Troe)  [1] reversible  [2] reactant occurrences (1..3)
+//   [3] product occurrences (1..3)  [4..6] reactant species per occurrence (coefficient nu expands into
+//   nu occurrences)  [7..9] product occurrences  [10] sum of net coefficients  [11] efficiency offset
+//   [12] efficiency count  [13] derivative-slot offset  [14] derivative-slot count  [15] unused
+constexpr int RX_I = 16;
+
+// ---- warp programs
+// Gather ("flattened segmented reduction"): step s, lane l executes op[s*32 + l]:
+//   acc = fma(value(a, b), acc); if dst != NONE: out[dst] = acc, acc = 0.
+// dst >= PARTIAL_BIT selects the partial-sum buffer; a combine list then adds partials into outputs.
+struct GatherOp {
+  uint16_t a, b, dst, flags;   // flags bit 0: padding (no accumulation)
+};
+constexpr uint16_t DST_NONE = 0xFFFF;
+constexpr uint16_t PARTIAL_BIT = 0x8000;
+
+// Elimination / solve program: step s has one kind; lane l executes op[s*32 + l] (t == OP_IDLE: idle).
+//   LU:    K_RECIP  dinv[t] = 1 / LU[a]      K_SCALE  LU[t] *= dinv[a]     K_UPDATE LU[t] -= LU[a] * LU[b]
+//   solve: K_SCALE  x[t] *= dinv[a]          K_UPDATE x[t] -= LU[a] * x[b]
+struct ElimOp {
+  uint16_t t, a, b, pad;
+};
+constexpr uint16_t OP_IDLE = 0xFFFF;
+enum : int { K_RECIP = 0, K_SCALE = 1, K_UPDATE = 2 };
+
+struct Gather {
+  const GatherOp* ops;   // [steps * 32]
+  int steps;
+  int n_partial;
+  const int* comb;       // [n_comb * 3]: dst, first partial, count
+  int n_comb;
+};
+
+struct MechView {
+  int n, R, m;
+  int n_troe, n_tb;          // reactions [0, n_troe) Troe, [n_troe, n_troe + n_tb) third-body
+  int nY;                    // Y-block entries of S (row-major by species, diagonal included)
+  int nnz_S;                 // nY + n (T column) + m (T row)
+  int nnz_LU;
+  int n_dslot;
+  const double* sp;          // [n * SP_STRIDE]
+  const double* rxd;         // [R * RX_D]
+  const int* rxi;            // [R * RX_I]
+  const int* eff_sp;         // listed efficiencies
+  const double* eff_am1;     // alpha - 1
+  const int* dslot_sp;       // [n_dslot] column species of each derivative slot
+  const int* dslot_mask;     // [n_dslot] bits 0..2 reactant occurrences, 3..5 product occurrences equal
+  const double* dslot_am1;   // [n_dslot] (efficiency - 1) of the slot species, 0 if not listed
+  const int* entry_row;      // [nY] species k of Y-block entry
+  const int* entry_col;      // [nY] species j
+  const double* entry_wratio;// [nY] W_k / W_j
+  Gather g_omega;            // species <- reactions (a = reaction, b = nu as int16)
+  Gather g_dtil;             // Y entries <- derivative slots (a = slot, b = nu)
+  Gather g_row;              // species k <- sum_j Dtil_kj C_j (a = entry, b = species j)
+  Gather g_col;              // species i <- sum_k h_k Dtil_ki (a = entry, b = species k)
+  const int* lu_src;         // [nnz_LU] S index feeding the slot (-1: fill)
+  const int* lu_diag;        // [m] LU slot of the diagonal of state index s (natural order)
+  const ElimOp* lu_ops;      // [lu_steps * 32]
+  const uint8_t* lu_kind;    // [lu_steps]
+  int lu_steps;
+  const ElimOp* sv_ops;      // forward + backward substitution program, vector indices in state order
+  const uint8_t* sv_kind;
+  int sv_steps;
+  const int* s_out;          // [nnz_S] position of internal S entry in the CSR output order
+};
+
+// Per-cell shared-memory layout (offsets in doubles).
+struct CellLayout {
+  int y, ytmp, f0, U1, U2, U3, U4, x, z, u, v;   // m-vectors
+  int C, hRT, eg, emg, cpR;                       // n-vectors
+  int q, dqdT;                                    // R-vectors
+  int S;                                          // nnz_S
+  int LU, dinv;                                   // nnz_LU, m (aliases the derivative slots)
+  int D;                                          // n_dslot
+  int part;                                       // partial sums of the gathers
+  int misc;                                       // 16 scalars
+  int total;                                      // doubles per cell
+};
+
+}  // namespace chemgb

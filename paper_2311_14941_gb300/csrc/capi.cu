@@ -40,9 +40,20 @@ struct chem_handle_s {
   int smem_optin = 0;
   int num_sms = 0;
   bool attr_set = false;
-  // scratch of the persistent mode (grows on demand)
+  // scratch of the sorted work queue and the time-budget stamp (grows on demand)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  int occ_blocks_per_sm[2] = {0, 0};   // persistent kernel occupancy per block size choice (cached)
+  // CUDA graph of the persistent sequence, re-captured when its arguments change
+  struct GraphKey {
+    int N, mode, wpb, chunk;
+    const void* ptr[10];
+    double d[5];
+    int i[3];
+    bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+  } gkey{};
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -85,6 +96,9 @@ size_t put(std::vector<char>& buf, const std::vector<T>& v) {
 
 // =============================================================================================== kernels
 namespace chemgb {
+
+__device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long long* stamp,
+                                                 unsigned long long budget_ns);
 
 // Load one cell's state into y (lanes over state components).
 __device__ __forceinline__ void load_state(double* y, int m, int N, int c, const double* T, const double* Y, int lane) {
@@ -148,7 +162,7 @@ __global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __rest
 __global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __restrict__ T, const double* __restrict__ p,
                                   double* __restrict__ Y, const double* __restrict__ dt, double* __restrict__ h_io,
                                   int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
-                                  IntOpts o) {
+                                  IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
   extern __shared__ double smem[];
   const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const int c0 = blockIdx.x * wpb;
@@ -158,7 +172,7 @@ __global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __res
   if (c >= N) return;
   double h = h_io[c];
   int ns = 0, na = 0, st = 0;
-  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, o, lane, c);
+  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, with_deadline(o, stamp, budget_ns), lane, c);
   const double* y = s + L.y;
   for (int i = lane; i < M.m; i += kWarp) {
     if (i == 0) T[c] = y[0];
@@ -169,6 +183,93 @@ __global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __res
     nsub[c] = ns;
     status[c] = st;
     if (nacc_out) nacc_out[c] = na;
+  }
+}
+
+// ---- sorted work queue (the on-chip form of the paper's dynamic load balancing)
+constexpr int kBuckets = 32;
+
+// Scratch layout (bytes): [0, 128) bucket counts, [128, 256) bucket cursors, [256, 260) queue head,
+// [264, 272) start stamp (ns), [512, 512 + 4N) permutation.
+constexpr size_t kScrCounts = 0, kScrCursor = 128, kScrHead = 256, kScrStamp = 264, kScrPerm = 512;
+
+__device__ __forceinline__ int cost_bucket(int ns) { return ns <= 1 ? 0 : min(kBuckets - 1, 31 - __clz(ns)); }
+
+__global__ void k_stamp(unsigned long long* stamp) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *stamp = global_ns();
+}
+
+__global__ void k_sort_count(int N, const int* __restrict__ nsub_prev, int* __restrict__ counts) {
+  __shared__ int sh[kBuckets];
+  for (int t = threadIdx.x; t < kBuckets; t += blockDim.x) sh[t] = 0;
+  __syncthreads();
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+    atomicAdd(&sh[cost_bucket(nsub_prev[c])], 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < kBuckets; t += blockDim.x)
+    if (sh[t]) atomicAdd(&counts[t], sh[t]);
+}
+
+// Costliest bucket first (largest previous substep count): long cells start early, cheap cells fill
+// the tail.
+__global__ void k_sort_scatter(int N, const int* __restrict__ nsub_prev, const int* __restrict__ counts,
+                               int* __restrict__ cursor, int* __restrict__ perm) {
+  __shared__ int off[kBuckets];
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = kBuckets - 1; b >= 0; --b) { off[b] = acc; acc += counts[b]; }
+  }
+  __syncthreads();
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    const int b = cost_bucket(nsub_prev[c]);
+    perm[off[b] + atomicAdd(&cursor[b], 1)] = c;
+  }
+}
+
+__device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long long* stamp,
+                                                 unsigned long long budget_ns) {
+  if (budget_ns && stamp) o.deadline_ns = *stamp + budget_ns;
+  return o;
+}
+
+// Persistent form: grid sized to the resident capacity; every warp pulls `chunk` cells at a time from
+// the sorted queue with one atomicAdd and integrates them one after the other.  No block-wide barrier:
+// warps of a block finish independently.
+__global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* __restrict__ T,
+                                       const double* __restrict__ p, double* __restrict__ Y,
+                                       const double* __restrict__ dt, double* __restrict__ h_io,
+                                       int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
+                                       const int* __restrict__ perm, int* __restrict__ head, int chunk, IntOpts o,
+                                       const unsigned long long* stamp, unsigned long long budget_ns) {
+  extern __shared__ double smem[];
+  const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  double* s = smem + (size_t)w * L.total;
+  const IntOpts oo = with_deadline(o, stamp, budget_ns);
+  while (true) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(head, chunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= N) break;
+    const int end = min(base + chunk, N);
+    for (int j = base; j < end; ++j) {
+      const int c = perm[j];
+      load_state(s + L.y, M.m, N, c, T, Y, lane);
+      double h = h_io[c];
+      int ns = 0, na = 0, st = 0;
+      integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, oo, lane, c);
+      const double* y = s + L.y;
+      for (int i = lane; i < M.m; i += kWarp) {
+        if (i == 0) T[c] = y[0];
+        else Y[(size_t)(i - 1) * N + c] = y[i];
+      }
+      if (lane == 0) {
+        h_io[c] = h;
+        nsub[c] = ns;
+        status[c] = st;
+        if (nacc_out) nacc_out[c] = na;
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -191,7 +292,9 @@ chem_status set_attrs(chem_handle h) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+      (e = cudaFuncSetAttribute(k_integrate_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_integrate_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+          cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute");
   h->attr_set = true;
   return CHEM_OK;
@@ -201,6 +304,22 @@ int warps_per_block(const chem_handle h, int requested) {
   int wpb = requested > 0 ? requested : 1;
   while (wpb > 1 && wpb * h->cell_bytes > h->smem_optin) --wpb;
   return wpb;
+}
+
+chem_status ensure_scratch(chem_handle h, int N) {
+  const size_t need = kScrPerm + (size_t)std::max(N, 1) * sizeof(int);
+  if (h->scratch_bytes >= need) return CHEM_OK;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  if (h->scratch) cudaFree(h->scratch);
+  h->scratch = nullptr;
+  h->scratch_bytes = 0;
+  const size_t bytes = std::max(need, need + need / 4);
+  if (cudaMalloc(&h->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CHEM_ENOMEM, "cudaMalloc of integrator scratch failed");
+  }
+  h->scratch_bytes = bytes;
+  return CHEM_OK;
 }
 
 chem_status launch_check(const char* what) {
@@ -300,6 +419,8 @@ chem_status chem_destroy(chem_handle h) {
   if (!h) return CHEM_OK;
   if (h->device < 0) { delete h; return CHEM_OK; }
   cudaSetDevice(h->device);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->blob) cudaFree(h->blob);
   if (h->scratch) cudaFree(h->scratch);
   delete h;
@@ -403,12 +524,72 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
     return fail(CHEM_EINVAL, "non-finite option");
-  if (o.mode != 0) return fail(CHEM_EUNSUPPORTED, "only mode 0 (plain) is available in this build");
+  if (o.mode != 0 && o.mode != 1) return fail(CHEM_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
+  if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
-  if (o.time_budget_s > 0.0) return fail(CHEM_EUNSUPPORTED, "time_budget_s is not available in this build");
+  const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
+  cudaStream_t strm = (cudaStream_t)stream;
+  cudaError_t e;
+  if (o.mode == 0) {
+    const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
+    unsigned long long* stamp = nullptr;
+    if (budget_ns) {
+      if ((st = ensure_scratch(h, 1)) != CHEM_OK) return st;
+      stamp = (unsigned long long*)((char*)h->scratch + kScrStamp);
+      k_stamp<<<1, 32, 0, strm>>>(stamp);
+    }
+    k_integrate_plain<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, strm>>>(
+        h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns);
+    return launch_check("chem_integrate launch");
+  }
+  // persistent mode: sort by previous cost, then one resident grid pulling from the queue; the whole
+  // sequence is one CUDA graph, captured once per argument set and replayed on `stream`
+  if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
   const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
-  k_integrate_plain<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(
-      h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, io);
+  const int chunk = o.chunk > 0 ? o.chunk : 1;
+  chem_handle_s::GraphKey key{};
+  key.N = N; key.mode = 1; key.wpb = wpb; key.chunk = chunk;
+  const void* ptrs[10] = {T, p, Y, dt, h_io, nsub, status, o.naccept, o.trace, h->scratch};
+  for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
+  key.d[0] = io.rtol; key.d[1] = io.atol; key.d[2] = io.h_init; key.d[3] = io.h_min; key.d[4] = o.time_budget_s;
+  key.i[0] = io.max_substeps; key.i[1] = io.max_nonfinite; key.i[2] = io.trace_cap;
+  if (!h->gexec || !(h->gkey == key)) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamCreate");
+    int bps = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_integrate_persistent, wpb * kWarp,
+                                                           (size_t)wpb * h->cell_bytes)) != cudaSuccess)
+      return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    bps = std::max(bps, 1);
+    const int grid = std::min(h->num_sms * bps, (N + wpb - 1) / wpb);
+    char* scr = (char*)h->scratch;
+    int* counts = (int*)(scr + kScrCounts);
+    int* cursor = (int*)(scr + kScrCursor);
+    int* head = (int*)(scr + kScrHead);
+    unsigned long long* stamp = (unsigned long long*)(scr + kScrStamp);
+    int* perm = (int*)(scr + kScrPerm);
+    const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
+    cudaStream_t cs = h->cap_stream;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaMemsetAsync(scr, 0, kScrHead + 4, cs);
+    k_stamp<<<1, 32, 0, cs>>>(stamp);
+    k_sort_count<<<sblocks, 256, 0, cs>>>(N, nsub, counts);
+    k_sort_scatter<<<sblocks, 256, 0, cs>>>(N, nsub, counts, cursor, perm);
+    k_integrate_persistent<<<grid, wpb * kWarp, wpb * h->cell_bytes, cs>>>(
+        h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+    cudaGraph_t graph = nullptr;
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(le, "persistent launch capture"); }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    h->gkey = key;
+  }
+  if ((e = cudaGraphLaunch(h->gexec, strm)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   return launch_check("chem_integrate launch");
 }
 

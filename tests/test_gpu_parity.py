@@ -144,13 +144,16 @@ def _compare_integration(o, g, r, F, max_flip_frac):
     balances).  Cells whose sequence differs (a decision at err ~ 1 flipped by rounding): within
     10 rtol relative (10 atol absolute)."""
     assert np.array_equal(g["status"], r["status"]), (g["status"], r["status"])
-    sg, so = np.sign(g["trace"]), np.sign(r["trace"])
-    same = np.all(sg == so, axis=0)
+    # Same sequence: identical accept/reject decisions and step sizes equal up to the rounding of the
+    # error estimate (the last, clipped step dt - t inherits the rounding of t: dt-relative term).
+    # Anything else -- a flipped decision, or a rejection taken through the non-finite branch (h/10)
+    # on one side and the error branch (h/5) on the other -- is a different sequence.
+    hr = np.abs(r["trace"])
+    hdiff = np.abs(np.abs(g["trace"]) - hr) / (hr + 1e-9 * F.dt[None, :])
+    same = np.all(np.sign(g["trace"]) == np.sign(r["trace"]), axis=0) & np.all(hdiff <= 1e-4, axis=0)
     flips = np.where(~same)[0]
     assert len(flips) <= max(1, int(max_flip_frac * F.n_cells)), (len(flips), F.n_cells)
-    # same decisions -> the step sizes agree to rounding
-    hr = np.abs(r["trace"][:, same])
-    assert np.all(np.abs(np.abs(g["trace"][:, same]) - hr) <= 1e-8 * hr)
+    hdiff = hdiff[:, same]
     yg = np.vstack([g["T"][None, :], g["Y"]])
     yr = np.vstack([r["T"][None, :], r["Y"]])
     big = np.abs(yr) > 1e-12
@@ -168,7 +171,8 @@ def _compare_integration(o, g, r, F, max_flip_frac):
     worst = rel[:, same & np.all(ok, axis=0)].max(initial=0.0)
     for c in flips:
         assert np.all(d[:, c] <= 10 * 1e-6 * np.abs(yr[:, c]) + 10 * 1e-12), c
-    print(f"cells {F.n_cells}: same sequence {int(same.sum())}, flips {len(flips)}, "
+    print(f"cells {F.n_cells}: same sequence {int(same.sum())} (max step-size drift {hdiff.max():.1e}), "
+          f"flips {len(flips)}, "
           f"within 1e-8 everywhere {int((same & np.all(ok, axis=0)).sum())} (worst {worst:.2e}), "
           f"at the rounding floor {floor_cells}")
     return len(flips)

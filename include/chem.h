@@ -172,6 +172,30 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
                            double* h_io, int* nsub, int* status, const chem_integrate_opts* opts,
                            chem_stream stream);
 
+/* chem_integrate without any device allocation.  (The paper has no counterpart: this is a calling
+   convenience of this library.)
+   Some callers cannot allocate device memory at the point where they integrate chemistry: a CFD code
+   whose memory pool has taken the device's memory at start-up, a time loop that must not pay the
+   implicit device synchronisation cudaMalloc/cudaFree can cause, or a plug-in that may not grow its
+   footprint after initialisation.  This entry point runs the same sorted work-queue integration as
+   chem_integrate with mode 1 (results are identical) but takes its scratch (sort counters, queue
+   head, time stamp, the cell permutation) from a fixed array in the library's static device memory
+   instead of handle-owned memory, and calls no allocating routine.  The handle itself must already
+   exist (chem_create allocates the mechanism tables once).
+   Limits and rules:
+   - at most 1,048,576 cells per call (larger N returns CHEM_EINVAL before anything is launched); the
+     array takes 4 MiB + 512 bytes on every GPU that loads the library, until the process exits;
+   - the first call on a device looks up the array's device address (once per device, with that
+     device current) -- make that first call before any stream capture;
+   - all calls share the one array and each call clears its counters first: calls whose GPU work
+     overlaps (different streams, or different host threads without ordering) race and must not be
+     issued; put them on one stream or synchronise between them;
+   - opts as for chem_integrate; opts.mode is ignored (always the sorted work queue).
+   Arguments, layouts and per-cell status as for chem_integrate. */
+chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
+                                   double* h_io, int* nsub, int* status, const chem_integrate_opts* opts,
+                                   chem_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

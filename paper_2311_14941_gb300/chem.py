@@ -74,8 +74,10 @@ def lib():
         L.chem_rates.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.chem_jacobian.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.chem_integrate.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(OptsC), _vp]
+        L.chem_integrate_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(OptsC),
+                                             _vp]
         for f in ("chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
-                  "chem_rates", "chem_jacobian", "chem_integrate"):
+                  "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -205,6 +207,24 @@ class Mechanism:
                                     _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
                                     _dptr(status, torch.int32, N, "status"), C.byref(o), _stream(stream)),
                "chem_integrate")
+
+
+    def integrate_noalloc(self, T, p, Y, dt, h_io, nsub, status, rtol=1e-6, atol=1e-12, h_init=0.0, h_min=0.0,
+                          time_budget_s=0.0, max_substeps=0, max_nonfinite=0, block_warps=0, chunk=0, naccept=None,
+                          trace=None, stream=None):
+        """chem_integrate_noalloc: the sorted work-queue integration with its scratch in the library's
+        static device memory (no allocation in the call; at most 1,048,576 cells; calls must not overlap
+        on the GPU).  In-place like ``integrate``."""
+        import torch
+        N = T.numel()
+        cap = trace.numel() // max(N, 1) if trace is not None else 0
+        o = OptsC(rtol, atol, h_init, h_min, time_budget_s, max_substeps, max_nonfinite, 1, block_warps, chunk,
+                  _dptr(naccept, torch.int32, N, "naccept"), _dptr(trace, torch.float64, cap * N, "trace"), cap)
+        _check(lib().chem_integrate_noalloc(
+            self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
+            _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
+            _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
+            _dptr(status, torch.int32, N, "status"), C.byref(o), _stream(stream)), "chem_integrate_noalloc")
 
 
 def create(desc, device: int = 0) -> Mechanism:

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -192,6 +193,12 @@ constexpr int kBuckets = 32;
 // Scratch layout (bytes): [0, 128) bucket counts, [128, 256) bucket cursors, [256, 260) queue head,
 // [264, 272) start stamp (ns), [512, 512 + 4N) permutation.
 constexpr size_t kScrCounts = 0, kScrCursor = 128, kScrHead = 256, kScrStamp = 264, kScrPerm = 512;
+
+// Scratch for chem_integrate_noalloc: a fixed array in the module's static device memory, so that
+// entry point never allocates.  Same layout as the handle scratch; room for kNoAllocMaxCells cells.
+constexpr int kNoAllocMaxCells = 1 << 20;
+constexpr size_t kNoAllocBytes = kScrPerm + (size_t)kNoAllocMaxCells * sizeof(int);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 __device__ __forceinline__ int cost_bucket(int ns) { return ns <= 1 ? 0 : min(kBuckets - 1, 31 - __clz(ns)); }
 
@@ -594,3 +601,81 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
 }
 
 }  // extern "C"
+
+// Device address of the static scratch array on the current device.  In host code the array's name
+// only stands for it; the real address is looked up once per device and kept.
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+chem_status noalloc_scratch_address(int device, char** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (device < 0 || device >= kNoAllocMaxDevices) return fail(CHEM_EUNSUPPORTED, "device index too large");
+  if (!g_noalloc_addr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    g_noalloc_addr[device] = ptr;
+  }
+  *out = (char*)g_noalloc_addr[device];
+  return CHEM_OK;
+}
+}  // namespace
+
+extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double* p, double* Y,
+                                              const double* dt, double* h_io, int* nsub, int* status,
+                                              const chem_integrate_opts* opts, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N > kNoAllocMaxCells)
+    return fail(CHEM_EINVAL, "chem_integrate_noalloc handles at most " + std::to_string(kNoAllocMaxCells) +
+                                 " cells per call (fixed static scratch); got " + std::to_string(N));
+  if (N == 0) return CHEM_OK;
+  if (!T || !p || !Y || !dt || !h_io || !nsub || !status) return fail(CHEM_EINVAL, "null array argument");
+  chem_integrate_opts o{};
+  if (opts) o = *opts;
+  IntOpts io;
+  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
+  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
+  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
+  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
+  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
+  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
+  io.deadline_ns = 0;
+  io.trace = o.trace;
+  io.trace_cap = o.trace ? o.trace_cap : 0;
+  io.N = N;
+  if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
+  if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
+    return fail(CHEM_EINVAL, "non-finite option");
+  if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  char* scr = nullptr;
+  if ((st = noalloc_scratch_address(h->device, &scr)) != CHEM_OK) return st;
+  const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
+  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
+  const int chunk = o.chunk > 0 ? o.chunk : 1;
+  int bps = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_integrate_persistent, wpb * kWarp,
+                                                                (size_t)wpb * h->cell_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  bps = std::max(bps, 1);
+  const int grid = std::min(h->num_sms * bps, (N + wpb - 1) / wpb);
+  const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
+  int* counts = (int*)(scr + kScrCounts);
+  int* cursor = (int*)(scr + kScrCursor);
+  int* head = (int*)(scr + kScrHead);
+  unsigned long long* stamp = (unsigned long long*)(scr + kScrStamp);
+  int* perm = (int*)(scr + kScrPerm);
+  cudaStream_t strm = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear the counters and the queue head first
+  if ((e = cudaMemsetAsync(scr, 0, kScrHead + 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  k_stamp<<<1, 32, 0, strm>>>(stamp);
+  k_sort_count<<<sblocks, 256, 0, strm>>>(N, nsub, counts);
+  k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, nsub, counts, cursor, perm);
+  k_integrate_persistent<<<grid, wpb * kWarp, wpb * h->cell_bytes, strm>>>(
+      h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+  return launch_check("chem_integrate_noalloc launch");
+}

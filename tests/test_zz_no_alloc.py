@@ -1,0 +1,87 @@
+"""chem_integrate_noalloc: integration for callers that cannot allocate device memory when they call in.
+
+Such callers are, for example, a CFD code whose memory pool took the device's memory at start-up, or
+a time loop that must not pay the implicit device synchronisation of cudaMalloc/cudaFree.  The entry
+point keeps its scratch in a fixed array of the library's static device memory.  It runs the same
+per-cell code and sorted work queue as chem_integrate in persistent mode, so its results must equal
+that entry point's bit for bit -- on a first call and on a second call that finds the previous call's
+data still in the shared array.
+
+Collected last on purpose (file name), so a run that stops at the first failure has run everything
+else before it; it also passes alone in a fresh process.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2311_14941_gb300 import chem, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _buffers(F, dev, nsub_in):
+    N = F.n_cells
+    return dict(T=torch.tensor(F.T, device=dev), p=torch.tensor(F.p, device=dev),
+                Y=torch.tensor(F.Y.reshape(-1), device=dev), dt=torch.tensor(F.dt, device=dev),
+                h_io=torch.zeros(N, dtype=torch.float64, device=dev),
+                nsub=torch.tensor(nsub_in, dtype=torch.int32, device=dev),
+                status=torch.zeros(N, dtype=torch.int32, device=dev),
+                naccept=torch.zeros(N, dtype=torch.int32, device=dev))
+
+
+def _call(h, F, dev, nsub_in, noalloc):
+    b = _buffers(F, dev, nsub_in)
+    fn = h.integrate_noalloc if noalloc else (lambda *a, **k: h.integrate(*a, mode=1, **k))
+    fn(b["T"], b["p"], b["Y"], b["dt"], b["h_io"], b["nsub"], b["status"], naccept=b["naccept"])
+    torch.cuda.synchronize()
+    return {k: b[k].cpu().numpy() for k in ("T", "Y", "h_io", "nsub", "status", "naccept")}
+
+
+def test_noalloc_matches_persistent_entry_point_on_two_calls(dev):
+    m = synth.mechanism_methane_sized()
+    h = chem.create(m, 0)
+    F = synth.field_lts_mix(m, 2500, seed=17, dt_range=(1e-7, 1e-4))
+    zeros = np.zeros(F.n_cells, dtype=np.int32)
+    ref1 = _call(h, F, dev, zeros, noalloc=False)
+    ref2 = _call(h, F, dev, ref1["nsub"], noalloc=False)       # second flow step: sorted by the counts
+    got1 = _call(h, F, dev, zeros, noalloc=True)
+    got2 = _call(h, F, dev, got1["nsub"], noalloc=True)        # the static array still holds call 1's data
+    for ref, got in ((ref1, got1), (ref2, got2)):
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+    assert np.all(got2["status"] == 0)
+    assert len(np.unique(ref1["nsub"])) > 5
+
+
+def test_noalloc_takes_no_device_memory_per_call(dev):
+    m = synth.mechanism_small()
+    h = chem.create(m, 0)
+    F = synth.field_uniform_random(m, 512, seed=3)
+    zeros = np.zeros(F.n_cells, dtype=np.int32)
+    b = _buffers(F, dev, zeros)
+    args = (b["T"], b["p"], b["Y"], b["dt"], b["h_io"], b["nsub"], b["status"])
+    h.integrate_noalloc(*args)                  # first call on the device: address look-up, module load
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        h.integrate_noalloc(*args)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+
+
+def test_noalloc_rejects_batches_above_its_limit(dev):
+    m = synth.mechanism_small()
+    h = chem.create(m, 0)
+    N = (1 << 20) + 1
+    z = lambda n, dt=torch.float64: torch.zeros(n, dtype=dt, device=dev)
+    with pytest.raises(chem.ChemError) as ei:
+        h.integrate_noalloc(z(N), z(N), z(N * m.n_species), z(N), z(N), z(N, torch.int32), z(N, torch.int32))
+    assert "1048576" in str(ei.value) and "status 1" in str(ei.value)

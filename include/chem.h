@@ -51,7 +51,10 @@ enum {
   CHEM_CELL_HMIN = 2,      /* step size fell below h_min */
   CHEM_CELL_NONFINITE = 3, /* max_nonfinite consecutive attempts produced non-finite values */
   CHEM_CELL_BADINPUT = 4,  /* T <= 0, p <= 0, dt < 0, non-finite input, or sum(Y/W) <= 0 */
-  CHEM_CELL_TIMEOUT = 5    /* the call's time budget ran out before this cell finished */
+  CHEM_CELL_TIMEOUT = 5,   /* the call's time budget ran out before this cell finished */
+  CHEM_CELL_NOTAPE = 6     /* chem_adjoint: the forward pass took more accepted steps than the tape holds;
+                              the cell's gradients are reported as zero (as for a failed forward pass,
+                              which keeps its own status) */
 };
 
 /* Mechanism description (host memory, copied by chem_create; the caller keeps ownership).
@@ -121,6 +124,8 @@ typedef struct {
   double* trace;          /* optional DEVICE array [trace_cap*N]: attempt i of cell c at trace[i*N + c],
                              +h if accepted, -h if rejected, 0 after the last attempt (NULL: off) */
   int trace_cap;          /* attempts recorded per cell */
+  int ckpt_every;         /* chem_adjoint: accepted steps between checkpoints (default 16, at most 64) */
+  int tape_steps;         /* chem_adjoint: accepted steps the tape holds per cell (default 4096) */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,
@@ -147,7 +152,9 @@ chem_status chem_jacobian_pattern(chem_handle h, int* row_ptr, int* col_idx);
      2 ordering: perm[p] = state index at factor position p (m ints);
      3 factor pattern: row_ptr (m+1) then col (nnz_LU), factor positions;
      4 factor slot sources: S entry (internal order) feeding each factor slot, -1 for fill (nnz_LU);
-     5 internal S entry -> CSR position of chem_jacobian_pattern (nnz_S).
+     5 internal S entry -> CSR position of chem_jacobian_pattern (nnz_S);
+     6 transposed substitution program (A^T x = b), same encoding as 1;
+     7 compiled reaction order: description index of each compiled reaction (R).
    With out == NULL only *count is written.  *count: number of ints. */
 chem_status chem_export_plan(chem_handle h, int which, int* out, int* count);
 
@@ -171,6 +178,29 @@ chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p
 chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
                            double* h_io, int* nsub, int* status, const chem_integrate_opts* opts,
                            chem_stream stream);
+
+/* Shift the Arrhenius parameters of every reaction relative to the description given to chem_create:
+   ln A_j -> ln A_j + dlnA[j], Ea_j -> Ea_j + dEa[j] (DEVICE arrays [R] in description order, either may
+   be NULL for zero).  For Troe reactions both limits shift together (the fall-off shape is unchanged and
+   k_f, k_r scale exactly by exp(dlnA) exp(-dEa/(Ru T))).  Stream-ordered; later calls see the new
+   parameters.  Calling it with two NULLs restores the description's values. */
+chem_status chem_set_params(chem_handle h, const double* dlnA, const double* dEa, chem_stream stream);
+
+/* Discrete adjoint of chem_integrate (the paper computes no sensitivities; this is the standard discrete
+   adjoint of the Rosenbrock steps).  With the accepted step sizes of the forward integration frozen,
+   for the objective L = sum_c (gT[c] T_c(dt) +
+   sum_k gY[k*N+c] Y_k,c(dt)) it returns
+     grad_lnA [R], grad_Ea [R] (DEVICE, description order, summed over cells; J/mol units for Ea),
+     grad_cell [2R*N] (nullable; entry j*N + c for ln A_j, (R + j)*N + c for Ea_j, per cell),
+     gT0 [N], gY0 [n*N] (nullable; dL/d initial T and Y).
+   T [N] and Y [n*N] are the initial state in and the final state out, as in chem_integrate (same
+   results).  The forward pass records the accepted step sizes and a checkpoint every
+   opts->ckpt_every accepted steps (tape of opts->tape_steps accepted steps per cell, handle scratch);
+   the reverse pass recomputes each segment from its checkpoint.  status [N] as chem_integrate, plus
+   CHEM_CELL_NOTAPE.  opts: tolerances and limits as for chem_integrate (mode is ignored). */
+chem_status chem_adjoint(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
+                         const double* gT, const double* gY, double* grad_lnA, double* grad_Ea, double* grad_cell,
+                         double* gT0, double* gY0, int* status, const chem_integrate_opts* opts, chem_stream stream);
 
 /* chem_integrate without any device allocation.  (The paper has no counterpart: this is a calling
    convenience of this library.)

@@ -44,7 +44,7 @@ class OptsC(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h_init", C.c_double), ("h_min", C.c_double),
                 ("time_budget_s", C.c_double), ("max_substeps", C.c_int), ("max_nonfinite", C.c_int),
                 ("mode", C.c_int), ("block_warps", C.c_int), ("chunk", C.c_int), ("naccept", _vp),
-                ("trace", _vp), ("trace_cap", C.c_int)]
+                ("trace", _vp), ("trace_cap", C.c_int), ("ckpt_every", C.c_int), ("tape_steps", C.c_int)]
 
 
 CELL_STATUS = {0: "OK", 1: "MAXSTEPS", 2: "HMIN", 3: "NONFINITE", 4: "BADINPUT", 5: "TIMEOUT"}
@@ -76,8 +76,12 @@ def lib():
         L.chem_integrate.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(OptsC), _vp]
         L.chem_integrate_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(OptsC),
                                              _vp]
+        L.chem_set_params.argtypes = [_vp, _vp, _vp, _vp]
+        L.chem_adjoint.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   C.POINTER(OptsC), _vp]
         for f in ("chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
-                  "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc"):
+                  "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc", "chem_set_params",
+                  "chem_adjoint"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -208,6 +212,29 @@ class Mechanism:
                                     _dptr(status, torch.int32, N, "status"), C.byref(o), _stream(stream)),
                "chem_integrate")
 
+
+    def set_params(self, dlnA=None, dEa=None, stream=None):
+        """chem_set_params: shift ln A and Ea of every reaction (device tensors [R], description order)."""
+        import torch
+        _check(lib().chem_set_params(self._h, _dptr(dlnA, torch.float64, self.R, "dlnA"),
+                                     _dptr(dEa, torch.float64, self.R, "dEa"), _stream(stream)), "chem_set_params")
+
+    def adjoint(self, T, p, Y, dt, gT, gY, grad_lnA, grad_Ea, status, grad_cell=None, gT0=None, gY0=None, rtol=1e-6,
+                atol=1e-12, h_init=0.0, h_min=0.0, max_substeps=0, max_nonfinite=0, ckpt_every=0, tape_steps=0,
+                stream=None):
+        """chem_adjoint on device tensors: T, Y in/out (initial -> final state); gradients written in place."""
+        import torch
+        N = T.numel()
+        o = OptsC(rtol, atol, h_init, h_min, 0.0, max_substeps, max_nonfinite, 0, 0, 0, None, None, 0, ckpt_every,
+                  tape_steps)
+        _check(lib().chem_adjoint(
+            self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
+            _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
+            _dptr(gT, torch.float64, N, "gT"), _dptr(gY, torch.float64, self.n * N, "gY"),
+            _dptr(grad_lnA, torch.float64, self.R, "grad_lnA"), _dptr(grad_Ea, torch.float64, self.R, "grad_Ea"),
+            _dptr(grad_cell, torch.float64, 2 * self.R * N, "grad_cell"), _dptr(gT0, torch.float64, N, "gT0"),
+            _dptr(gY0, torch.float64, self.n * N, "gY0"), _dptr(status, torch.int32, N, "status"), C.byref(o),
+            _stream(stream)), "chem_adjoint")
 
     def integrate_noalloc(self, T, p, Y, dt, h_io, nsub, status, rtol=1e-6, atol=1e-12, h_init=0.0, h_min=0.0,
                           time_budget_s=0.0, max_substeps=0, max_nonfinite=0, block_warps=0, chunk=0, naccept=None,

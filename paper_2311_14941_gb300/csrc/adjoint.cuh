@@ -1,0 +1,266 @@
+// adjoint.cuh -- discrete adjoint of the RODAS3 integration (one warp per cell).
+//
+// The forward pass records the accepted step sizes and a checkpoint every K accepted steps.  The reverse
+// pass walks the segments backwards, recomputes a segment's states from its checkpoint with the same
+// arithmetic as the forward pass, and applies the adjoint of each step in reverse order.  Gradients are
+// those of the discrete map with the accepted step sizes frozen.
+//
+// Adjoint of one step (transformed form, M = I/(h gamma) - J(y), A U_i = r_i):
+//   mu_i = m_i lambda';  for i = 4..1:  w_i = M^-T mu_i;  mu_j += (c_ij/h) w_i (j < i);
+//     stage states Y_i = y + sum_j a_ij U_j:  g_i = J(Y_i)^T w_i,  lambda += g_i,  mu_j += a_ij g_i;
+//     Hessian term (J depends on y):           lambda += d/de [J(y + e U_i)^T w_i]
+//     parameters theta_j = (ln A_j, Ea_j):     dL/dtheta += w_i^T f_theta(Y_i) + w_i^T J_theta(y) U_i
+//   lambda (= dL/dy_n) = lambda' + sum of the above.
+// With J = S + u v^T: J^T w = S^T w + v (u.w), and M^-T x by Sherman-Morrison on the transposed factor.
+// A shift of ln A_j scales reaction j's forward and reverse rates (both fall-off limits for Troe), so
+// d f / d lnA_j = e_j q_j with e_j = d f / d q_j, and d f / d Ea_j = -e_j q_j / (Ru T); w^T e_j is a
+// sum over the reaction's participants of a_k = W_k w_k / rho - w_T H_k / (rho c_p).
+// The Hessian and the mixed parameter terms use forward-mode dual numbers through the same rate and
+// Jacobian code (exact, no finite differences).
+#pragma once
+#include "device.cuh"
+
+namespace chemgb {
+
+struct AdjLayout {
+  CellLayout L;        // base workspace (factor kept apart from the derivative slots)
+  int Y3, Y4, AU1, AU2, AU3, AU4, W1, W2, W3, W4, MU1, MU2, MU3, MU4, LAM, G, ZT, WS;   // m-vectors
+  int SY, UY, VY;      // S, u, v at y (the step's own Jacobian)
+  int A;               // n: participant coefficients of the parameter terms
+  int SEG;             // K*m: recomputed states of one segment
+  int GA, GE;          // R: gradient accumulators (compiled reaction order)
+  int total;
+};
+
+// out = J^T w = S^T w + v (u . w) with S in the internal entry order
+template <class Sc>
+__device__ __forceinline__ void vjp(const MechView& M, const Sc* S, const Sc* u, const Sc* v, const double* w, Sc* out,
+                                    Sc* part, int lane) {
+  run_gather(M.g_col, out + 1, part, [&](int a, int b) { return S[a] * w[1 + b]; }, lane);
+  Sc t0 = Sc(0.0), uw = Sc(0.0);
+  for (int k = lane; k < M.n; k += kWarp) t0 = sfma(S[M.nY + k], Sc(w[1 + k]), t0);
+  for (int i = lane; i < M.m; i += kWarp) uw = sfma(u[i], Sc(w[i]), uw);
+  t0 = warp_sum(t0);
+  uw = warp_sum(uw);
+  for (int c = lane; c < M.m; c += kWarp) {
+    const Sc base = (c == 0) ? t0 : out[c];
+    out[c] = sfma(v[c], uw, sfma(S[M.nY + M.n + c], Sc(w[0]), base));
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void acc_theta(double& g, double c) { g += c; }
+__device__ __forceinline__ void acc_theta(double& g, const Dual& c) { g += c.d; }
+
+// dL/dtheta += w^T f_theta at the evaluated state (value part for double, tangent part for Dual):
+// for reaction r, q_r * E_r with E_r = sum_products a_k - sum_reactants a_k.
+template <class Sc>
+__device__ __forceinline__ void theta_terms(const MechView& M, const Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
+                                            const double* w, Sc* a, double* GA, double* GE, int lane) {
+  const Sc c1 = (w[0] * kRu) * sc.T / (sc.rho * sc.cp);
+  for (int k = lane; k < M.n; k += kWarp)
+    a[k] = sfma(Sc(__ldg(M.sp + (size_t)k * SP_STRIDE + 1) * w[1 + k]), sc.irho, -(c1 * s[L.hRT + k]));
+  __syncwarp();
+  const Sc iRT = 1.0 / (kRu * sc.T);
+  for (int r = lane; r < M.R; r += kWarp) {
+    const int* I = M.rxi + (size_t)r * RX_I;
+    const int nro = __ldg(I + 2), npo = __ldg(I + 3);
+    Sc E = Sc(0.0);
+    for (int i = 0; i < npo; ++i) E += a[__ldg(I + 7 + i)];
+    for (int i = 0; i < nro; ++i) E -= a[__ldg(I + 4 + i)];
+    const Sc qE = s[L.q + r] * E;
+    acc_theta(GA[r], qE);
+    acc_theta(GE[r], -(qE * iRT));
+  }
+  __syncwarp();
+}
+
+// x <- A^-T x (transposed substitution with the same factor)
+__device__ __forceinline__ void lu_solveT(const MechView& M, const double* s, const CellLayout& L, double* x, int lane) {
+  const double* LU = s + L.LU;
+  const double* dinv = s + L.dinv;
+  const ElimOp* op = M.svT_ops + lane;
+  for (int st = 0; st < M.svT_steps; ++st, op += kWarp) {
+    const ElimOp o = ld_eop(op);
+    const int kind = __ldg(M.svT_kind + st);
+    if (o.t != OP_IDLE) {
+      if (kind == K_UPDATE) x[o.t] = fma(-LU[o.a], x[o.b], x[o.t]);
+      else x[o.t] *= dinv[o.a];
+    }
+    __syncwarp();
+  }
+}
+
+// x <- M^-T x with M^T = A^T - v u^T:  x = A^-T x + zt (u . A^-T x) / (1 - u . zt),  zt = A^-T v
+__device__ __forceinline__ void smT_solve(const MechView& M, const double* s, const AdjLayout& A, double* x,
+                                          double idenT, int lane) {
+  lu_solveT(M, s, A.L, x, lane);
+  const double* u = s + A.UY;
+  const double* zt = s + A.ZT;
+  double d = 0.0;
+  for (int i = lane; i < M.m; i += kWarp) d = fma(u[i], x[i], d);
+  d = warp_sum(d) * idenT;
+  for (int i = lane; i < M.m; i += kWarp) x[i] = fma(zt[i], d, x[i]);
+  __syncwarp();
+}
+
+__device__ __forceinline__ void vset(double* dst, const double* src, int m, int lane) {
+  for (int i = lane; i < m; i += kWarp) dst[i] = src[i];
+  __syncwarp();
+}
+
+// One adjoint step at state y (in A.SEG) with step h.  lambda (A.LAM) is updated in place.
+// Returns false if the factor is singular (cannot happen for a step the forward pass accepted).
+__device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
+                                             const CellLayout& Ld, const double* y, double p, double h, int lane) {
+  const CellLayout& L = A.L;
+  const int m = M.m;
+  const double ih = 1.0 / h;
+  double* U1 = s + A.AU1; double* U2 = s + A.AU2; double* U3 = s + A.AU3; double* U4 = s + A.AU4;
+  double* W1 = s + A.W1; double* W2 = s + A.W2; double* W3 = s + A.W3; double* W4 = s + A.W4;
+  double* MU1 = s + A.MU1; double* MU2 = s + A.MU2; double* MU3 = s + A.MU3; double* MU4 = s + A.MU4;
+  double* LAM = s + A.LAM; double* G = s + A.G; double* Y3 = s + A.Y3; double* Y4 = s + A.Y4;
+  double* GA = s + A.GA; double* GE = s + A.GE;
+  // ---- forward quantities of the step (same arithmetic as the forward attempt)
+  vset(s + L.y, y, m, lane);
+  eval_jac<double>(M, s, L, s + L.y, p, lane);
+  vset(s + A.SY, s + L.S, M.nnz_S, lane);
+  vset(s + A.UY, s + L.u, m, lane);
+  vset(s + A.VY, s + L.v, m, lane);
+  if (!lu_build_factor(M, s, L, ih * (1.0 / RG), lane)) return false;
+  double* z = s + L.z;
+  const double* u = s + A.UY;
+  const double* v = s + A.VY;
+  const double* f0 = s + L.f0;
+  for (int i = lane; i < m; i += kWarp) { z[i] = u[i]; U1[i] = f0[i]; }
+  __syncwarp();
+  lu_solve_impl<true>(M, s, L, z, U1, lane);
+  double vz = 0.0, vx = 0.0;
+  for (int i = lane; i < m; i += kWarp) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
+  vz = warp_sum(vz);
+  vx = warp_sum(vx);
+  const double iden = 1.0 / (1.0 - vz);
+  vx *= iden;
+  for (int i = lane; i < m; i += kWarp) U1[i] = fma(z[i], vx, U1[i]);
+  __syncwarp();
+  for (int i = lane; i < m; i += kWarp) U2[i] = fma(C21 * ih, U1[i], f0[i]);
+  __syncwarp();
+  sm_solve(M, s, L, U2, iden, lane);
+  for (int i = lane; i < m; i += kWarp) Y3[i] = fma(A31, U1[i], y[i]);
+  __syncwarp();
+  eval_f<double>(M, s, L, Y3, p, U3, lane);
+  for (int i = lane; i < m; i += kWarp) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
+  __syncwarp();
+  sm_solve(M, s, L, U3, iden, lane);
+  for (int i = lane; i < m; i += kWarp) Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
+  __syncwarp();
+  eval_f<double>(M, s, L, Y4, p, U4, lane);
+  for (int i = lane; i < m; i += kWarp) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
+  __syncwarp();
+  sm_solve(M, s, L, U4, iden, lane);
+  // transposed Sherman-Morrison vector
+  double* zt = s + A.ZT;
+  vset(zt, v, m, lane);
+  lu_solveT(M, s, L, zt, lane);
+  double uz = 0.0;
+  for (int i = lane; i < m; i += kWarp) uz = fma(u[i], zt[i], uz);
+  uz = warp_sum(uz);
+  const double idenT = 1.0 / (1.0 - uz);
+  // ---- reverse sweep over the stages
+  for (int i = lane; i < m; i += kWarp) {
+    MU1[i] = M1 * LAM[i]; MU2[i] = 0.0; MU3[i] = M3 * LAM[i]; MU4[i] = M4 * LAM[i];
+  }
+  __syncwarp();
+  // stage 4: r4 = f(Y4) + (c41 U1 + c42 U2 + c43 U3)/h, Y4 = y + a41 U1 + a43 U3
+  vset(W4, MU4, m, lane);
+  smT_solve(M, s, A, W4, idenT, lane);
+  {
+    ScalT<double> sc = eval_jac<double>(M, s, L, Y4, p, lane);
+    theta_terms<double>(M, s, L, sc, W4, s + A.A, GA, GE, lane);
+    vjp<double>(M, s + L.S, s + L.u, s + L.v, W4, G, s + L.part, lane);
+  }
+  for (int i = lane; i < m; i += kWarp) {
+    MU1[i] = fma(C41 * ih, W4[i], fma(A41, G[i], MU1[i]));
+    MU2[i] = fma(C42 * ih, W4[i], MU2[i]);
+    MU3[i] = fma(C43 * ih, W4[i], fma(A43, G[i], MU3[i]));
+    LAM[i] += G[i];
+  }
+  __syncwarp();
+  // stage 3: r3 = f(Y3) + (c31 U1 + c32 U2)/h, Y3 = y + a31 U1
+  vset(W3, MU3, m, lane);
+  smT_solve(M, s, A, W3, idenT, lane);
+  {
+    ScalT<double> sc = eval_jac<double>(M, s, L, Y3, p, lane);
+    theta_terms<double>(M, s, L, sc, W3, s + A.A, GA, GE, lane);
+    vjp<double>(M, s + L.S, s + L.u, s + L.v, W3, G, s + L.part, lane);
+  }
+  for (int i = lane; i < m; i += kWarp) {
+    MU1[i] = fma(C31 * ih, W3[i], fma(A31, G[i], MU1[i]));
+    MU2[i] = fma(C32 * ih, W3[i], MU2[i]);
+    LAM[i] += G[i];
+  }
+  __syncwarp();
+  // stage 2: r2 = f(y) + (c21/h) U1;  stage 1: r1 = f(y)
+  vset(W2, MU2, m, lane);
+  smT_solve(M, s, A, W2, idenT, lane);
+  for (int i = lane; i < m; i += kWarp) MU1[i] = fma(C21 * ih, W2[i], MU1[i]);
+  __syncwarp();
+  vset(W1, MU1, m, lane);
+  smT_solve(M, s, A, W1, idenT, lane);
+  double* WS = s + A.WS;
+  for (int i = lane; i < m; i += kWarp) WS[i] = W1[i] + W2[i];
+  __syncwarp();
+  vjp<double>(M, s + A.SY, s + A.UY, s + A.VY, WS, G, s + L.part, lane);
+  for (int i = lane; i < m; i += kWarp) LAM[i] += G[i];
+  __syncwarp();
+  {
+    vset(s + L.y, y, m, lane);
+    ScalT<double> sc = eval_f<double>(M, s, L, s + L.y, p, s + L.f0, lane);
+    theta_terms<double>(M, s, L, sc, WS, s + A.A, GA, GE, lane);
+  }
+  // ---- Hessian and mixed parameter terms: derivative of J(y) along U_i, contracted with w_i
+  const double* Us[4] = {U1, U2, U3, U4};
+  const double* Ws[4] = {W1, W2, W3, W4};
+  for (int st = 0; st < 4; ++st) {
+    Dual* yd = dw + Ld.y;
+    for (int i = lane; i < m; i += kWarp) yd[i] = Dual(y[i], Us[st][i]);
+    __syncwarp();
+    ScalT<Dual> scd = eval_jac<Dual>(M, dw, Ld, yd, p, lane);
+    Dual* Gd = dw + Ld.x;
+    vjp<Dual>(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws[st], Gd, dw + Ld.part, lane);
+    for (int i = lane; i < m; i += kWarp) LAM[i] += Gd[i].d;
+    __syncwarp();
+    theta_terms<Dual>(M, dw, Ld, scd, Ws[st], dw + Ld.z, GA, GE, lane);
+  }
+  return true;
+}
+
+// Reverse pass of one cell from its tape.  Returns false on a singular factor.
+__device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
+                                             const CellLayout& Ld, double p, int n_acc, const double* rec_h,
+                                             const double* rec_ck, int K, int N, int cell, int lane,
+                                             const IntOpts& o) {
+  const int m = M.m;
+  const CellLayout& L = A.L;
+  double* seg = s + A.SEG;
+  const int nseg = (n_acc + K - 1) / K;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int n0 = sg * K, n1 = min(n_acc, n0 + K);
+    for (int i = lane; i < m; i += kWarp) seg[i] = rec_ck[((size_t)sg * m + i) * N + cell];
+    __syncwarp();
+    // recompute the segment's states with the forward arithmetic
+    for (int nn = n0; nn < n1 - 1; ++nn) {
+      vset(s + L.y, seg + (size_t)(nn - n0) * m, m, lane);
+      eval_jac<double>(M, s, L, s + L.y, p, lane);
+      const StepOut so = ros_attempt(M, s, L, p, rec_h[(size_t)nn * N + cell], o.rtol, o.atol, lane);
+      if (!so.good) return false;
+      vset(seg + (size_t)(nn - n0 + 1) * m, s + L.ytmp, m, lane);
+    }
+    for (int nn = n1 - 1; nn >= n0; --nn)
+      if (!adjoint_step(M, s, A, dw, Ld, seg + (size_t)(nn - n0) * m, p, rec_h[(size_t)nn * N + cell], lane))
+        return false;
+  }
+  return true;
+}
+
+}  // namespace chemgb

@@ -10,6 +10,7 @@
 
 #include "../../include/chem.h"
 #include "compile.h"
+#include "adjoint.cuh"
 #include "device.cuh"
 
 using namespace chemgb;
@@ -41,9 +42,13 @@ struct chem_handle_s {
   int smem_optin = 0;
   int num_sms = 0;
   bool attr_set = false;
+  bool adj_attr_set = false;
+  const double* rxd0 = nullptr;   // the compiled (unshifted) reaction table
   // scratch of the sorted work queue and the time-budget stamp (grows on demand)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* adj_scratch = nullptr;     // adjoint tape, gradients, dual workspaces (grows on demand)
+  size_t adj_scratch_bytes = 0;
   int occ_blocks_per_sm[2] = {0, 0};   // persistent kernel occupancy per block size choice (cached)
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
@@ -60,7 +65,7 @@ struct chem_handle_s {
 namespace {
 
 // Shared-memory layout of one cell (offsets in doubles).
-CellLayout make_layout(const HostMech& hm) {
+CellLayout make_layout(const HostMech& hm, bool separate_lu = false) {
   CellLayout L{};
   int o = 0;
   const int m = hm.m, n = hm.n, R = hm.R;
@@ -72,17 +77,40 @@ CellLayout make_layout(const HostMech& hm) {
   L.S = take(hm.nnz_S);
   // the derivative slots are dead once S is assembled; the factor reuses their space
   const int lu_part = hm.nnz_LU + m;
-  const int reuse = std::max(lu_part, hm.n_dslot);
-  L.D = o;
-  L.LU = o;
-  L.dinv = o + hm.nnz_LU;
-  o += reuse;
+  if (separate_lu) {
+    L.D = take(std::max(hm.n_dslot, 1));
+    L.LU = take(hm.nnz_LU);
+    L.dinv = take(m);
+  } else {
+    const int reuse = std::max(lu_part, hm.n_dslot);
+    L.D = o;
+    L.LU = o;
+    L.dinv = o + hm.nnz_LU;
+    o += reuse;
+  }
   int np = 1;
   for (const HostGather* g : {&hm.g_omega, &hm.g_dtil, &hm.g_row, &hm.g_col}) np = std::max(np, g->n_partial);
   L.part = take(2 * np);
   L.misc = take(16);
   L.total = o;
   return L;
+}
+
+AdjLayout make_adj_layout(const HostMech& hm, int K) {
+  AdjLayout A{};
+  A.L = make_layout(hm, true);
+  int o = A.L.total;
+  const int m = hm.m;
+  auto take = [&](int cnt) { int at = o; o += cnt; return at; };
+  A.Y3 = take(m); A.Y4 = take(m); A.AU1 = take(m); A.AU2 = take(m); A.AU3 = take(m); A.AU4 = take(m);
+  A.W1 = take(m); A.W2 = take(m); A.W3 = take(m); A.W4 = take(m); A.MU1 = take(m); A.MU2 = take(m);
+  A.MU3 = take(m); A.MU4 = take(m); A.LAM = take(m); A.G = take(m); A.ZT = take(m); A.WS = take(m);
+  A.SY = take(hm.nnz_S); A.UY = take(m); A.VY = take(m);
+  A.A = take(hm.n);
+  A.SEG = take(K * m);
+  A.GA = take(std::max(hm.R, 1)); A.GE = take(std::max(hm.R, 1));
+  A.total = o;
+  return A;
 }
 
 template <class T>
@@ -131,7 +159,7 @@ __global__ void k_rates(MechView M, CellLayout L, int N, const double* __restric
   const int c = c0 + w;
   if (c >= N) return;
   double* f = s + L.f0;
-  Scal sc = eval_f(M, s, L, s + L.y, p[c], f, lane);
+  Scal sc = eval_f<double>(M, s, L, s + L.y, p[c], f, lane);
   for (int i = lane; i < M.m; i += kWarp) {
     if (i == 0) dTdt[c] = f[0];
     else dYdt[(size_t)(i - 1) * N + c] = f[i];
@@ -151,7 +179,7 @@ __global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __rest
   load_tile(smem, L, M.m, N, c0, wpb, T, Y);
   const int c = c0 + w;
   if (c >= N) return;
-  eval_jac(M, s, L, s + L.y, p[c], lane);
+  eval_jac<double>(M, s, L, s + L.y, p[c], lane);
   for (int e = lane; e < M.nnz_S; e += kWarp) Sv[(size_t)__ldg(M.s_out + e) * N + c] = s[L.S + e];
   for (int i = lane; i < M.m; i += kWarp) {
     u[(size_t)i * N + c] = s[L.u + i];
@@ -280,6 +308,81 @@ __global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* 
   }
 }
 
+// ---- discrete adjoint: resident warps pull cells; each has its own dual-number workspace in global
+// memory (the forward-layout size in Duals)
+__global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const double* __restrict__ p,
+                          const double* __restrict__ rec_h, const double* __restrict__ rec_ck,
+                          const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
+                          const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
+                          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head, Dual* dual_ws,
+                          IntOpts o) {
+  extern __shared__ double smem[];
+  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  double* s = smem + (size_t)w * A.total;
+  Dual* dw = dual_ws + (size_t)(blockIdx.x * wpb + w) * Ld.total;
+  const int m = M.m;
+  while (true) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(head, 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= N) break;
+    const int na = rec_n[c];
+    double* LAM = s + A.LAM;
+    for (int i = lane; i < m; i += kWarp) LAM[i] = (i == 0) ? gT[c] : gY[(size_t)(i - 1) * N + c];
+    for (int r = lane; r < M.R; r += kWarp) { s[A.GA + r] = 0.0; s[A.GE + r] = 0.0; }
+    __syncwarp();
+    bool ok = na >= 0;
+    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, lane, o);
+    if (!ok) {
+      for (int i = lane; i < m; i += kWarp) LAM[i] = 0.0;
+      for (int r = lane; r < M.R; r += kWarp) { s[A.GA + r] = 0.0; s[A.GE + r] = 0.0; }
+      __syncwarp();
+    }
+    for (int r = lane; r < M.R; r += kWarp) {
+      const int d = __ldg(M.rx_order + r);
+      grad_cell[(size_t)d * N + c] = s[A.GA + r];
+      grad_cell[(size_t)(M.R + d) * N + c] = s[A.GE + r];
+    }
+    if (gT0 && lane == 0) gT0[c] = LAM[0];
+    if (gY0)
+      for (int i = 1 + lane; i < m; i += kWarp) gY0[(size_t)(i - 1) * N + c] = LAM[i];
+    if (status && lane == 0 && !ok && status[c] == CHEM_CELL_OK) status[c] = CHEM_CELL_NOTAPE;
+    __syncwarp();
+  }
+}
+
+// sums over cells in a fixed order (one warp per parameter): deterministic gradients
+__global__ void k_grad_reduce(int N, int P, const double* __restrict__ grad_cell, double* __restrict__ out1,
+                              double* __restrict__ out2, int half) {
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp, lane = threadIdx.x % kWarp;
+  if (wg >= P) return;
+  double acc = 0.0;
+  for (int c = lane; c < N; c += kWarp) acc += grad_cell[(size_t)wg * N + c];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    if (wg < half) out1[wg] = acc;
+    else out2[wg - half] = acc;
+  }
+}
+
+// parameter shifts: ln A_r = ln A_r,0 + dlnA[d], Ea_r = Ea_r,0 + dEa[d] (d: description index of
+// compiled reaction r); Troe low-pressure limits shift jointly
+__global__ void k_set_params(MechView M, const double* __restrict__ rxd0, double* __restrict__ rxd,
+                             const double* __restrict__ dlnA, const double* __restrict__ dEa) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M.R) return;
+  const int d = __ldg(M.rx_order + r);
+  const double a = dlnA ? dlnA[d] : 0.0, e = dEa ? dEa[d] / kRu : 0.0;
+  const double* src = rxd0 + (size_t)r * RX_D;
+  double* dst = rxd + (size_t)r * RX_D;
+  dst[0] = src[0] + a;
+  dst[2] = src[2] + e;
+  if (__ldg((const int*)(M.rxi + (size_t)r * RX_I)) == 2) {
+    dst[3] = src[3] + a;
+    dst[5] = src[5] + e;
+  }
+}
+
 }  // namespace chemgb
 
 // =============================================================================================== ABI
@@ -388,7 +491,8 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
          o_dam = put(buf, hm.dslot_am1), o_er = put(buf, hm.entry_row), o_ec = put(buf, hm.entry_col),
          o_ew = put(buf, hm.entry_wratio), o_lsrc = put(buf, hm.lu_src), o_ldiag = put(buf, hm.lu_diag),
          o_lops = put(buf, hm.lu_ops), o_lkind = put(buf, hm.lu_kind), o_sops = put(buf, hm.sv_ops),
-         o_skind = put(buf, hm.sv_kind), o_sout = put(buf, hm.s_out);
+         o_skind = put(buf, hm.sv_kind), o_sout = put(buf, hm.s_out), o_tops = put(buf, hm.svT_ops),
+         o_tkind = put(buf, hm.svT_kind), o_rxo = put(buf, hm.rx_order), o_rxd0 = put(buf, hm.rxd);
   size_t o_g[4][2];
   const HostGather* gs[4] = {&hm.g_omega, &hm.g_dtil, &hm.g_row, &hm.g_col};
   for (int i = 0; i < 4; ++i) { o_g[i][0] = put(buf, gs[i]->ops); o_g[i][1] = put(buf, gs[i]->comb); }
@@ -410,6 +514,10 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   V.lu_ops = (const ElimOp*)(b + o_lops); V.lu_kind = (const uint8_t*)(b + o_lkind); V.lu_steps = (int)hm.lu_kind.size();
   V.sv_ops = (const ElimOp*)(b + o_sops); V.sv_kind = (const uint8_t*)(b + o_skind); V.sv_steps = (int)hm.sv_kind.size();
   V.s_out = (const int*)(b + o_sout);
+  V.svT_ops = (const ElimOp*)(b + o_tops); V.svT_kind = (const uint8_t*)(b + o_tkind);
+  V.svT_steps = (int)hm.svT_kind.size();
+  V.rx_order = (const int*)(b + o_rxo);
+  h->rxd0 = (const double*)(b + o_rxd0);
   Gather* vg[4] = {&V.g_omega, &V.g_dtil, &V.g_row, &V.g_col};
   for (int i = 0; i < 4; ++i) {
     vg[i]->ops = (const GatherOp*)(b + o_g[i][0]);
@@ -430,6 +538,7 @@ chem_status chem_destroy(chem_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->blob) cudaFree(h->blob);
   if (h->scratch) cudaFree(h->scratch);
+  if (h->adj_scratch) cudaFree(h->adj_scratch);
   delete h;
   return CHEM_OK;
 }
@@ -473,6 +582,8 @@ chem_status chem_export_plan(chem_handle h, int which, int* out, int* count) {
     case 3: v = hm.lu_rowptr; v.insert(v.end(), hm.lu_col.begin(), hm.lu_col.end()); break;
     case 4: v = hm.lu_src; break;
     case 5: v = hm.s_out; break;
+    case 6: prog(hm.svT_ops, hm.svT_kind); break;
+    case 7: v = hm.rx_order; break;
     default: return fail(CHEM_EINVAL, "unknown plan part");
   }
   if (out) std::copy(v.begin(), v.end(), out);
@@ -528,6 +639,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   io.trace = o.trace;
   io.trace_cap = o.trace ? o.trace_cap : 0;
   io.N = N;
+  io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
     return fail(CHEM_EINVAL, "non-finite option");
@@ -602,6 +714,113 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
 
 }  // extern "C"
 
+extern "C" chem_status chem_set_params(chem_handle h, const double* dlnA, const double* dEa, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (h->hm.R == 0) return CHEM_OK;
+  k_set_params<<<(h->hm.R + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->view, h->rxd0, (double*)h->view.rxd,
+                                                                         dlnA, dEa);
+  return launch_check("chem_set_params launch");
+}
+
+extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
+                                    const double* gT, const double* gY, double* grad_lnA, double* grad_Ea,
+                                    double* grad_cell, double* gT0, double* gY0, int* status,
+                                    const chem_integrate_opts* opts, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N == 0) return CHEM_OK;
+  if (!T || !p || !Y || !dt || !gT || !gY || !grad_lnA || !grad_Ea || !status)
+    return fail(CHEM_EINVAL, "null array argument");
+  chem_integrate_opts o{};
+  if (opts) o = *opts;
+  IntOpts io;
+  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
+  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
+  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
+  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
+  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
+  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
+  io.deadline_ns = 0;
+  io.trace = nullptr;
+  io.trace_cap = 0;
+  io.N = N;
+  const int K = o.ckpt_every > 0 ? o.ckpt_every : 16;
+  const int cap = o.tape_steps > 0 ? o.tape_steps : 4096;
+  if (K > 64) return fail(CHEM_EINVAL, "ckpt_every must be <= 64");
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  const HostMech& hm = h->hm;
+  const int m = hm.m;
+  const AdjLayout A = make_adj_layout(hm, K);
+  const int adj_bytes = A.total * (int)sizeof(double);
+  if (adj_bytes > h->smem_optin)
+    return fail(CHEM_EUNSUPPORTED, "adjoint needs " + std::to_string(adj_bytes) + " bytes of shared memory per cell");
+  cudaError_t e;
+  if (!h->adj_attr_set) {
+    if ((e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_optin)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    h->adj_attr_set = true;
+  }
+  int bps = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_adjoint, kWarp, (size_t)adj_bytes)) != cudaSuccess)
+    return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  bps = std::max(bps, 1);
+  const int grid = std::min(h->num_sms * bps, N);
+  // scratch: head, tape (h, checkpoints, counts), h_io/nsub of the forward pass, per-cell gradients,
+  // dual workspaces
+  const size_t nck = (size_t)(cap / K + 1);
+  const size_t b_head = 256;
+  const size_t b_rh = align_up((size_t)cap * N * 8, 256);
+  const size_t b_ck = align_up(nck * m * N * 8, 256);
+  const size_t b_rn = align_up((size_t)N * 4, 256);
+  const size_t b_hio = align_up((size_t)N * 8, 256);
+  const size_t b_ns = align_up((size_t)N * 4, 256);
+  const size_t b_gc = grad_cell ? 0 : align_up((size_t)2 * hm.R * N * 8, 256);
+  const size_t b_dw = align_up((size_t)grid * h->L.total * sizeof(Dual), 256);
+  const size_t need = b_head + b_rh + b_ck + b_rn + b_hio + b_ns + b_gc + b_dw;
+  if (need > h->adj_scratch_bytes) {
+    if (h->adj_scratch) cudaFree(h->adj_scratch);
+    h->adj_scratch = nullptr;
+    h->adj_scratch_bytes = 0;
+    if (cudaMalloc(&h->adj_scratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CHEM_ENOMEM, "cudaMalloc of adjoint scratch (" + std::to_string(need) + " bytes) failed");
+    }
+    h->adj_scratch_bytes = need;
+  }
+  char* q = (char*)h->adj_scratch;
+  int* head = (int*)q; q += b_head;
+  double* rec_h = (double*)q; q += b_rh;
+  double* rec_ck = (double*)q; q += b_ck;
+  int* rec_n = (int*)q; q += b_rn;
+  double* hio = (double*)q; q += b_hio;
+  int* nsub = (int*)q; q += b_ns;
+  double* gcell = grad_cell;
+  if (!gcell) { gcell = (double*)q; q += b_gc; }
+  Dual* dws = (Dual*)q;
+  cudaStream_t strm = (cudaStream_t)stream;
+  // forward pass with the tape
+  io.rec_h = rec_h; io.rec_ck = rec_ck; io.rec_n = rec_n; io.rec_cap = cap; io.rec_K = K;
+  if ((e = cudaMemsetAsync(hio, 0, (size_t)N * 8, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  k_integrate_plain<<<N, kWarp, h->cell_bytes, strm>>>(h->view, h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
+                                                       io, nullptr, 0ull);
+  if ((st = launch_check("chem_adjoint forward launch")) != CHEM_OK) return st;
+  // reverse pass
+  io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr;
+  if ((e = cudaMemsetAsync(head, 0, 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  CellLayout Ld = h->L;
+  k_adjoint<<<grid, kWarp, adj_bytes, strm>>>(h->view, A, Ld, N, p, rec_h, rec_ck, rec_n, K, gT, gY, gcell, gT0, gY0,
+                                               status, head, dws, io);
+  if ((st = launch_check("chem_adjoint reverse launch")) != CHEM_OK) return st;
+  const int P = 2 * hm.R;
+  if (P > 0) {
+    k_grad_reduce<<<(P * kWarp + 255) / 256, 256, 0, strm>>>(N, P, gcell, grad_lnA, grad_Ea, hm.R);
+    if ((st = launch_check("chem_adjoint reduction launch")) != CHEM_OK) return st;
+  }
+  return CHEM_OK;
+}
+
 // Device address of the static scratch array on the current device.  In host code the array's name
 // only stands for it; the real address is looked up once per device and kept.
 namespace {
@@ -647,6 +866,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   io.trace = o.trace;
   io.trace_cap = o.trace ? o.trace_cap : 0;
   io.N = N;
+  io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
     return fail(CHEM_EINVAL, "non-finite option");

@@ -537,6 +537,45 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
     for (auto& pr : bw) ops[sc[pr.second]].succ.push_back(pr.first);           // RAW backward
     if (!schedule(ops, hm.sv_ops, hm.sv_kind, err)) return CHEM_EINVAL;
   }
+  // ---- transposed substitution (A^T x = b): forward with U^T (scaled by 1/diag), then backward with
+  //      the unit L^T.  In factor positions: x_p -= U_qp x_q (q < p), x_p *= 1/U_pp; then x_p -= L_qp x_q
+  //      (q > p).  Same op encoding, state-order vector indices.
+  {
+    std::vector<DagOp> ops;
+    std::vector<std::vector<int>> f_w(m), f_r(m), b_w(m);
+    std::vector<int> sc(m);
+    for (int p = 0; p < m; ++p) {
+      sc[p] = (int)ops.size();
+      ops.push_back(DagOp{K_SCALE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)p, 0, 0}, {}});
+    }
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < p; ++q)
+        if (slot[q][p] >= 0) {   // U entry (q, p)
+          int id = (int)ops.size();
+          ops.push_back(DagOp{K_UPDATE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)slot[q][p], (uint16_t)hm.perm[q], 0}, {}});
+          f_w[p].push_back(id);
+          f_r[q].push_back(id);
+          ops[sc[q]].succ.push_back(id);    // reads x_q after its scaling
+          ops[id].succ.push_back(sc[p]);    // x_p scaled after all its updates
+        }
+    std::vector<std::pair<int, int>> bl;    // (op id, q)
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q)
+        if (slot[q][p] >= 0) {   // L entry (q, p)
+          int id = (int)ops.size();
+          ops.push_back(DagOp{K_UPDATE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)slot[q][p], (uint16_t)hm.perm[q], 0}, {}});
+          b_w[p].push_back(id);
+          bl.push_back({id, q});
+          ops[sc[p]].succ.push_back(id);                       // backward phase after x_p's forward value
+          for (int r : f_r[p]) ops[r].succ.push_back(id);      // WAR: forward readers of x_p first
+        }
+    for (auto& pr : bl) {
+      const int q = pr.second;
+      ops[sc[q]].succ.push_back(pr.first);                     // x_q forward-final
+      for (int w : b_w[q]) ops[w].succ.push_back(pr.first);    // x_q backward-final
+    }
+    if (!schedule(ops, hm.svT_ops, hm.svT_kind, err)) return CHEM_EINVAL;
+  }
   return CHEM_OK;
 }
 

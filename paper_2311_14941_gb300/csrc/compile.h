@@ -24,8 +24,8 @@ struct HostMech {
   std::vector<int> perm, iperm;        // LU position -> state index, and back
   std::vector<int> lu_src, lu_diag, s_out;
   std::vector<int> lu_rowptr, lu_col;  // factor pattern, CSR in LU (permuted) order
-  std::vector<ElimOp> lu_ops, sv_ops;
-  std::vector<uint8_t> lu_kind, sv_kind;
+  std::vector<ElimOp> lu_ops, sv_ops, svT_ops;
+  std::vector<uint8_t> lu_kind, sv_kind, svT_kind;
   std::vector<int> csr_ptr, csr_col;   // S pattern in natural state order
   long long lu_flops = 0;              // multiply-adds of one factorisation (algorithmic)
 };

@@ -23,6 +23,7 @@
 #include <cstdint>
 
 #include "mech.h"
+#include "scalar.cuh"
 
 namespace chemgb {
 
@@ -38,11 +39,6 @@ constexpr double M1 = 2.0, M3 = 1.0, M4 = 1.0;
 constexpr double kInvLn10 = 0.43429448190325182765;
 constexpr double kLn10 = 2.30258509299404568402;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;   // identical on every lane (each butterfly stage adds the same pair of operands)
-}
 
 __device__ __forceinline__ GatherOp ld_gop(const GatherOp* p) {
   uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
@@ -61,28 +57,37 @@ __device__ __forceinline__ ElimOp ld_eop(const ElimOp* p) {
 }
 
 // Per-cell scalars shared by all lanes (every lane holds the same values).
-struct Scal {
-  double T, lnT, invT, Wbar, rho, irho, cp, ctot, rtp, irtp, dcps;
+template <class Sc>
+struct ScalT {
+  Sc T, lnT, invT, Wbar, rho, irho, cp, ctot, rtp, irtp, dcps;
 };
+using Scal = ScalT<double>;
+
+// Coefficients nu = -3..3 of the gather programs, looked up instead of converted (a conversion to
+// double would occupy the FP64 pipe).
+__device__ __forceinline__ double nu_of(int b) {
+  const int v = (int)(int16_t)(uint16_t)b;
+  return v == 1 ? 1.0 : v == -1 ? -1.0 : v == 2 ? 2.0 : v == -2 ? -2.0 : v == 3 ? 3.0 : v == -3 ? -3.0 : 0.0;
+}
 
 // -------------------------------------------------------------------------------------- gathers
 // out[g] = sum over the group's terms of val(a, b); partial sums of split groups are combined after.
-template <class F>
-__device__ __forceinline__ void run_gather(const Gather& G, double* out, double* part, F val, int lane) {
-  double acc = 0.0;
+template <class Sc, class F>
+__device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F valf, int lane) {
+  Sc acc = Sc(0.0);
   const GatherOp* op = G.ops + lane;
   for (int s = 0; s < G.steps; ++s, op += kWarp) {
     GatherOp o = ld_gop(op);
-    if (!(o.flags & 1)) acc += val(o.a, o.b);
+    if (!(o.flags & 1)) acc += valf(o.a, o.b);
     if (o.dst != DST_NONE) {
       if (o.dst & PARTIAL_BIT) part[o.dst & 0x7FFF] = acc; else out[o.dst] = acc;
-      acc = 0.0;
+      acc = Sc(0.0);
     }
   }
   __syncwarp();
   for (int c = lane; c < G.n_comb; c += kWarp) {
     const int dst = __ldg(G.comb + 3 * c), f = __ldg(G.comb + 3 * c + 1), cnt = __ldg(G.comb + 3 * c + 2);
-    double s = 0.0;
+    Sc s = Sc(0.0);
     for (int i = 0; i < cnt; ++i) s += part[f + i];
     out[dst] = s;
   }
@@ -90,16 +95,17 @@ __device__ __forceinline__ void run_gather(const Gather& G, double* out, double*
 }
 
 // Same program, two accumulators: out1[g] = sum nu q[r], out2[g] = sum nu dq[r].
-__device__ __forceinline__ void run_gather2(const Gather& G, double* out1, double* out2, double* part,
-                                            const double* q, const double* dq, int lane) {
-  double acc1 = 0.0, acc2 = 0.0;
+template <class Sc>
+__device__ __forceinline__ void run_gather2(const Gather& G, Sc* out1, Sc* out2, Sc* part, const Sc* q,
+                                            const Sc* dq, int lane) {
+  Sc acc1 = Sc(0.0), acc2 = Sc(0.0);
   const GatherOp* op = G.ops + lane;
   for (int s = 0; s < G.steps; ++s, op += kWarp) {
     GatherOp o = ld_gop(op);
     if (!(o.flags & 1)) {
-      const double nu = (double)(int16_t)o.b;
-      acc1 = fma(nu, q[o.a], acc1);
-      acc2 = fma(nu, dq[o.a], acc2);
+      const double nu = nu_of(o.b);
+      acc1 = sfma(Sc(nu), q[o.a], acc1);
+      acc2 = sfma(Sc(nu), dq[o.a], acc2);
     }
     if (o.dst != DST_NONE) {
       if (o.dst & PARTIAL_BIT) {
@@ -109,13 +115,13 @@ __device__ __forceinline__ void run_gather2(const Gather& G, double* out1, doubl
         out1[o.dst] = acc1;
         out2[o.dst] = acc2;
       }
-      acc1 = acc2 = 0.0;
+      acc1 = acc2 = Sc(0.0);
     }
   }
   __syncwarp();
   for (int c = lane; c < G.n_comb; c += kWarp) {
     const int dst = __ldg(G.comb + 3 * c), f = __ldg(G.comb + 3 * c + 1), cnt = __ldg(G.comb + 3 * c + 2);
-    double s1 = 0.0, s2 = 0.0;
+    Sc s1 = Sc(0.0), s2 = Sc(0.0);
     for (int i = 0; i < cnt; ++i) { s1 += part[2 * (f + i)]; s2 += part[2 * (f + i) + 1]; }
     out1[dst] = s1;
     out2[dst] = s2;
@@ -124,41 +130,64 @@ __device__ __forceinline__ void run_gather2(const Gather& G, double* out1, doubl
 }
 
 // -------------------------------------------------------------------------------------- thermo
-// NASA-7 at T for every species (lanes over species); fills C, hRT, eg = exp(g), emg = 1/eg, cpR.
-template <bool DERIV>
-__device__ __forceinline__ Scal eval_species(const MechView& M, double* s, const CellLayout& L, const double* y,
-                                             double p, int lane) {
-  Scal sc;
+// One species at T: cp/R, h/RT, g = h/RT - s/R and its exponential (NASA-7, range by T vs T_mid).
+template <class Sc>
+struct SpOut {
+  Sc cpR, hRT, eg, yw, dcp;
+};
+
+template <class Sc, bool DERIV>
+__device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, const Sc* y, Sc T, Sc lnT, Sc invT) {
+  const double* t = M.sp + (size_t)k * SP_STRIDE;
+  const double iw = __ldg(t);
+  const double* c = t + 4 + (val(T) < __ldg(t + 2) ? 0 : SP_RANGE);
+  const Sc a0 = __ldg(c + 0), a1 = __ldg(c + 1), a2 = __ldg(c + 2), a3 = __ldg(c + 3), a4 = __ldg(c + 4);
+  SpOut<Sc> o;
+  o.cpR = sfma(T, sfma(T, sfma(T, sfma(T, a4, a3), a2), a1), a0);
+  const Sc h = sfma(T, sfma(T, sfma(T, sfma(T, Sc(__ldg(c + 8)), Sc(__ldg(c + 7))), Sc(__ldg(c + 6))), Sc(__ldg(c + 5))),
+                    a0);
+  const Sc a5 = __ldg(c + 13), a6 = __ldg(c + 14);
+  o.hRT = sfma(a5, invT, h);
+  const Sc gp = sfma(T, sfma(T, sfma(T, sfma(T, Sc(__ldg(c + 12)), Sc(__ldg(c + 11))), Sc(__ldg(c + 10))),
+                             Sc(__ldg(c + 9))),
+                     sfma(a5, invT, -a6));
+  o.eg = sexp(sfma(a0, 1.0 - lnT, gp));
+  o.yw = y[1 + k] * iw;
+  o.dcp = DERIV ? sfma(T, sfma(T, Sc(__ldg(c + 17)) * T + Sc(__ldg(c + 16)), Sc(__ldg(c + 15))), a1) : Sc(0.0);
+  return o;
+}
+
+// NASA-7 at T for every species, two species per lane at a time (independent exp chains in flight);
+// fills C, hRT, eg = exp(g), emg = 1/eg, cpR.
+template <class Sc, bool DERIV>
+__device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, const CellLayout& L, const Sc* y,
+                                                  double p, int lane) {
+  ScalT<Sc> sc;
   sc.T = y[0];
-  sc.lnT = log(sc.T);
+  sc.lnT = slog(sc.T);
   sc.invT = 1.0 / sc.T;
-  const double T = sc.T;
-  double sig = 0.0, cps = 0.0, dcps = 0.0;
-  for (int k = lane; k < M.n; k += kWarp) {
-    const double* t = M.sp + (size_t)k * SP_STRIDE;
-    const double iw = __ldg(t);
-    const double* c = t + 4 + (T < __ldg(t + 2) ? 0 : SP_RANGE);
-    const double a0 = __ldg(c + 0), a1 = __ldg(c + 1), a2 = __ldg(c + 2), a3 = __ldg(c + 3), a4 = __ldg(c + 4);
-    const double cpR = fma(T, fma(T, fma(T, fma(T, a4, a3), a2), a1), a0);
-    const double h = fma(T, fma(T, fma(T, fma(T, __ldg(c + 8), __ldg(c + 7)), __ldg(c + 6)), __ldg(c + 5)), a0);
-    const double a5 = __ldg(c + 13), a6 = __ldg(c + 14);
-    const double hRT = fma(a5, sc.invT, h);
-    const double gp = fma(T, fma(T, fma(T, fma(T, __ldg(c + 12), __ldg(c + 11)), __ldg(c + 10)), __ldg(c + 9)),
-                          fma(a5, sc.invT, -a6));
-    const double g = fma(a0, 1.0 - sc.lnT, gp);
-    const double eg = exp(g);
-    const double yw = y[1 + k] * iw;
-    sig += yw;
-    cps = fma(yw, cpR, cps);
+  const Sc T = sc.T;
+  Sc sig = Sc(0.0), cps = Sc(0.0), dcps = Sc(0.0);
+  Sc* __restrict__ hRT = s + L.hRT;
+  Sc* __restrict__ egv = s + L.eg;
+  Sc* __restrict__ emg = s + L.emg;
+  Sc* __restrict__ cpv = s + L.cpR;
+  Sc* __restrict__ C = s + L.C;
+  for (int k = lane; k < M.n; k += 2 * kWarp) {
+    const bool v2 = k + kWarp < M.n;
+    const int k2 = v2 ? k + kWarp : k;
+    const SpOut<Sc> a = species_item<Sc, DERIV>(M, k, y, T, sc.lnT, sc.invT);
+    const SpOut<Sc> b = species_item<Sc, DERIV>(M, k2, y, T, sc.lnT, sc.invT);
+    const Sc ia = 1.0 / a.eg, ib = 1.0 / b.eg;
+    sig += a.yw + (v2 ? b.yw : Sc(0.0));
+    cps = sfma(a.yw, a.cpR, cps);
+    if (v2) cps = sfma(b.yw, b.cpR, cps);
     if (DERIV) {
-      const double dcp = fma(T, fma(T, __ldg(c + 17) * T + __ldg(c + 16), __ldg(c + 15)), a1);
-      dcps = fma(yw, dcp, dcps);
+      dcps = sfma(a.yw, a.dcp, dcps);
+      if (v2) dcps = sfma(b.yw, b.dcp, dcps);
     }
-    s[L.hRT + k] = hRT;
-    s[L.eg + k] = eg;
-    s[L.emg + k] = 1.0 / eg;
-    s[L.cpR + k] = cpR;
-    s[L.C + k] = yw;
+    hRT[k] = a.hRT; egv[k] = a.eg; emg[k] = ia; cpv[k] = a.cpR; C[k] = a.yw;
+    if (v2) { hRT[k2] = b.hRT; egv[k2] = b.eg; emg[k2] = ib; cpv[k2] = b.cpR; C[k2] = b.yw; }
   }
   sig = warp_sum(sig);
   cps = warp_sum(cps);
@@ -171,150 +200,184 @@ __device__ __forceinline__ Scal eval_species(const MechView& M, double* s, const
   sc.dcps = dcps;
   sc.rtp = kRu * T * (1.0 / kP0);
   sc.irtp = 1.0 / sc.rtp;
-  for (int k = lane; k < M.n; k += kWarp) s[L.C + k] *= sc.rho;
+  __syncwarp();
+  for (int k = lane; k < M.n; k += kWarp) C[k] *= sc.rho;
   __syncwarp();
   return sc;
 }
 
 // -------------------------------------------------------------------------------------- reactions
-// Rates of progress q (and, with DERIV, dq/dT at fixed C and the derivative slots dq/dC_j).
-template <bool DERIV>
-__device__ __forceinline__ void eval_reactions(const MechView& M, double* s, const CellLayout& L, const Scal& sc,
-                                               int lane) {
-  const double* C = s + L.C;
-  const double* eg = s + L.eg;
-  const double* emg = s + L.emg;
-  const double* hRT = s + L.hRT;
-  for (int r = lane; r < M.R; r += kWarp) {
-    const int* I = M.rxi + (size_t)r * RX_I;
-    const double* D = M.rxd + (size_t)r * RX_D;
-    const int type = __ldg(I), rev = __ldg(I + 1), nro = __ldg(I + 2), npo = __ldg(I + 3);
-    const int r0 = __ldg(I + 4), r1 = __ldg(I + 5), r2 = __ldg(I + 6);
-    const int p0 = __ldg(I + 7), p1 = __ldg(I + 8), p2 = __ldg(I + 9);
-    const double lnA = __ldg(D), bb = __ldg(D + 1), Ta = __ldg(D + 2);
-    const double lnkinf = fma(-Ta, sc.invT, fma(bb, sc.lnT, lnA));
-    double kf = exp(lnkinf);
-    // concentration products and the partial products without one occurrence
-    const double cr0 = C[r0], cr1 = nro > 1 ? C[r1] : 1.0, cr2 = nro > 2 ? C[r2] : 1.0;
-    const double cp0 = C[p0], cp1 = npo > 1 ? C[p1] : 1.0, cp2 = npo > 2 ? C[p2] : 1.0;
-    const double Pf = cr0 * cr1 * cr2, Pb = cp0 * cp1 * cp2;
-    // third-body concentration: total concentration plus listed corrections
-    double Mv = sc.ctot;
-    if (type != 0) {
-      const int eo = __ldg(I + 11), ec = __ldg(I + 12);
-      for (int i = 0; i < ec; ++i) Mv = fma(__ldg(M.eff_am1 + eo + i), C[__ldg(M.eff_sp + eo + i)], Mv);
-    }
-    double dlnkf_dT = 0.0, dlnk_dlnM = 0.0, iM = 0.0;
-    if (DERIV) dlnkf_dT = fma(Ta, sc.invT, bb) * sc.invT;
-    if (type == 2) {
-      // Troe fall-off: Pr = k0 [M] / k_inf, F from the broadening function of F_cent
-      const double lnk0 = fma(-__ldg(D + 5), sc.invT, fma(__ldg(D + 4), sc.lnT, __ldg(D + 3)));
-      const double lnM = log(Mv);
-      const double lnPr = lnk0 - lnkinf + lnM;
-      const double Pr = exp(lnPr);
-      const double e3 = exp(-sc.T * __ldg(D + 8)), e1 = exp(-sc.T * __ldg(D + 9));
-      const double T2 = __ldg(D + 10);
-      const double e2 = T2 > 0.0 ? exp(-T2 * sc.invT) : 0.0;
-      const double Fc = fma(__ldg(D + 6), e3, fma(__ldg(D + 7), e1, e2));
-      const double Lc = log(Fc) * kInvLn10;
-      const double cc = fma(-0.67, Lc, -0.4);
-      const double nn = fma(-1.27, Lc, 0.75);
-      const double x = fma(lnPr, kInvLn10, cc);
-      const double den = fma(-0.14, x, nn);
-      const double iden = 1.0 / den;
-      const double f1 = x * iden;
-      const double ib = 1.0 / fma(f1, f1, 1.0);
-      const double log10F = Lc * ib;
-      const double F = exp(log10F * kLn10);
-      const double ipr1 = 1.0 / (1.0 + Pr);
-      kf = kf * (Pr * ipr1) * F;
-      if (DERIV) {
-        const double dlnk0_dT = fma(__ldg(D + 5), sc.invT, __ldg(D + 4)) * sc.invT;
-        const double dlnPr_dT = dlnk0_dT - dlnkf_dT;
-        const double dFc_dT = -__ldg(D + 6) * __ldg(D + 8) * e3 - __ldg(D + 7) * __ldg(D + 9) * e1 +
-                              T2 * sc.invT * sc.invT * e2;
-        const double dLc_dT = dFc_dT / Fc * kInvLn10;
-        const double dx_dT = fma(dlnPr_dT, kInvLn10, -0.67 * dLc_dT);
-        const double dnn_dT = -1.27 * dLc_dT;
-        const double df1_dT = (dx_dT * nn - x * dnn_dT) * iden * iden;
-        const double dlog10F_dT = fma(dLc_dT, ib, -2.0 * Lc * f1 * df1_dT * ib * ib);
-        dlnkf_dT = dlnkf_dT + dlnPr_dT * ipr1 + kLn10 * dlog10F_dT;
-        const double df1_dlnM = nn * kInvLn10 * iden * iden;
-        dlnk_dlnM = ipr1 - kLn10 * 2.0 * Lc * f1 * df1_dlnM * ib * ib;
-        iM = exp(-lnM);
-      }
-    }
-    // reverse rate: k_r = k_f * prod exp(g)^nu_products * prod exp(-g)^nu_reactants * (Ru T/p0)^sum(nu)
-    double kr = 0.0, dlnKc_dT = 0.0;
-    if (rev) {
-      double ik = eg[p0] * emg[r0];
-      if (npo > 1) ik *= eg[p1];
-      if (npo > 2) ik *= eg[p2];
-      if (nro > 1) ik *= emg[r1];
-      if (nro > 2) ik *= emg[r2];
-      const int dn = npo - nro;
-      if (dn > 0) { ik *= sc.rtp; if (dn > 1) ik *= sc.rtp; if (dn > 2) ik *= sc.rtp; }
-      if (dn < 0) { ik *= sc.irtp; if (dn < -1) ik *= sc.irtp; if (dn < -2) ik *= sc.irtp; }
-      kr = kf * ik;
-      if (DERIV) {
-        double sh = hRT[p0] - hRT[r0];
-        if (npo > 1) sh += hRT[p1];
-        if (npo > 2) sh += hRT[p2];
-        if (nro > 1) sh -= hRT[r1];
-        if (nro > 2) sh -= hRT[r2];
-        dlnKc_dT = (sh - (double)dn) * sc.invT;
-      }
-    }
-    const double Mfac = (type == 1) ? Mv : 1.0;
-    const double qn = fma(kf, Pf, -kr * Pb);
-    const double q = Mfac * qn;
-    s[L.q + r] = q;
+// Per-reaction quantities of the rate evaluation that the derivative part needs afterwards.
+template <class Sc>
+struct RxCore {
+  Sc q, qn, kf, kr, Mfac, dlnkf_dT, dlnKc_dT, dlnk_dlnM, iM;
+  Sc cr0, cr1, cr2, cp0, cp1, cp2;
+  int so, scn;
+};
+
+// Rate of progress of reaction r, specialised on the reaction type (0 elementary, 1 third-body,
+// 2 Troe).  Branch-free in the participant counts: absent occurrences read index 0 and count as 1.
+template <class Sc, int TYPE, bool DERIV>
+__device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc* __restrict__ C,
+                                              const Sc* __restrict__ eg, const Sc* __restrict__ emg,
+                                              const Sc* __restrict__ hRT, const ScalT<Sc>& sc) {
+  const int* I = M.rxi + (size_t)r * RX_I;
+  const double* D = M.rxd + (size_t)r * RX_D;
+  const int rev = __ldg(I + 1), nro = __ldg(I + 2), npo = __ldg(I + 3);
+  const int r0 = __ldg(I + 4), r1 = max(__ldg(I + 5), 0), r2 = max(__ldg(I + 6), 0);
+  const int p0 = __ldg(I + 7), p1 = max(__ldg(I + 8), 0), p2 = max(__ldg(I + 9), 0);
+  const Sc lnA = __ldg(D), bb = __ldg(D + 1), Ta = __ldg(D + 2);
+  RxCore<Sc> x;
+  const Sc lnkinf = sfma(-Ta, sc.invT, sfma(bb, sc.lnT, lnA));
+  Sc kf = sexp(lnkinf);
+  x.cr0 = C[r0]; x.cr1 = nro > 1 ? C[r1] : Sc(1.0); x.cr2 = nro > 2 ? C[r2] : Sc(1.0);
+  x.cp0 = C[p0]; x.cp1 = npo > 1 ? C[p1] : Sc(1.0); x.cp2 = npo > 2 ? C[p2] : Sc(1.0);
+  const Sc Pf = x.cr0 * x.cr1 * x.cr2, Pb = x.cp0 * x.cp1 * x.cp2;
+  Sc Mv = sc.ctot;
+  if (TYPE != 0) {
+    const int eo = __ldg(I + 11), ec = __ldg(I + 12);
+    for (int i = 0; i < ec; ++i) Mv = sfma(Sc(__ldg(M.eff_am1 + eo + i)), C[__ldg(M.eff_sp + eo + i)], Mv);
+  }
+  x.dlnkf_dT = DERIV ? sfma(Ta, sc.invT, bb) * sc.invT : Sc(0.0);
+  x.dlnk_dlnM = Sc(0.0);
+  x.iM = Sc(0.0);
+  if (TYPE == 2) {
+    const Sc lnk0 = sfma(-Sc(__ldg(D + 5)), sc.invT, sfma(Sc(__ldg(D + 4)), sc.lnT, Sc(__ldg(D + 3))));
+    const Sc lnM = slog(Mv);
+    const Sc lnPr = lnk0 - lnkinf + lnM;
+    const Sc Pr = sexp(lnPr);
+    const Sc e3 = sexp(-sc.T * __ldg(D + 8)), e1 = sexp(-sc.T * __ldg(D + 9));
+    const double T2 = __ldg(D + 10);
+    const Sc e2 = T2 > 0.0 ? sexp(-T2 * sc.invT) : Sc(0.0);
+    const Sc Fc = sfma(Sc(__ldg(D + 6)), e3, sfma(Sc(__ldg(D + 7)), e1, e2));
+    const Sc Lc = slog(Fc) * kInvLn10;
+    const Sc cc = sfma(Sc(-0.67), Lc, Sc(-0.4));
+    const Sc nn = sfma(Sc(-1.27), Lc, Sc(0.75));
+    const Sc xx = sfma(lnPr, Sc(kInvLn10), cc);
+    const Sc den = sfma(Sc(-0.14), xx, nn);
+    const Sc iden = 1.0 / den;
+    const Sc f1 = xx * iden;
+    const Sc ib = 1.0 / sfma(f1, f1, Sc(1.0));
+    const Sc F = sexp(Lc * ib * kLn10);
+    const Sc ipr1 = 1.0 / (1.0 + Pr);
+    kf = kf * (Pr * ipr1) * F;
     if (DERIV) {
-      const double kfM = kf * Mfac, krM = kr * Mfac;
-      const double qf = kfM * Pf, qr = krM * Pb;
-      double dqdM = 0.0;
-      if (type == 1) dqdM = qn;
-      else if (type == 2) dqdM = dlnk_dlnM * q * iM;
-      // dq/dT at fixed C; [M] depends on T through the total concentration p/(Ru T)
-      const double dqdT = fma(dlnkf_dT, qf, -(dlnkf_dT - dlnKc_dT) * qr) - dqdM * sc.ctot * sc.invT;
-      s[L.dqdT + r] = dqdT;
-      // partial products: d(prod)/d(occurrence i) = product of the other occurrences
-      const double dr0 = cr1 * cr2, dr1 = cr0 * cr2, dr2 = cr0 * cr1;
-      const double dp0 = cp1 * cp2, dp1 = cp0 * cp2, dp2 = cp0 * cp1;
-      const int so = __ldg(I + 13), scn = __ldg(I + 14);
-      for (int i = 0; i < scn; ++i) {
-        const int mask = __ldg(M.dslot_mask + so + i);
-        double v = __ldg(M.dslot_am1 + so + i) * dqdM;
-        double fr = 0.0, fp = 0.0;
-        if (mask & 1) fr += dr0;
-        if (mask & 2) fr += dr1;
-        if (mask & 4) fr += dr2;
-        if (mask & 8) fp += dp0;
-        if (mask & 16) fp += dp1;
-        if (mask & 32) fp += dp2;
-        v = fma(kfM, fr, v);
-        v = fma(-krM, fp, v);
-        s[L.D + so + i] = v;
-      }
+      const Sc dlnk0_dT = sfma(Sc(__ldg(D + 5)), sc.invT, Sc(__ldg(D + 4))) * sc.invT;
+      const Sc dlnPr_dT = dlnk0_dT - x.dlnkf_dT;
+      const Sc dFc_dT = -(__ldg(D + 6) * __ldg(D + 8)) * e3 - (__ldg(D + 7) * __ldg(D + 9)) * e1 +
+                        T2 * sc.invT * sc.invT * e2;
+      const Sc dLc_dT = dFc_dT / Fc * kInvLn10;
+      const Sc dx_dT = sfma(dlnPr_dT, Sc(kInvLn10), -0.67 * dLc_dT);
+      const Sc dnn_dT = -1.27 * dLc_dT;
+      const Sc df1_dT = (dx_dT * nn - xx * dnn_dT) * iden * iden;
+      const Sc dlog10F_dT = sfma(dLc_dT, ib, -2.0 * Lc * f1 * df1_dT * ib * ib);
+      x.dlnkf_dT = x.dlnkf_dT + dlnPr_dT * ipr1 + kLn10 * dlog10F_dT;
+      const Sc df1_dlnM = nn * kInvLn10 * iden * iden;
+      x.dlnk_dlnM = ipr1 - kLn10 * 2.0 * Lc * f1 * df1_dlnM * ib * ib;
+      x.iM = sexp(-lnM);
     }
+  }
+  // reverse rate: k_r = k_f * prod exp(g)^nu'' * prod exp(-g)^nu' * (Ru T/p0)^(sum nu)
+  const int dn = npo - nro;
+  Sc ik = eg[p0] * emg[r0];
+  ik *= (npo > 1 ? eg[p1] : Sc(1.0)) * (npo > 2 ? eg[p2] : Sc(1.0));
+  ik *= (nro > 1 ? emg[r1] : Sc(1.0)) * (nro > 2 ? emg[r2] : Sc(1.0));
+  const Sc fp = dn > 0 ? sc.rtp : sc.irtp;
+  const int adn = dn < 0 ? -dn : dn;
+  ik *= (adn >= 1 ? fp : Sc(1.0)) * (adn >= 2 ? fp : Sc(1.0)) * (adn >= 3 ? fp : Sc(1.0));
+  x.kr = rev ? kf * ik : Sc(0.0);
+  x.kf = kf;
+  if (DERIV) {
+    Sc sh = hRT[p0] - hRT[r0];
+    sh += (npo > 1 ? hRT[p1] : Sc(0.0)) + (npo > 2 ? hRT[p2] : Sc(0.0));
+    sh -= (nro > 1 ? hRT[r1] : Sc(0.0)) + (nro > 2 ? hRT[r2] : Sc(0.0));
+    const double dnd = dn == 0 ? 0.0 : dn == 1 ? 1.0 : dn == -1 ? -1.0 : dn == 2 ? 2.0 : dn == -2 ? -2.0 :
+                       dn == 3 ? 3.0 : -3.0;
+    x.dlnKc_dT = rev ? (sh - dnd) * sc.invT : Sc(0.0);
+  } else {
+    x.dlnKc_dT = Sc(0.0);
+  }
+  x.Mfac = (TYPE == 1) ? Mv : Sc(1.0);
+  x.qn = sfma(kf, Pf, -(x.kr * Pb));
+  x.q = x.Mfac * x.qn;
+  x.so = DERIV ? __ldg(I + 13) : 0;
+  x.scn = DERIV ? __ldg(I + 14) : 0;
+  return x;
+}
+
+// Store q (and with DERIV: dq/dT at fixed C, and the derivative slots dq/dC_j) of reaction r.
+template <class Sc, int TYPE, bool DERIV>
+__device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<Sc>& x, Sc* s, const CellLayout& L,
+                                         const ScalT<Sc>& sc, bool valid) {
+  if (!valid) return;
+  s[L.q + r] = x.q;
+  if (!DERIV) return;
+  const Sc kfM = x.kf * x.Mfac, krM = x.kr * x.Mfac;
+  const Sc qf = kfM * x.cr0 * x.cr1 * x.cr2, qr = krM * x.cp0 * x.cp1 * x.cp2;
+  Sc dqdM = Sc(0.0);
+  if (TYPE == 1) dqdM = x.qn;
+  if (TYPE == 2) dqdM = x.dlnk_dlnM * x.q * x.iM;
+  // [M] depends on T through the total concentration p/(Ru T)
+  s[L.dqdT + r] = sfma(x.dlnkf_dT, qf, -((x.dlnkf_dT - x.dlnKc_dT) * qr)) - dqdM * sc.ctot * sc.invT;
+  // partial products: d(prod)/d(occurrence i) = product of the other occurrences
+  const Sc dr0 = x.cr1 * x.cr2, dr1 = x.cr0 * x.cr2, dr2 = x.cr0 * x.cr1;
+  const Sc dp0 = x.cp1 * x.cp2, dp1 = x.cp0 * x.cp2, dp2 = x.cp0 * x.cp1;
+  for (int i = 0; i < x.scn; ++i) {
+    const int mask = __ldg(M.dslot_mask + x.so + i);
+    Sc v = __ldg(M.dslot_am1 + x.so + i) * dqdM;
+    Sc fr = Sc(0.0), fq = Sc(0.0);
+    if (mask & 1) fr += dr0;
+    if (mask & 2) fr += dr1;
+    if (mask & 4) fr += dr2;
+    if (mask & 8) fq += dp0;
+    if (mask & 16) fq += dp1;
+    if (mask & 32) fq += dp2;
+    v = sfma(kfM, fr, v);
+    v = sfma(-krM, fq, v);
+    s[L.D + x.so + i] = v;
+  }
+}
+
+// Rates of progress of all reactions.  Reactions are ordered Troe, third-body, elementary, so every
+// segment has warp-uniform control flow; elementary reactions go two per lane (two exp chains).
+template <class Sc, bool DERIV>
+__device__ __forceinline__ void eval_reactions(const MechView& M, Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
+                                               int lane) {
+  const Sc* C = s + L.C;
+  const Sc* eg = s + L.eg;
+  const Sc* emg = s + L.emg;
+  const Sc* hRT = s + L.hRT;
+  const int e0 = M.n_troe + M.n_tb;
+  for (int r = lane; r < M.n_troe; r += kWarp)
+    rx_store<Sc, 2, DERIV>(M, r, rx_core<Sc, 2, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true);
+  for (int r = M.n_troe + lane; r < e0; r += kWarp)
+    rx_store<Sc, 1, DERIV>(M, r, rx_core<Sc, 1, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true);
+  for (int r = e0 + lane; r < M.R; r += 2 * kWarp) {
+    const bool v2 = r + kWarp < M.R;
+    const int r2 = v2 ? r + kWarp : r;
+    const RxCore<Sc> a = rx_core<Sc, 0, DERIV>(M, r, C, eg, emg, hRT, sc);
+    const RxCore<Sc> b = rx_core<Sc, 0, DERIV>(M, r2, C, eg, emg, hRT, sc);
+    rx_store<Sc, 0, DERIV>(M, r, a, s, L, sc, true);
+    rx_store<Sc, 0, DERIV>(M, r2, b, s, L, sc, v2);
   }
   __syncwarp();
 }
 
 // -------------------------------------------------------------------------------------- f and J
 // f(y) into out[m].  Uses C/hRT/eg/emg/cpR/q scratch.  Returns the scalars of the evaluation.
-__device__ __forceinline__ Scal eval_f(const MechView& M, double* s, const CellLayout& L, const double* y, double p,
-                                       double* out, int lane) {
-  Scal sc = eval_species<false>(M, s, L, y, p, lane);
-  eval_reactions<false>(M, s, L, sc, lane);
-  const double* q = s + L.q;
-  double* part = s + L.part;
-  double* w = out + 1;   // production rates written in place, then scaled
-  run_gather(M.g_omega, w, part, [&](int a, int b) { return (double)(int16_t)b * q[a]; }, lane);
-  double Qs = 0.0;
+template <class Sc>
+__device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
+                                            Sc* out, int lane) {
+  ScalT<Sc> sc = eval_species<Sc, false>(M, s, L, y, p, lane);
+  eval_reactions<Sc, false>(M, s, L, sc, lane);
+  const Sc* q = s + L.q;
+  Sc* part = s + L.part;
+  Sc* w = out + 1;   // production rates written in place, then scaled
+  run_gather(M.g_omega, w, part, [&](int a, int b) { return nu_of(b) * q[a]; }, lane);
+  Sc Qs = Sc(0.0);
   for (int k = lane; k < M.n; k += kWarp) {
-    const double om = w[k];
-    Qs = fma(s[L.hRT + k], om, Qs);
+    const Sc om = w[k];
+    Qs = sfma(s[L.hRT + k], om, Qs);
     w[k] = om * __ldg(M.sp + (size_t)k * SP_STRIDE + 1) * sc.irho;
   }
   Qs = warp_sum(Qs);
@@ -325,62 +388,64 @@ __device__ __forceinline__ Scal eval_f(const MechView& M, double* s, const CellL
 
 // f(y) into f0[m], S[nnz_S] (internal order), u[m], v[m].  Scratch: C.., q, dqdT, D, x (w), z (w_T),
 // U1 (g), U2 (t).
-__device__ __forceinline__ void eval_jac(const MechView& M, double* s, const CellLayout& L, const double* y, double p,
-                                         int lane) {
-  Scal sc = eval_species<true>(M, s, L, y, p, lane);
-  eval_reactions<true>(M, s, L, sc, lane);
-  double* part = s + L.part;
-  double* w = s + L.x;      // w_k
-  double* wT = s + L.z;     // w_T,k
-  double* gk = s + L.U1;
-  double* tk = s + L.U2;
-  double* S = s + L.S;
-  const double* C = s + L.C;
-  const double* hRT = s + L.hRT;
-  const double* Dsl = s + L.D;
+template <class Sc>
+__device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
+                                              int lane) {
+  ScalT<Sc> sc = eval_species<Sc, true>(M, s, L, y, p, lane);
+  eval_reactions<Sc, true>(M, s, L, sc, lane);
+  Sc* part = s + L.part;
+  Sc* w = s + L.x;      // w_k
+  Sc* wT = s + L.z;     // w_T,k
+  Sc* gk = s + L.U1;
+  Sc* tk = s + L.U2;
+  Sc* S = s + L.S;
+  const Sc* C = s + L.C;
+  const Sc* hRT = s + L.hRT;
+  const Sc* Dsl = s + L.D;
   run_gather2(M.g_omega, w, wT, part, s + L.q, s + L.dqdT, lane);
-  run_gather(M.g_dtil, S, part, [&](int a, int b) { return (double)(int16_t)b * Dsl[a]; }, lane);
+  run_gather(M.g_dtil, S, part, [&](int a, int b) { return nu_of(b) * Dsl[a]; }, lane);
   run_gather(M.g_row, gk, part, [&](int a, int b) { return S[a] * C[b]; }, lane);
   run_gather(M.g_col, tk, part, [&](int a, int b) { return S[a] * hRT[b]; }, lane);
-  double* f = s + L.f0;
-  double* u = s + L.u;
-  double* v = s + L.v;
-  const double T = sc.T;
+  Sc* f = s + L.f0;
+  Sc* u = s + L.u;
+  Sc* v = s + L.v;
+  const Sc T = sc.T;
   // f, u and the T column; partial sums for the T row scalars
-  double Qs = 0.0, A1 = 0.0, A2 = 0.0;
+  Sc Qs = Sc(0.0), A1 = Sc(0.0), A2 = Sc(0.0);
   for (int k = lane; k < M.n; k += kWarp) {
     const double Wk = __ldg(M.sp + (size_t)k * SP_STRIDE + 1);
-    const double om = w[k], g = gk[k];
-    const double fk = Wk * om * sc.irho;
+    const Sc om = w[k], g = gk[k];
+    const Sc fk = Wk * om * sc.irho;
     f[1 + k] = fk;
     u[1 + k] = Wk * sc.irho * (om - g);
-    S[M.nY + k] = fma(Wk * sc.irho, fma(-g, sc.invT, wT[k]), fk * sc.invT);
+    S[M.nY + k] = sfma(Wk * sc.irho, sfma(-g, sc.invT, wT[k]), fk * sc.invT);
     v[1 + k] = sc.Wbar * __ldg(M.sp + (size_t)k * SP_STRIDE);
-    const double h = hRT[k];
-    Qs = fma(h, om, Qs);
-    A1 = fma(s[L.cpR + k], om, fma(T * h, fma(-g, sc.invT, wT[k]), A1));
-    A2 = fma(h, g, A2);
+    const Sc h = hRT[k];
+    Qs = sfma(h, om, Qs);
+    A1 = sfma(s[L.cpR + k], om, sfma(T * h, sfma(-g, sc.invT, wT[k]), A1));
+    A2 = sfma(h, g, A2);
   }
   Qs = warp_sum(Qs);
   A1 = warp_sum(A1);
   A2 = warp_sum(A2);
-  const double rcp = sc.rho * sc.cp;
-  const double fT = -kRu * T * Qs / rcp;
+  const Sc rcp = sc.rho * sc.cp;
+  const Sc fT = -kRu * T * Qs / rcp;
   // T row: S_Tj for species j, then S_TT; u_T; v_T
   for (int j = lane; j < M.n; j += kWarp) {
     const double iw = __ldg(M.sp + (size_t)j * SP_STRIDE);
-    S[M.nY + M.n + 1 + j] = -kRu * fma(T, tk[j], fT * s[L.cpR + j]) * iw / sc.cp;
+    S[M.nY + M.n + 1 + j] = -kRu * sfma(T, tk[j], fT * s[L.cpR + j]) * iw / sc.cp;
   }
   if (lane == 0) {
     f[0] = fT;
     S[M.nY + M.n] = -kRu * A1 / rcp + fT * (sc.invT - kRu * sc.dcps / sc.cp);
     u[0] = kRu * T * A2 / rcp + fT;
-    v[0] = 0.0;
+    v[0] = Sc(0.0);
   }
   __syncwarp();
   // species block: S_kj = (W_k / W_j) Dtil_kj (after the row and column sums used Dtil)
   for (int e = lane; e < M.nY; e += kWarp) S[e] *= __ldg(M.entry_wratio + e);
   __syncwarp();
+  return sc;
 }
 
 // -------------------------------------------------------------------------------------- linear algebra
@@ -400,11 +465,13 @@ __device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, co
   __syncwarp();
   bool ok = true;
   const ElimOp* op = M.lu_ops + lane;
-  ElimOp nx = M.lu_steps > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, 0};
-  for (int st = 0; st < M.lu_steps; ++st) {
-    const ElimOp o = nx;
-    op += kWarp;
-    if (st + 1 < M.lu_steps) nx = ld_eop(op);
+  const int NS = M.lu_steps;
+  ElimOp n1 = NS > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, 0};
+  ElimOp n2 = NS > 1 ? ld_eop(op + kWarp) : ElimOp{OP_IDLE, 0, 0, 0};
+  for (int st = 0; st < NS; ++st) {
+    const ElimOp o = n1;
+    n1 = n2;
+    if (st + 2 < NS) n2 = ld_eop(op + (size_t)(st + 2) * kWarp);
     const int kind = __ldg(M.lu_kind + st);
     if (o.t != OP_IDLE) {
       if (kind == K_UPDATE) {
@@ -423,24 +490,40 @@ __device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, co
   return __all_sync(0xffffffffu, ok);
 }
 
-// x <- A^{-1} x (forward and backward substitution by the precomputed program; state-order vector)
-__device__ __forceinline__ void lu_solve(const MechView& M, const double* s, const CellLayout& L, double* x,
-                                         int lane) {
+// x <- A^{-1} x (forward and backward substitution by the precomputed program; state-order vector).
+// With x2 != nullptr the same program solves a second right-hand side in the same steps.
+template <bool TWO>
+__device__ __forceinline__ void lu_solve_impl(const MechView& M, const double* s, const CellLayout& L, double* x,
+                                              double* x2, int lane) {
   const double* LU = s + L.LU;
   const double* dinv = s + L.dinv;
   const ElimOp* op = M.sv_ops + lane;
-  ElimOp nx = M.sv_steps > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, 0};
-  for (int st = 0; st < M.sv_steps; ++st) {
-    const ElimOp o = nx;
-    op += kWarp;
-    if (st + 1 < M.sv_steps) nx = ld_eop(op);
+  const int S = M.sv_steps;
+  ElimOp n1 = S > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, 0};
+  ElimOp n2 = S > 1 ? ld_eop(op + kWarp) : ElimOp{OP_IDLE, 0, 0, 0};
+  for (int st = 0; st < S; ++st) {
+    const ElimOp o = n1;
+    n1 = n2;
+    if (st + 2 < S) n2 = ld_eop(op + (size_t)(st + 2) * kWarp);
     const int kind = __ldg(M.sv_kind + st);
     if (o.t != OP_IDLE) {
-      if (kind == K_UPDATE) x[o.t] = fma(-LU[o.a], x[o.b], x[o.t]);
-      else x[o.t] *= dinv[o.a];
+      if (kind == K_UPDATE) {
+        const double l = LU[o.a];
+        x[o.t] = fma(-l, x[o.b], x[o.t]);
+        if (TWO) x2[o.t] = fma(-l, x2[o.b], x2[o.t]);
+      } else {
+        const double d = dinv[o.a];
+        x[o.t] *= d;
+        if (TWO) x2[o.t] *= d;
+      }
     }
     __syncwarp();
   }
+}
+
+__device__ __forceinline__ void lu_solve(const MechView& M, const double* s, const CellLayout& L, double* x,
+                                         int lane) {
+  lu_solve_impl<false>(M, s, L, x, nullptr, lane);
 }
 
 // x <- M^{-1} x with M = A - u v^T:  x = A^-1 x + z (v . A^-1 x) / (1 - v . z),  z = A^-1 u
@@ -480,20 +563,21 @@ __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, con
   double* z = s + L.z;
   const double* u = s + L.u;
   const double* v = s + L.v;
-  // z = A^-1 u and the Sherman-Morrison denominator
-  for (int i = lane; i < m; i += kWarp) z[i] = u[i];
+  // z = A^-1 u (the Sherman-Morrison vector) and stage 1's A^-1 f0, in one pass of the solve program
+  for (int i = lane; i < m; i += kWarp) { z[i] = u[i]; U1[i] = f0[i]; }
   __syncwarp();
-  lu_solve(M, s, L, z, lane);
-  double vz = 0.0;
-  for (int i = lane; i < m; i += kWarp) vz = fma(v[i], z[i], vz);
+  lu_solve_impl<true>(M, s, L, z, U1, lane);
+  double vz = 0.0, vx = 0.0;
+  for (int i = lane; i < m; i += kWarp) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
   vz = warp_sum(vz);
+  vx = warp_sum(vx);
   const double den = 1.0 - vz;
   if (!(den != 0.0) || !isfinite(den)) return so;
   const double iden = 1.0 / den;
-  // stage 1
-  for (int i = lane; i < m; i += kWarp) U1[i] = f0[i];
+  // stage 1: Sherman-Morrison correction of A^-1 f0
+  vx *= iden;
+  for (int i = lane; i < m; i += kWarp) U1[i] = fma(z[i], vx, U1[i]);
   __syncwarp();
-  sm_solve(M, s, L, U1, iden, lane);
   // stage 2 (a21 = 0: f(y) again)
   for (int i = lane; i < m; i += kWarp) U2[i] = fma(C21 * ih, U1[i], f0[i]);
   __syncwarp();
@@ -501,14 +585,14 @@ __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, con
   // stage 3
   for (int i = lane; i < m; i += kWarp) yt[i] = fma(A31, U1[i], y[i]);
   __syncwarp();
-  eval_f(M, s, L, yt, p, U3, lane);
+  eval_f<double>(M, s, L, yt, p, U3, lane);
   for (int i = lane; i < m; i += kWarp) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
   __syncwarp();
   sm_solve(M, s, L, U3, iden, lane);
   // stage 4
   for (int i = lane; i < m; i += kWarp) yt[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
   __syncwarp();
-  eval_f(M, s, L, yt, p, U4, lane);
+  eval_f<double>(M, s, L, yt, p, U4, lane);
   for (int i = lane; i < m; i += kWarp) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
   __syncwarp();
   sm_solve(M, s, L, U4, iden, lane);
@@ -538,6 +622,13 @@ struct IntOpts {
   double* trace;                    // optional step trace (see chem_integrate_opts)
   int trace_cap;
   int N;
+  // optional tape for the discrete adjoint: accepted step sizes rec_h[i*N + c] (i < rec_cap) and
+  // checkpoints rec_ck[(j*m + l)*N + c] = state component l after j*rec_K accepted steps; rec_n[c] is the
+  // number of accepted steps, or -1 when the tape overflowed
+  double* rec_h;
+  double* rec_ck;
+  int* rec_n;
+  int rec_cap, rec_K;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -564,12 +655,18 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
   ok = __all_sync(0xffffffffu, ok) && sig > 0.0;
   nsub = 0;
   nacc = 0;
-  if (!ok) { status = CHEM_CELL_BADINPUT; return; }
+  if (!ok) {
+    status = CHEM_CELL_BADINPUT;
+    if (o.rec_h && lane == 0) o.rec_n[cell] = -1;
+    return;
+  }
   double h = (h_io > 0.0 && isfinite(h_io)) ? h_io : o.h_init;
   if (dt > 0.0) h = fmin(h, dt);
   double t = 0.0;
   bool rejected_last = false, needJ = true;
   int nonfinite = 0, ns = 0, na = 0, st = CHEM_CELL_OK;
+  if (o.rec_h)
+    for (int i = lane; i < m; i += kWarp) o.rec_ck[(size_t)i * o.N + cell] = y[i];
   while (t < dt) {
     if (ns >= o.max_substeps) { st = CHEM_CELL_MAXSTEPS; break; }
     if (o.deadline_ns) {
@@ -582,7 +679,7 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
     if (hu < o.h_min) { st = CHEM_CELL_HMIN; break; }
     ++ns;
     if (needJ) {
-      eval_jac(M, s, L, y, p, lane);
+      eval_jac<double>(M, s, L, y, p, lane);
       needJ = false;
     }
     const StepOut so = ros_attempt(M, s, L, p, hu, o.rtol, o.atol, lane);
@@ -602,6 +699,11 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       const double* yt = s + L.ytmp;
       for (int i = lane; i < m; i += kWarp) y[i] = yt[i];
       __syncwarp();
+      if (o.rec_h && na <= o.rec_cap) {
+        if (lane == 0) o.rec_h[(size_t)(na - 1) * o.N + cell] = hu;
+        if (na % o.rec_K == 0)
+          for (int i = lane; i < m; i += kWarp) o.rec_ck[((size_t)(na / o.rec_K) * m + i) * o.N + cell] = y[i];
+      }
       h = hu * fmin(rejected_last ? 1.0 : 6.0, fac);
       rejected_last = false;
       needJ = true;
@@ -611,6 +713,7 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
     }
   }
   if (o.trace && lane == 0 && ns < o.trace_cap) o.trace[(size_t)ns * o.N + cell] = 0.0;
+  if (o.rec_h && lane == 0) o.rec_n[cell] = (na <= o.rec_cap && st == CHEM_CELL_OK) ? na : -1;
   h_io = h;
   nsub = ns;
   nacc = na;

@@ -92,6 +92,10 @@ struct MechView {
   const ElimOp* sv_ops;      // forward + backward substitution program, vector indices in state order
   const uint8_t* sv_kind;
   int sv_steps;
+  const ElimOp* svT_ops;     // transposed substitution program (A^T x = b)
+  const uint8_t* svT_kind;
+  int svT_steps;
+  const int* rx_order;       // [R] compiled reaction -> description index
   const int* s_out;          // [nnz_S] position of internal S entry in the CSR output order
 };
 

@@ -94,6 +94,32 @@ def test_programs_reproduce_dense_solve(compiled):
         assert np.max(np.abs(x - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+def test_transposed_program_solves_the_transpose(compiled):
+    """The transposed substitution program applied to the same factor solves A^T x = b."""
+    m_, h = compiled
+    rng = np.random.default_rng(2)
+    S_csr = rng.standard_normal(h.info["nnz_S"])
+    S_int, S_dense = _internal_S_dense(h, S_csr)
+    gh = 3.0 * np.abs(S_dense).sum(axis=1).max()
+    A = gh * np.eye(h.m) - S_dense
+    lu_src = h.export_plan(4)
+    LU = np.where(lu_src >= 0, -S_int[np.maximum(lu_src, 0)], 0.0)
+    pat = h.export_plan(3)
+    rowptr, col = pat[: h.m + 1], pat[h.m + 1:]
+    for p in range(h.m):
+        for sl in range(rowptr[p], rowptr[p + 1]):
+            if col[sl] == p:
+                LU[sl] += gh
+    dinv = np.zeros(h.m)
+    _run_elimination(h.export_plan(0), LU, dinv)
+    for _ in range(3):
+        bvec = rng.standard_normal(h.m)
+        x = bvec.copy()
+        _run_solve(h.export_plan(6), LU, dinv, x)
+        ref = np.linalg.solve(A.T, bvec)
+        assert np.max(np.abs(x - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 def test_pattern_holds_the_sparse_part_of_the_exact_jacobian(compiled):
     """Outside the compiled pattern the oracle's exact Jacobian must be the rank-one density coupling
     u_i Wbar / W_j (the same u_i for every column of a row)."""

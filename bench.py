@@ -118,6 +118,46 @@ def cpu_baseline(m, F, budget_s=12.0):
                       f"OpenMP over cells ({t_used:.1f} s)"}
 
 
+def adjoint_bench(h, m, dev, n_cells=4096):
+    """Seconds per gradient: one chem_adjoint call (one cotangent vector, all cells, all 2R parameters) on
+    igniting cells (T0 ~ U(1000, 1400) K, p ~ logU(1, 10) atm) integrated to t = 1e-3 s; objective = final
+    T plus 5 seeded species mass fractions; checkpoints every 16 accepted steps."""
+    import torch
+    from paper_2311_14941_gb300 import synth
+    F = synth.field_igniting(m, n_cells, seed=4, dt=1e-3)
+    sel = synth.cotangent_species(m, 5, seed=4)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    N = F.n_cells
+    gT = t(np.full(N, 1e-3))
+    gYn = np.zeros((m.n_species, N))
+    gYn[sel] = 1.0
+    gY = t(gYn.reshape(-1))
+    gA = torch.zeros(h.R, dtype=torch.float64, device=dev)
+    gE = torch.zeros(h.R, dtype=torch.float64, device=dev)
+    st = torch.zeros(N, dtype=torch.int32, device=dev)
+    P, D = t(F.p), t(F.dt)
+    # warm-up on a few cells (module load, scratch growth happens on the full call below as well)
+    h.adjoint(t(F.T[:64]), P[:64].contiguous(), t(F.Y[:, :64].reshape(-1)), D[:64].contiguous(), gT[:64].contiguous(),
+              t(gYn[:, :64].reshape(-1)), gA, gE, st[:64].contiguous())
+    torch.cuda.synchronize()
+    T, Y = t(F.T), t(F.Y.reshape(-1))
+    h.adjoint(T, P, Y, D, gT, gY, gA, gE, st)   # sizes the scratch for the full batch
+    torch.cuda.synchronize()
+    T, Y = t(F.T), t(F.Y.reshape(-1))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    h.adjoint(T, P, Y, D, gT, gY, gA, gE, st)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    stat = st.cpu().numpy()
+    return {"s_per_grad": s, "cells": N, "params": 2 * h.R, "cotangent": "final T (x1e-3) + 5 seeded species",
+            "workload": "53sp/325rxn igniting cells, T0 1000-1400 K, p 1-10 atm, integrated to 1e-3 s, "
+                        "checkpoints every 16 accepted steps",
+            "cell_status": {str(k): int(v) for k, v in zip(*np.unique(stat, return_counts=True))},
+            "grad_norm": float(torch.linalg.vector_norm(torch.cat([gA, gE])).item())}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -158,6 +198,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=0, help="integrate only this many seeded-random cells (profiling)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint seconds-per-gradient measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -284,6 +325,8 @@ def main():
     ck_s = ck.summary(local)
     if ck_s:
         line["clocks"] = ck_s
+    if not args.no_adjoint and not args.cells:
+        line["adjoint"] = adjoint_bench(h, m, dev)
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(m, F)
     print(json.dumps(line))

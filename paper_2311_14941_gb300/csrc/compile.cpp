@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <numeric>
 #include <set>
@@ -412,6 +413,18 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       gr[hm.entry_row[e]].push_back({e, hm.entry_col[e]});
       gc[hm.entry_col[e]].push_back({e, hm.entry_row[e]});
     }
+    // the coefficient nu of the omega and Dtil gathers travels as the top 16 bits of the IEEE double nu
+    // (+-1, +-2, +-3 have 16 trailing zero bits in their high word), so the device rebuilds it with integer
+    // instructions only
+    auto enc = [](int nu) -> int {
+      const double d = (double)nu;
+      uint64_t bits;
+      std::memcpy(&bits, &d, 8);
+      return (int)(bits >> 48);
+    };
+    for (auto* G : {&gw, &gd})
+      for (auto& grp : *G)
+        for (auto& t : grp) t.second = enc(t.second);
     if (!build_gather(gw, hm.g_omega, err) || !build_gather(gd, hm.g_dtil, err) || !build_gather(gr, hm.g_row, err) ||
         !build_gather(gc, hm.g_col, err))
       return CHEM_EUNSUPPORTED;

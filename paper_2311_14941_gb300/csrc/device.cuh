@@ -63,12 +63,9 @@ struct ScalT {
 };
 using Scal = ScalT<double>;
 
-// Coefficients nu = -3..3 of the gather programs, looked up instead of converted (a conversion to
-// double would occupy the FP64 pipe).
-__device__ __forceinline__ double nu_of(int b) {
-  const int v = (int)(int16_t)(uint16_t)b;
-  return v == 1 ? 1.0 : v == -1 ? -1.0 : v == 2 ? 2.0 : v == -2 ? -2.0 : v == 3 ? 3.0 : v == -3 ? -3.0 : 0.0;
-}
+// Coefficient nu of the omega and Dtil gather programs: the op carries the top 16 bits of the IEEE
+// double nu (exact for +-1, +-2, +-3), rebuilt with integer instructions (no conversion on the FP64 pipe).
+__device__ __forceinline__ double nu_of(int b) { return __hiloint2double(b << 16, 0); }
 
 // -------------------------------------------------------------------------------------- gathers
 // out[g] = sum over the group's terms of val(a, b); partial sums of split groups are combined after.

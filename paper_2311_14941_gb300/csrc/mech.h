@@ -80,8 +80,8 @@ struct MechView {
   const int* entry_row;      // [nY] species k of Y-block entry
   const int* entry_col;      // [nY] species j
   const double* entry_wratio;// [nY] W_k / W_j
-  Gather g_omega;            // species <- reactions (a = reaction, b = nu as int16)
-  Gather g_dtil;             // Y entries <- derivative slots (a = slot, b = nu)
+  Gather g_omega;            // species <- reactions (a = reaction, b = top 16 bits of double(nu))
+  Gather g_dtil;             // Y entries <- derivative slots (a = slot, b = top 16 bits of double(nu))
   Gather g_row;              // species k <- sum_j Dtil_kj C_j (a = entry, b = species j)
   Gather g_col;              // species i <- sum_k h_k Dtil_ki (a = entry, b = species k)
   const int* lu_src;         // [nnz_LU] S index feeding the slot (-1: fill)

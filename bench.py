@@ -1,12 +1,19 @@
 """Benchmark: reactor-steps/s of the stiff chemistry integrator on GB300.
 
 One step = one chem_integrate call advancing every cell of the workload over its flow time step dt
-(a "reactor-step" is one cell integrated over its dt).  Default workload: the 53-species / 325-reaction
-synthetic mechanism on the 65,536-cell bimodal jet field (40 % unburnt, 60 % burnt, mixing layer),
-uniform dt = 1e-5 s, FP64, rtol 1e-6 / atol 1e-12.  Every step starts from the same initial state
-(restored by device copies inside the step).
+(a "reactor-step" is one cell integrated over its dt).  Workloads (--workload):
+  jet    (default) 53-species / 325-reaction synthetic mechanism on the 65,536-cell bimodal jet field
+         (40 % unburnt, 60 % burnt, mixing layer), uniform dt = 1e-5 s; every step starts from the same
+         initial state (restored by device copies inside the step)
+  lts    the same mechanism on 262,144 cells (70 % cold, 20 % burnt, 10 % igniting) with per-cell dt
+         log-uniform in [1e-7, 1e-3] s; consecutive steps advance the evolving field (the first, untimed,
+         seeds the substep counts that the sorted queue uses)
+  large  150-species / 1000-reaction mechanism on a 131,072-cell bimodal field, per-cell dt log-uniform
+         in [1e-6, 1e-4] s, state restored every step
+FP64, rtol 1e-6 / atol 1e-12.  The headline value is the sorted persistent queue; the plain grid is timed
+on the same steps beside it.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--mode plain|persistent] [--impl reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload jet|lts|large] [--impl reference]
 Prints one JSON line (rank 0).  With torchrun each rank integrates its own field (weak scaling).
 """
 from __future__ import annotations
@@ -25,23 +32,45 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "reactor-steps/s, 53sp/325rxn FP64 rtol1e-6: persistent vs plain; adjoint s/grad"
-NX, NY = 256, 256
-DT = 1e-5
 RTOL, ATOL = 1e-6, 1e-12
 
+WORKLOADS = {
+    "jet": {"workload": "methane-sized 53sp/325rxn, 65536-cell bimodal jet field (40% unburnt 300-600 K, "
+                        "60% burnt 1600-2200 K, tanh mixing layer), uniform dt=1e-5 s",
+            "n_cells": 65536, "evolving": False},
+    "lts": {"workload": "methane-sized 53sp/325rxn, 262144-cell LTS mix (70% cold 300-600 K, 20% burnt "
+                        "1600-2200 K, 10% igniting 1000-1300 K), per-cell dt log-uniform 1e-7..1e-3 s, "
+                        "evolving field over consecutive steps",
+            "n_cells": 262144, "evolving": True},
+    "large": {"workload": "large 150sp/1000rxn, 131072-cell bimodal jet field (512x256), per-cell dt "
+                          "log-uniform 1e-6..1e-4 s",
+              "n_cells": 131072, "evolving": False},
+}
 
-def workload(seed_offset=0):
+
+def workload(name="jet", seed_offset=0):
     from paper_2311_14941_gb300 import synth
-    m = synth.mechanism_methane_sized()
-    F = synth.field_bimodal_jet(m, NX, NY, seed=2 + seed_offset, dt=DT)
+    if name == "jet":
+        m = synth.mechanism_methane_sized()
+        F = synth.field_bimodal_jet(m, 256, 256, seed=2 + seed_offset, dt=1e-5)
+    elif name == "lts":
+        m = synth.mechanism_methane_sized()
+        F = synth.field_lts_mix(m, 262144, seed=3 + seed_offset)
+    elif name == "large":
+        m = synth.mechanism_large()
+        F = synth.field_bimodal_jet(m, 512, 256, seed=5 + seed_offset, dt_range=(1e-6, 1e-4))
+    else:
+        raise ValueError(name)
     return m, F
 
 
-def config(mode):
-    return {"workload": "methane-sized 53sp/325rxn, 65536-cell bimodal jet field (40% unburnt 300-600 K, "
-                        "60% burnt 1600-2200 K, tanh mixing layer), uniform dt=1e-5 s",
-            "n_cells": NX * NY, "dt_s": DT, "rtol": RTOL, "atol": ATOL, "mode": mode,
-            "l2": "flushed between timed steps (256 MiB write)", "state": "restored to the same initial field each step"}
+def config(name, mode):
+    w = WORKLOADS[name]
+    c = {"workload": w["workload"], "n_cells": w["n_cells"], "rtol": RTOL, "atol": ATOL, "mode": mode,
+         "l2": "flushed between timed steps (256 MiB write)"}
+    c["state"] = ("advanced from step to step (evolving field)" if w["evolving"]
+                  else "restored to the same initial field each step")
+    return c
 
 
 class Clocks:
@@ -96,7 +125,7 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(m, F, budget_s=12.0):
+def cpu_baseline(m, F, name, budget_s=12.0):
     """The oracle as it stands on this host's cores over a bounded sample of the workload's cells."""
     from oracle.oracle import Oracle
     o = Oracle(m)
@@ -114,17 +143,28 @@ def cpu_baseline(m, F, budget_s=12.0):
         done += len(sl)
         chunk = min(chunk * 2, 1024)
     return {"value": done / t_used, "unit": "reactor-steps/s", "cores": int(threads), "kind": "oracle",
-            "sample": f"{done} seeded-random cells of the same 65536-cell field, integrated over dt=1e-5 s with "
-                      f"OpenMP over cells ({t_used:.1f} s)"}
+            "sample": f"{done} seeded-random cells of the {name} workload's initial field, each integrated over "
+                      f"its dt with OpenMP over cells ({t_used:.1f} s)"}
 
 
-def adjoint_bench(h, m, dev, n_cells=4096):
-    """Seconds per gradient: one chem_adjoint call (one cotangent vector, all cells, all 2R parameters) on
-    igniting cells (T0 ~ U(1000, 1400) K, p ~ logU(1, 10) atm) integrated to t = 1e-3 s; objective = final
-    T plus 5 seeded species mass fractions; checkpoints every 16 accepted steps."""
-    import torch
+def adjoint_fields(name, m, F):
+    """Adjoint workload: 4096 igniting cells to t = 1e-3 s for the 53/325 mechanism; a seeded 2048-cell
+    subset of the field for the 150/1000 one."""
     from paper_2311_14941_gb300 import synth
-    F = synth.field_igniting(m, n_cells, seed=4, dt=1e-3)
+    rank = int(os.environ.get("RANK", "0"))
+    if name == "large":
+        idx = np.sort(np.random.default_rng(21 + rank).choice(F.n_cells, 2048, replace=False))
+        return F.subset(idx), "150sp/1000rxn, seeded 2048-cell subset of the bimodal field, own dt"
+    return (synth.field_igniting(m, 4096, seed=4 + rank, dt=1e-3),
+            "53sp/325rxn igniting cells, T0 1000-1400 K, p 1-10 atm, integrated to 1e-3 s")
+
+
+def adjoint_bench(h, m, dev, F, label):
+    """Seconds per gradient: one chem_adjoint call (one cotangent vector, all cells, all 2R parameters);
+    objective = final T (x1e-3) plus 5 seeded species mass fractions; checkpoints every 16 accepted
+    steps.  The forward integration of the same cells is timed alone for the cost ratio."""
+    import torch
+    from paper_2311_14941_gb300 import shard, synth
     sel = synth.cotangent_species(m, 5, seed=4)
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     N = F.n_cells
@@ -136,24 +176,32 @@ def adjoint_bench(h, m, dev, n_cells=4096):
     gE = torch.zeros(h.R, dtype=torch.float64, device=dev)
     st = torch.zeros(N, dtype=torch.int32, device=dev)
     P, D = t(F.p), t(F.dt)
-    # warm-up on a few cells (module load, scratch growth happens on the full call below as well)
-    h.adjoint(t(F.T[:64]), P[:64].contiguous(), t(F.Y[:, :64].reshape(-1)), D[:64].contiguous(), gT[:64].contiguous(),
-              t(gYn[:, :64].reshape(-1)), gA, gE, st[:64].contiguous())
-    torch.cuda.synchronize()
+    # untimed call on all cells over a 1e-12 s interval: loads the module and sizes the scratch (it
+    # depends on the cell count and the tape options only)
     T, Y = t(F.T), t(F.Y.reshape(-1))
-    h.adjoint(T, P, Y, D, gT, gY, gA, gE, st)   # sizes the scratch for the full batch
+    h.adjoint(T, P, Y, torch.full_like(D, 1e-12), gT, gY, gA, gE, st)
     torch.cuda.synchronize()
     T, Y = t(F.T), t(F.Y.reshape(-1))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     h.adjoint(T, P, Y, D, gT, gY, gA, gE, st)
+    shard.allreduce_gradients(gA, gE)      # ranks sum their cells' parameter gradients (no-op on one GPU)
     e1.record()
     torch.cuda.synchronize()
-    s = e0.elapsed_time(e1) / 1e3
+    s = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     stat = st.cpu().numpy()
-    return {"s_per_grad": s, "cells": N, "params": 2 * h.R, "cotangent": "final T (x1e-3) + 5 seeded species",
-            "workload": "53sp/325rxn igniting cells, T0 1000-1400 K, p 1-10 atm, integrated to 1e-3 s, "
-                        "checkpoints every 16 accepted steps",
+    T, Y = t(F.T), t(F.Y.reshape(-1))
+    hio = torch.zeros(N, dtype=torch.float64, device=dev)
+    ns = torch.zeros(N, dtype=torch.int32, device=dev)
+    st2 = torch.zeros(N, dtype=torch.int32, device=dev)
+    e0.record()
+    h.integrate(T, P, Y, D, hio, ns, st2, rtol=RTOL, atol=ATOL, mode=0)
+    e1.record()
+    torch.cuda.synchronize()
+    s_fwd = e0.elapsed_time(e1) / 1e3
+    return {"s_per_grad": s, "forward_s": s_fwd, "cells": N, "params": 2 * h.R,
+            "cotangent": "final T (x1e-3) + 5 seeded species", "workload": label + ", checkpoints every 16 "
+            "accepted steps", "substeps_mean": float(ns.float().mean().item()),
             "cell_status": {str(k): int(v) for k, v in zip(*np.unique(stat, return_counts=True))},
             "grad_norm": float(torch.linalg.vector_norm(torch.cat([gA, gE])).item())}
 
@@ -162,7 +210,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    m, F = workload()
+    m, F = workload(args.workload)
     from oracle.oracle import Oracle
     o = Oracle(m)
     rng = np.random.default_rng(13)
@@ -181,9 +229,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "reactor-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config("oracle"), sample=f"{per_step} random cells per step"),
+            "config": dict(config(args.workload, "oracle"), sample=f"{per_step} random cells per step"),
             "cpu_baseline": {"value": v, "unit": "reactor-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} seeded-random cells of the workload per step"},
+                             "sample": f"{per_step} seeded-random cells of the workload's initial field per step"},
             "e2e": {"value": v, "unit": "reactor-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -194,9 +242,12 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--mode", default="persistent", choices=["plain", "persistent"])
+    ap.add_argument("--workload", default="jet", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="persistent", choices=["plain", "persistent"],
+                    help="the mode of the headline value (the other one is timed beside it)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-mode", action="store_true", help="time only --mode")
     ap.add_argument("--cells", type=int, default=0, help="integrate only this many seeded-random cells (profiling)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint seconds-per-gradient measurement")
     args = ap.parse_args()
@@ -205,7 +256,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2311_14941_gb300 import chem, opcount
+    from paper_2311_14941_gb300 import chem, opcount, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,13 +265,13 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    m, F = workload(seed_offset=rank)
+    m, F = workload(args.workload, seed_offset=rank)
     if args.cells:
         F = F.subset(np.sort(np.random.default_rng(5).permutation(F.n_cells)[: args.cells]))
+    evolving = WORKLOADS[args.workload]["evolving"]
     h = chem.create(m, local)
     oc = opcount.model(m, h.export_plan(0), h.export_plan(1))
     N = F.n_cells
-    mode = 1 if args.mode == "persistent" else 0
 
     T0 = torch.tensor(F.T, device=dev)
     Y0 = torch.tensor(F.Y.reshape(-1), device=dev)
@@ -234,47 +285,60 @@ def main():
     nacc = torch.zeros(N, dtype=torch.int32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream()
+    clocks_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                               f"bench_clocks_r{rank}.csv")
 
-    def step():
-        # same initial state every step; nsub keeps the previous call's counts (the persistent mode's
-        # sort key, as in consecutive flow steps)
+    def run_mode(mode_name):
+        """W untimed and K timed steps in one mode; returns per-step ms, work counts and clocks."""
+        mode = 1 if mode_name == "persistent" else 0
         T.copy_(T0)
         Y.copy_(Y0)
         hio.zero_()
-        h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode, naccept=nacc)
+        ns.zero_()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    with Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                             f"bench_clocks_r{rank}.csv")) as ck:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            evs[i][0].record(stream)
+        def step():
+            if not evolving:
+                # same initial state every step; nsub keeps the previous call's counts (the sort key)
+                T.copy_(T0)
+                Y.copy_(Y0)
+                hio.zero_()
+            h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode, naccept=nacc)
+
+        for _ in range(args.warmup):
             step()
-            evs[i][1].record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_total = sum(step_ms) / 1e3
-    t_max = torch.tensor([t_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_total = float(t_max.item())
-    value = world * N * args.steps / t_total
-    status = st.cpu().numpy()
-    nsub = ns.cpu().numpy()
-    nac = nacc.cpu().numpy()
+        if world > 1:
+            dist.barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        slots = 0.0
+        torch.cuda.synchronize()
+        with Clocks(clocks_path) as ck:
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                step()
+                evs[i][1].record(stream)
+                if evolving:   # per-step work differs: count it step by step (outside the timed events)
+                    slots += float(oc.cell_slots(ns.cpu().numpy(), nacc.cpu().numpy()).sum())
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        if not evolving:
+            slots = args.steps * float(oc.cell_slots(ns.cpu().numpy(), nacc.cpu().numpy()).sum())
+        t_total = shard.max_over_ranks(sum(step_ms) / 1e3, dev)
+        return {"t": t_total, "step_ms": step_ms, "slots": slots, "nsub": ns.cpu().numpy(),
+                "nacc": nacc.cpu().numpy(), "status": st.cpu().numpy(), "clocks": ck.summary(local)}
 
-    # roofline: algorithmic FP64 work of one launch / its duration
-    slots = float(oc.cell_slots(nsub, nac).sum())
-    launch_s = t_total / args.steps
-    achieved = opcount.FLOP_PER_SLOT * slots / launch_s / 1e12
+    other = "plain" if args.mode == "persistent" else "persistent"
+    res_other = None if args.no_other_mode else run_mode(other)
+    res = run_mode(args.mode)
+    t_total = res["t"]
+    value = world * N * args.steps / t_total
+
+    # roofline: algorithmic FP64 work of the launches / their duration
+    achieved = opcount.FLOP_PER_SLOT * res["slots"] / t_total / 1e12
     peak = opcount.fp64_peak_tflops()
 
     # end to end through the ABI with host buffers (pinned), copies inside the timed region
@@ -286,6 +350,7 @@ def main():
     Yo = torch.empty_like(Yh).pin_memory()
     So = torch.empty(N, dtype=torch.int32).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
+    mode = 1 if args.mode == "persistent" else 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -299,36 +364,46 @@ def main():
         Yo.copy_(Y, non_blocking=True)
         So.copy_(st, non_blocking=True)
         torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+    t_e2e = shard.max_over_ranks(time.perf_counter() - t0, dev)
     h2d = (Th.numel() + Yh.numel() + Ph.numel() + Dh.numel()) * 8
     d2h = (To.numel() + Yo.numel()) * 8 + So.numel() * 4
 
+    adj = None
+    if not args.no_adjoint and not args.cells and args.workload in ("jet", "large"):
+        Fa, label = adjoint_fields(args.workload, m, F)
+        adj = adjoint_bench(h, m, dev, Fa, label)
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return 0
+    nsub, nac = res["nsub"], res["nacc"]
     line = {
         "metric": METRIC, "value": value, "unit": "reactor-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(config(args.mode), n_cells=N),
+        "config": dict(config(args.workload, args.mode), n_cells=N),
         "e2e": {"value": world * N * e2e_steps / t_e2e, "unit": "reactor-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (4 if args.mode == "persistent" else 1),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None,
                      "note": "FP64 pipe slots of the algorithm (opcount model, 2 flop per slot) / CUDA-event time of "
-                             "the integrate launch; peak derived: 2 DFMA/clk/SM x 152 SM x 2.07 GHz"},
+                             "the integrate launches; peak derived: 2 DFMA/clk/SM x 152 SM x 2.07 GHz"},
         "substeps": {"total": int(nsub.sum()), "mean": float(nsub.mean()), "max": int(nsub.max()),
                      "accepted": int(nac.sum())},
-        "cell_status": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
-        "step_ms": step_ms,
+        "cell_status": {str(k): int(v) for k, v in zip(*np.unique(res["status"], return_counts=True))},
+        "step_ms": res["step_ms"],
     }
-    ck_s = ck.summary(local)
-    if ck_s:
-        line["clocks"] = ck_s
-    if not args.no_adjoint and not args.cells:
-        line["adjoint"] = adjoint_bench(h, m, dev)
-    if not args.no_cpu_baseline and world >= 1:
-        line["cpu_baseline"] = cpu_baseline(m, F)
+    if res_other is not None:
+        line[other] = {"value": world * N * args.steps / res_other["t"], "unit": "reactor-steps/s",
+                       "ms_per_step": 1e3 * res_other["t"] / args.steps, "step_ms": res_other["step_ms"],
+                       "clocks": res_other["clocks"]}
+    if res["clocks"]:
+        line["clocks"] = res["clocks"]
+    if adj is not None:
+        line["adjoint"] = adj
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, F, args.workload)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

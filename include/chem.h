@@ -226,6 +226,14 @@ chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double
                                    double* h_io, int* nsub, int* status, const chem_integrate_opts* opts,
                                    chem_stream stream);
 
+/* Diagnostic: evaluates an elementary function of the device code on N doubles (device pointers x, y,
+   y[i] = f(x[i])): fn 0 = the library's table-driven exponential (used for every rate constant,
+   equilibrium constant and fall-off factor), fn 1 = the CUDA math library's exp on the same inputs.
+   It has no counterpart in the paper; it exists so that the library's exponential can be checked
+   against CUDA's.  Runs on the current device.  CHEM_EINVAL for fn outside {0, 1}, N < 0 or null
+   pointers with N > 0. */
+chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

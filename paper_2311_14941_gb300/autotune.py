@@ -1,0 +1,140 @@
+"""Launch-shape autotuner for chem_integrate.
+
+Knobs searched (one warp always integrates one cell; the kernels are written for that mapping):
+  mode         0 = one grid over all cells, 1 = cells sorted by their previous substep count and pulled
+               by resident warps from an atomic queue (the on-chip form of the paper's dynamic load
+               balancing, Sec. 2.5)
+  block_warps  warps (cells) per block: changes how shared memory is carved up per SM and how many
+               blocks share an SM
+  chunk        cells a warp claims per queue operation (mode 1)
+
+Every candidate integrates the same sample of the caller's cells, starting from the same state, once
+untimed and then timed with CUDA events on the caller's stream; the fastest is kept.  The sample keeps
+the cost distribution of the whole field: cells are ordered by previous substep count and every k-th is
+taken (a seeded random pick when no counts are known yet).  Results are cached per (mechanism digest,
+cell-count bucket, device name, tolerances) in a JSON file next to the compiled library.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CACHE = os.path.join(_build.OUT, "autotune_cache.json")
+
+
+def mechanism_digest(desc) -> str:
+    h = hashlib.sha1()
+    for name in ("W", "nasa_lo", "nasa_hi", "T_mid", "reac_ptr", "reac_sp", "reac_nu", "prod_ptr", "prod_sp",
+                 "prod_nu", "A", "b", "Ea", "rtype", "reversible", "eff_ptr", "eff_sp", "eff_alpha", "troe", "low"):
+        h.update(np.ascontiguousarray(getattr(desc, name)).tobytes())
+    return h.hexdigest()[:16]
+
+
+def candidates(max_block_warps: int):
+    """The search space: plain grids and sorted queues over a few block shapes and chunks."""
+    shapes = sorted({1, 2, 4, max(1, max_block_warps)})
+    out = [dict(mode=0, block_warps=w, chunk=1) for w in shapes]
+    out += [dict(mode=1, block_warps=w, chunk=c) for w in shapes for c in (1, 2, 4)]
+    return out
+
+
+def sample_cells(n_cells: int, nsub_prev=None, size: int = 8192, seed: int = 0) -> np.ndarray:
+    """Indices of a cost-stratified sample of at most `size` cells."""
+    if n_cells <= size:
+        return np.arange(n_cells)
+    if nsub_prev is None or not np.any(np.asarray(nsub_prev)):
+        return np.sort(np.random.default_rng(seed).choice(n_cells, size, replace=False))
+    order = np.argsort(-np.asarray(nsub_prev), kind="stable")
+    pick = order[np.linspace(0, n_cells - 1, size).round().astype(np.int64)]
+    return np.sort(np.unique(pick))
+
+
+def _key(mech, n_cells, rtol, atol):
+    import torch
+    bucket = 1 << max(0, int(np.ceil(np.log2(max(n_cells, 1)))))
+    dev = torch.cuda.get_device_name(mech.device)
+    return f"{mechanism_digest(mech.desc)}|{bucket}|{dev}|{rtol:g}|{atol:g}"
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key, value):
+    data = _load()
+    data[key] = value
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int = 8192, use_cache: bool = True,
+         repeats: int = 1, stream=None):
+    """Best launch shape for integrating these cells; returns {mode, block_warps, chunk, ms, table}.
+
+    T, p, dt: device tensors [N]; Y: [n*N] species-major; nsub_prev: previous substep counts (device or
+    host, may be None).  The inputs are not modified."""
+    import torch
+    N = T.numel()
+    key = _key(mech, N, rtol, atol)
+    if use_cache:
+        hit = _load().get(key)
+        if hit is not None:
+            return hit
+    ns_host = None if nsub_prev is None else np.asarray(
+        nsub_prev.cpu().numpy() if hasattr(nsub_prev, "cpu") else nsub_prev)
+    idx = sample_cells(N, ns_host, sample)
+    ii = torch.as_tensor(idx, device=T.device)
+    n = mech.n
+    Ts, Ps, Ds = T[ii].contiguous(), p[ii].contiguous(), dt[ii].contiguous()
+    Ys = Y.view(n, N)[:, ii].contiguous().view(-1)
+    ns0 = torch.zeros(len(idx), dtype=torch.int32, device=T.device) if ns_host is None else \
+        torch.as_tensor(ns_host[idx].astype(np.int32), device=T.device)
+    cell_bytes = mech.info["smem_per_cell"]
+    props = torch.cuda.get_device_properties(mech.device)
+    optin = getattr(props, "shared_memory_per_block_optin", 227 * 1024)
+    wmax = max(1, min(32, optin // max(cell_bytes, 1)))
+    strm = stream or torch.cuda.current_stream(T.device)
+    Tw, Yw = torch.empty_like(Ts), torch.empty_like(Ys)
+    hio = torch.empty(len(idx), dtype=torch.float64, device=T.device)
+    ns = torch.empty_like(ns0)
+    st = torch.empty_like(ns0)
+    table = []
+    for c in candidates(wmax):
+        times = []
+        for r in range(1 + repeats):
+            with torch.cuda.stream(strm):
+                Tw.copy_(Ts)
+                Yw.copy_(Ys)
+                hio.zero_()
+                ns.copy_(ns0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(strm)
+                mech.integrate(Tw, Ps, Yw, Ds, hio, ns, st, rtol=rtol, atol=atol, stream=strm, **c)
+                e1.record(strm)
+            strm.synchronize()
+            if r > 0:
+                times.append(e0.elapsed_time(e1))
+        table.append(dict(c, ms=float(min(times))))
+    best = min(table, key=lambda d: d["ms"])
+    out = dict(mode=best["mode"], block_warps=best["block_warps"], chunk=best["chunk"], ms=best["ms"],
+               sample=int(len(idx)), table=table)
+    if use_cache:
+        _store(key, out)
+    return out
+
+
+def launch_options(result) -> dict:
+    """The chem_integrate keyword arguments of a `tune` result."""
+    return dict(mode=int(result["mode"]), block_warps=int(result["block_warps"]), chunk=int(result["chunk"]))

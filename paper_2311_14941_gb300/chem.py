@@ -79,7 +79,8 @@ def lib():
         L.chem_set_params.argtypes = [_vp, _vp, _vp, _vp]
         L.chem_adjoint.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                    C.POINTER(OptsC), _vp]
-        for f in ("chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
+        L.chem_eval_elementary.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp]
+        for f in ("chem_eval_elementary", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
                   "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc", "chem_set_params",
                   "chem_adjoint"):
             getattr(L, f).restype = C.c_int
@@ -252,6 +253,14 @@ class Mechanism:
             _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
             _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
             _dptr(status, torch.int32, N, "status"), C.byref(o), _stream(stream)), "chem_integrate_noalloc")
+
+
+def eval_elementary(fn: int, x, y, stream=None):
+    """chem_eval_elementary: y = f(x) on the device (fn 0 library exp, 1 CUDA exp)."""
+    import torch
+    N = x.numel()
+    _check(lib().chem_eval_elementary(fn, N, _dptr(x, torch.float64, N, "x"), _dptr(y, torch.float64, N, "y"),
+                                      _stream(stream)), "chem_eval_elementary")
 
 
 def create(desc, device: int = 0) -> Mechanism:

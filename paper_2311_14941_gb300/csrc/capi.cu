@@ -49,7 +49,7 @@ struct chem_handle_s {
   size_t scratch_bytes = 0;
   void* adj_scratch = nullptr;     // adjoint tape, gradients, dual workspaces (grows on demand)
   size_t adj_scratch_bytes = 0;
-  int occ_blocks_per_sm[2] = {0, 0};   // persistent kernel occupancy per block size choice (cached)
+  int default_wpb = 1;             // warps per block that fit the most cells per SM (set with the attributes)
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
     int N, mode, wpb, chunk;
@@ -73,24 +73,26 @@ CellLayout make_layout(const HostMech& hm, bool separate_lu = false) {
   L.y = take(m); L.ytmp = take(m); L.f0 = take(m); L.U1 = take(m); L.U2 = take(m); L.U3 = take(m);
   L.U4 = take(m); L.x = take(m); L.z = take(m); L.u = take(m); L.v = take(m);
   L.C = take(n); L.hRT = take(n); L.eg = take(n); L.emg = take(n); L.cpR = take(n);
-  L.q = take(std::max(R, 1)); L.dqdT = take(std::max(R, 1));
+  L.q = take(std::max(R, 1));
   L.S = take(hm.nnz_S);
-  // the derivative slots are dead once S is assembled; the factor reuses their space
+  // the Jacobian passes' dq/dT values and derivative slots are dead once S is assembled; the factor and
+  // 1/diag reuse their space (the adjoint keeps the factor apart: separate_lu)
   const int lu_part = hm.nnz_LU + m;
   if (separate_lu) {
-    L.D = take(std::max(hm.n_dslot, 1));
+    L.D = take(std::max(hm.jreg, 1));
     L.LU = take(hm.nnz_LU);
     L.dinv = take(m);
   } else {
-    const int reuse = std::max(lu_part, hm.n_dslot);
+    const int reuse = std::max(lu_part, hm.jreg);
     L.D = o;
     L.LU = o;
     L.dinv = o + hm.nnz_LU;
     o += reuse;
   }
   int np = 1;
-  for (const HostGather* g : {&hm.g_omega, &hm.g_dtil, &hm.g_row, &hm.g_col}) np = std::max(np, g->n_partial);
-  L.part = take(2 * np);
+  for (const HostGather* g : {&hm.g_omega, &hm.g_row, &hm.g_col}) np = std::max(np, g->n_partial);
+  for (const HostGather& g : hm.g_jac) np = std::max(np, g.n_partial);
+  L.part = take(np);
   L.misc = take(16);
   L.total = o;
   return L;
@@ -406,6 +408,17 @@ chem_status set_attrs(chem_handle h) {
       (e = cudaFuncSetAttribute(k_integrate_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute");
+  // default block shape: the most resident cells per SM (each block also reserves some shared memory,
+  // so a few cells per block can fit one more cell per SM than single-cell blocks); ties -> fewer warps
+  int best_w = 1, best_cells = 0;
+  for (int w = 1; w <= 16 && w * h->cell_bytes <= h->smem_optin; ++w) {
+    int blocks = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_integrate_persistent, w * kWarp,
+                                                           (size_t)w * h->cell_bytes)) != cudaSuccess)
+      return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (blocks * w > best_cells) { best_cells = blocks * w; best_w = w; }
+  }
+  h->default_wpb = best_w;
   h->attr_set = true;
   return CHEM_OK;
 }
@@ -493,9 +506,13 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
          o_lops = put(buf, hm.lu_ops), o_lkind = put(buf, hm.lu_kind), o_sops = put(buf, hm.sv_ops),
          o_skind = put(buf, hm.sv_kind), o_sout = put(buf, hm.s_out), o_tops = put(buf, hm.svT_ops),
          o_tkind = put(buf, hm.svT_kind), o_rxo = put(buf, hm.rx_order), o_rxd0 = put(buf, hm.rxd);
-  size_t o_g[4][2];
-  const HostGather* gs[4] = {&hm.g_omega, &hm.g_dtil, &hm.g_row, &hm.g_col};
-  for (int i = 0; i < 4; ++i) { o_g[i][0] = put(buf, gs[i]->ops); o_g[i][1] = put(buf, gs[i]->comb); }
+  const int n_jp = (int)hm.g_jac.size();
+  if (n_jp > kMaxJPass) { delete h; return fail(CHEM_EUNSUPPORTED, "too many Jacobian passes"); }
+  constexpr int kMaxG = 3 + kMaxJPass;
+  size_t o_g[kMaxG][2];
+  const HostGather* gs[kMaxG] = {&hm.g_omega, &hm.g_row, &hm.g_col};
+  for (int i = 0; i < n_jp; ++i) gs[3 + i] = &hm.g_jac[i];
+  for (int i = 0; i < 3 + n_jp; ++i) { o_g[i][0] = put(buf, gs[i]->ops); o_g[i][1] = put(buf, gs[i]->comb); }
   if ((e = cudaMalloc(&h->blob, buf.size())) != cudaSuccess) { delete h; return fail(CHEM_ENOMEM, "cudaMalloc of mechanism tables failed"); }
   if ((e = cudaMemcpy(h->blob, buf.data(), buf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(h->blob);
@@ -518,8 +535,12 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   V.svT_steps = (int)hm.svT_kind.size();
   V.rx_order = (const int*)(b + o_rxo);
   h->rxd0 = (const double*)(b + o_rxd0);
-  Gather* vg[4] = {&V.g_omega, &V.g_dtil, &V.g_row, &V.g_col};
-  for (int i = 0; i < 4; ++i) {
+  V.n_jpass = n_jp;
+  for (int i = 0; i < n_jp; ++i)
+    for (int j = 0; j < 4; ++j) V.jpass[i][j] = hm.jpass[(size_t)i * 4 + j];
+  Gather* vg[kMaxG] = {&V.g_omega, &V.g_row, &V.g_col};
+  for (int i = 0; i < n_jp; ++i) vg[3 + i] = &V.g_jac[i];
+  for (int i = 0; i < 3 + n_jp; ++i) {
     vg[i]->ops = (const GatherOp*)(b + o_g[i][0]);
     vg[i]->steps = gs[i]->steps;
     vg[i]->n_partial = gs[i]->n_partial;
@@ -650,7 +671,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   cudaStream_t strm = (cudaStream_t)stream;
   cudaError_t e;
   if (o.mode == 0) {
-    const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
+    const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : h->default_wpb);
     unsigned long long* stamp = nullptr;
     if (budget_ns) {
       if ((st = ensure_scratch(h, 1)) != CHEM_OK) return st;
@@ -664,7 +685,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   // persistent mode: sort by previous cost, then one resident grid pulling from the queue; the whole
   // sequence is one CUDA graph, captured once per argument set and replayed on `stream`
   if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
-  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
+  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : h->default_wpb);
   const int chunk = o.chunk > 0 ? o.chunk : 1;
   chem_handle_s::GraphKey key{};
   key.N = N; key.mode = 1; key.wpb = wpb; key.chunk = chunk;
@@ -875,7 +896,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   char* scr = nullptr;
   if ((st = noalloc_scratch_address(h->device, &scr)) != CHEM_OK) return st;
   const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : 1);
+  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : h->default_wpb);
   const int chunk = o.chunk > 0 ? o.chunk : 1;
   int bps = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_integrate_persistent, wpb * kWarp,
@@ -898,4 +919,21 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   k_integrate_persistent<<<grid, wpb * kWarp, wpb * h->cell_bytes, strm>>>(
       h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
   return launch_check("chem_integrate_noalloc launch");
+}
+
+namespace {
+__global__ void k_elementary(int fn, int N, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  y[i] = fn == 0 ? fast_exp(x[i]) : exp(x[i]);
+}
+}  // namespace
+
+extern "C" chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem_stream stream) {
+  if (fn < 0 || fn > 1) return fail(CHEM_EINVAL, "fn must be 0 (library exp) or 1 (CUDA exp)");
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N == 0) return CHEM_OK;
+  if (!x || !y) return fail(CHEM_EINVAL, "null array argument");
+  k_elementary<<<(N + 255) / 256, 256, 0, (cudaStream_t)stream>>>(fn, N, x, y);
+  return launch_check("chem_eval_elementary launch");
 }

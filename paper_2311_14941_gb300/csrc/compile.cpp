@@ -28,14 +28,26 @@ namespace {
 
 bool fin(double x) { return std::isfinite(x); }
 
+// Gather coefficient nu as the top 16 bits of the IEEE double nu (+-1, +-2, +-3 have 16 trailing zero
+// bits in their high word), so that the device rebuilds it with integer instructions only.
+int enc_nu(int nu) {
+  const double d = (double)nu;
+  uint64_t bits;
+  std::memcpy(&bits, &d, 8);
+  return (int)(bits >> 48);
+}
+
 // ------------------------------------------------------------------------ gather programs
 // groups[g] = list of (a, b) terms summed into output g.  Terms are dealt to the 32 lanes so that the
 // longest lane is as short as possible: a group longer than the per-lane target is split into pieces
-// whose partial sums are combined afterwards; pieces go to lanes largest first (LPT).
-bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, HostGather& G, std::string& err) {
+// whose partial sums are combined afterwards; pieces go to lanes largest first (LPT).  With skip_empty,
+// outputs without terms are left untouched (programs that accumulate into their outputs); otherwise
+// they are written with 0.
+bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, HostGather& G, std::string& err,
+                  bool skip_empty = false) {
   G = HostGather();
   long total = 0;
-  for (auto& g : groups) total += std::max<size_t>(g.size(), 1);
+  for (auto& g : groups) total += skip_empty ? (long)g.size() : (long)std::max<size_t>(g.size(), 1);
   if (groups.empty()) return true;
   const long cap = std::max<long>(1, (total + kWarp - 1) / kWarp);
   struct Piece { int g; int first; int count; int partial; };
@@ -43,6 +55,7 @@ bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, H
   int n_partial = 0;
   for (size_t g = 0; g < groups.size(); ++g) {
     const int L = (int)groups[g].size();
+    if (L == 0 && skip_empty) continue;
     if (L <= cap) {
       pieces.push_back({(int)g, 0, L, -1});
     } else {
@@ -58,6 +71,7 @@ bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, H
     }
   }
   G.n_partial = n_partial;
+  if (pieces.empty()) return true;
   std::vector<int> order(pieces.size());
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
@@ -395,38 +409,15 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
 
   // ---- gather programs
   {
-    std::vector<std::vector<std::pair<int, int>>> gw(n), gd(hm.nY), gr(n), gc(n);
+    std::vector<std::vector<std::pair<int, int>>> gw(n), gr(n), gc(n);
     for (int r = 0; r < R; ++r)
       for (auto& kv : netmap[r])
-        if (kv.second != 0) gw[kv.first].push_back({r, kv.second});
-    for (int r = 0; r < R; ++r) {
-      const int base = hm.rxi[(size_t)r * RX_I + 13];
-      for (auto& kv : netmap[r]) {
-        if (kv.second == 0) continue;
-        for (size_t c = 0; c < slots_sp[r].size(); ++c) {
-          int e = eidx[kv.first][slots_sp[r][c]];
-          gd[e].push_back({base + (int)c, kv.second});
-        }
-      }
-    }
+        if (kv.second != 0) gw[kv.first].push_back({r, enc_nu(kv.second)});
     for (int e = 0; e < hm.nY; ++e) {
       gr[hm.entry_row[e]].push_back({e, hm.entry_col[e]});
       gc[hm.entry_col[e]].push_back({e, hm.entry_row[e]});
     }
-    // the coefficient nu of the omega and Dtil gathers travels as the top 16 bits of the IEEE double nu
-    // (+-1, +-2, +-3 have 16 trailing zero bits in their high word), so the device rebuilds it with integer
-    // instructions only
-    auto enc = [](int nu) -> int {
-      const double d = (double)nu;
-      uint64_t bits;
-      std::memcpy(&bits, &d, 8);
-      return (int)(bits >> 48);
-    };
-    for (auto* G : {&gw, &gd})
-      for (auto& grp : *G)
-        for (auto& t : grp) t.second = enc(t.second);
-    if (!build_gather(gw, hm.g_omega, err) || !build_gather(gd, hm.g_dtil, err) || !build_gather(gr, hm.g_row, err) ||
-        !build_gather(gc, hm.g_col, err))
+    if (!build_gather(gw, hm.g_omega, err) || !build_gather(gr, hm.g_row, err) || !build_gather(gc, hm.g_col, err))
       return CHEM_EUNSUPPORTED;
   }
 
@@ -588,6 +579,56 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       for (int w : b_w[q]) ops[w].succ.push_back(pr.first);    // x_q backward-final
     }
     if (!schedule(ops, hm.svT_ops, hm.svT_kind, err)) return CHEM_EINVAL;
+  }
+
+  // ---- Jacobian passes.  A reaction leaves one dq/dT value and one derivative slot per column species;
+  // they are consumed by the pass's gather right after the pass.  Reactions are cut into P consecutive
+  // ranges of about equal size, P the smallest count whose largest range fits the region the factor
+  // and 1/diag take during a step (nnz_LU + m doubles), so the Jacobian needs no storage of its own.
+  {
+    std::vector<int> cost(R);
+    long total = 0;
+    for (int r = 0; r < R; ++r) { cost[r] = 1 + hm.rxi[(size_t)r * RX_I + 14]; total += cost[r]; }
+    const long cap = hm.nnz_LU + m;
+    std::vector<int> cut;   // first reaction of each pass, then R
+    for (int P = std::max<long>(1, (total + cap - 1) / cap); ; ++P) {
+      cut.assign(1, 0);
+      long acc = 0, biggest = 0, cur = 0;
+      for (int r = 0; r < R; ++r) {
+        if (cur > 0 && (acc + cost[r]) * P > total * (long)cut.size() && (int)cut.size() < P) {
+          cut.push_back(r);
+          biggest = std::max(biggest, cur);
+          cur = 0;
+        }
+        acc += cost[r];
+        cur += cost[r];
+      }
+      biggest = std::max(biggest, cur);
+      cut.push_back(R);
+      hm.jreg = (int)std::max<long>(biggest, 1);
+      if (biggest <= cap || P >= kMaxJPass || P >= R) break;
+    }
+    const int P = (int)cut.size() - 1;
+    hm.jpass.clear();
+    hm.g_jac.assign(P, HostGather());
+    for (int p = 0; p < P; ++p) {
+      const int rb = cut[p], re = cut[p + 1];
+      const int sb = R > 0 && rb < R ? hm.rxi[(size_t)rb * RX_I + 13] : hm.n_dslot;
+      const int cnt = re - rb;
+      hm.jpass.insert(hm.jpass.end(), {rb, re, sb, cnt});
+      std::vector<std::vector<std::pair<int, int>>> gj(hm.nY + n);
+      for (int r = rb; r < re; ++r) {
+        const int base = hm.rxi[(size_t)r * RX_I + 13];
+        for (auto& kv : netmap[r]) {
+          if (kv.second == 0) continue;
+          const int nu = enc_nu(kv.second);
+          gj[hm.nY + kv.first].push_back({r - rb, nu});
+          for (size_t c = 0; c < slots_sp[r].size(); ++c)
+            gj[eidx[kv.first][slots_sp[r][c]]].push_back({cnt + base + (int)c - sb, nu});
+        }
+      }
+      if (!build_gather(gj, hm.g_jac[p], err, true)) return CHEM_EUNSUPPORTED;
+    }
   }
   return CHEM_OK;
 }

@@ -20,7 +20,10 @@ struct HostMech {
   std::vector<int> rx_order;           // compiled reaction index -> description index
   std::vector<double> sp, rxd, eff_am1, dslot_am1, entry_wratio;
   std::vector<int> rxi, eff_sp, dslot_sp, dslot_mask, entry_row, entry_col;
-  HostGather g_omega, g_dtil, g_row, g_col;
+  HostGather g_omega, g_row, g_col;
+  std::vector<HostGather> g_jac;       // one gather program per Jacobian pass
+  std::vector<int> jpass;              // [passes * 4]: first reaction, end reaction, first slot, reactions
+  int jreg = 0;                        // doubles of the largest pass (dq/dT values + derivative slots)
   std::vector<int> perm, iperm;        // LU position -> state index, and back
   std::vector<int> lu_src, lu_diag, s_out;
   std::vector<int> lu_rowptr, lu_col;  // factor pattern, CSR in LU (permuted) order

@@ -69,7 +69,8 @@ __device__ __forceinline__ double nu_of(int b) { return __hiloint2double(b << 16
 
 // -------------------------------------------------------------------------------------- gathers
 // out[g] = sum over the group's terms of val(a, b); partial sums of split groups are combined after.
-template <class Sc, class F>
+// ACC: out[g] += sum instead (outputs without terms in the program are left as they are).
+template <bool ACC = false, class Sc, class F>
 __device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F valf, int lane) {
   Sc acc = Sc(0.0);
   const GatherOp* op = G.ops + lane;
@@ -77,7 +78,9 @@ __device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F
     GatherOp o = ld_gop(op);
     if (!(o.flags & 1)) acc += valf(o.a, o.b);
     if (o.dst != DST_NONE) {
-      if (o.dst & PARTIAL_BIT) part[o.dst & 0x7FFF] = acc; else out[o.dst] = acc;
+      if (o.dst & PARTIAL_BIT) part[o.dst & 0x7FFF] = acc;
+      else if (ACC) out[o.dst] += acc;
+      else out[o.dst] = acc;
       acc = Sc(0.0);
     }
   }
@@ -86,42 +89,7 @@ __device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F
     const int dst = __ldg(G.comb + 3 * c), f = __ldg(G.comb + 3 * c + 1), cnt = __ldg(G.comb + 3 * c + 2);
     Sc s = Sc(0.0);
     for (int i = 0; i < cnt; ++i) s += part[f + i];
-    out[dst] = s;
-  }
-  __syncwarp();
-}
-
-// Same program, two accumulators: out1[g] = sum nu q[r], out2[g] = sum nu dq[r].
-template <class Sc>
-__device__ __forceinline__ void run_gather2(const Gather& G, Sc* out1, Sc* out2, Sc* part, const Sc* q,
-                                            const Sc* dq, int lane) {
-  Sc acc1 = Sc(0.0), acc2 = Sc(0.0);
-  const GatherOp* op = G.ops + lane;
-  for (int s = 0; s < G.steps; ++s, op += kWarp) {
-    GatherOp o = ld_gop(op);
-    if (!(o.flags & 1)) {
-      const double nu = nu_of(o.b);
-      acc1 = sfma(Sc(nu), q[o.a], acc1);
-      acc2 = sfma(Sc(nu), dq[o.a], acc2);
-    }
-    if (o.dst != DST_NONE) {
-      if (o.dst & PARTIAL_BIT) {
-        part[2 * (o.dst & 0x7FFF)] = acc1;
-        part[2 * (o.dst & 0x7FFF) + 1] = acc2;
-      } else {
-        out1[o.dst] = acc1;
-        out2[o.dst] = acc2;
-      }
-      acc1 = acc2 = Sc(0.0);
-    }
-  }
-  __syncwarp();
-  for (int c = lane; c < G.n_comb; c += kWarp) {
-    const int dst = __ldg(G.comb + 3 * c), f = __ldg(G.comb + 3 * c + 1), cnt = __ldg(G.comb + 3 * c + 2);
-    Sc s1 = Sc(0.0), s2 = Sc(0.0);
-    for (int i = 0; i < cnt; ++i) { s1 += part[2 * (f + i)]; s2 += part[2 * (f + i) + 1]; }
-    out1[dst] = s1;
-    out2[dst] = s2;
+    if (ACC) out[dst] += s; else out[dst] = s;
   }
   __syncwarp();
 }
@@ -302,10 +270,11 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
   return x;
 }
 
-// Store q (and with DERIV: dq/dT at fixed C, and the derivative slots dq/dC_j) of reaction r.
+// Store q (and with DERIV: dq/dT at fixed C into s[dq_off + r], and the derivative slots dq/dC_j into
+// s[d_off + slot]) of reaction r.
 template <class Sc, int TYPE, bool DERIV>
 __device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<Sc>& x, Sc* s, const CellLayout& L,
-                                         const ScalT<Sc>& sc, bool valid) {
+                                         const ScalT<Sc>& sc, bool valid, int dq_off, int d_off) {
   if (!valid) return;
   s[L.q + r] = x.q;
   if (!DERIV) return;
@@ -315,7 +284,7 @@ __device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<
   if (TYPE == 1) dqdM = x.qn;
   if (TYPE == 2) dqdM = x.dlnk_dlnM * x.q * x.iM;
   // [M] depends on T through the total concentration p/(Ru T)
-  s[L.dqdT + r] = sfma(x.dlnkf_dT, qf, -((x.dlnkf_dT - x.dlnKc_dT) * qr)) - dqdM * sc.ctot * sc.invT;
+  s[dq_off + r] = sfma(x.dlnkf_dT, qf, -((x.dlnkf_dT - x.dlnKc_dT) * qr)) - dqdM * sc.ctot * sc.invT;
   // partial products: d(prod)/d(occurrence i) = product of the other occurrences
   const Sc dr0 = x.cr1 * x.cr2, dr1 = x.cr0 * x.cr2, dr2 = x.cr0 * x.cr1;
   const Sc dp0 = x.cp1 * x.cp2, dp1 = x.cp0 * x.cp2, dp2 = x.cp0 * x.cp1;
@@ -331,31 +300,31 @@ __device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<
     if (mask & 32) fq += dp2;
     v = sfma(kfM, fr, v);
     v = sfma(-krM, fq, v);
-    s[L.D + x.so + i] = v;
+    s[d_off + x.so + i] = v;
   }
 }
 
-// Rates of progress of all reactions.  Reactions are ordered Troe, third-body, elementary, so every
+// Rates of progress of reactions [rb, re).  Reactions are ordered Troe, third-body, elementary, so every
 // segment has warp-uniform control flow; elementary reactions go two per lane (two exp chains).
 template <class Sc, bool DERIV>
 __device__ __forceinline__ void eval_reactions(const MechView& M, Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
-                                               int lane) {
+                                               int lane, int rb, int re, int dq_off = 0, int d_off = 0) {
   const Sc* C = s + L.C;
   const Sc* eg = s + L.eg;
   const Sc* emg = s + L.emg;
   const Sc* hRT = s + L.hRT;
-  const int e0 = M.n_troe + M.n_tb;
-  for (int r = lane; r < M.n_troe; r += kWarp)
-    rx_store<Sc, 2, DERIV>(M, r, rx_core<Sc, 2, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true);
-  for (int r = M.n_troe + lane; r < e0; r += kWarp)
-    rx_store<Sc, 1, DERIV>(M, r, rx_core<Sc, 1, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true);
-  for (int r = e0 + lane; r < M.R; r += 2 * kWarp) {
-    const bool v2 = r + kWarp < M.R;
+  const int t1 = min(re, M.n_troe), e0 = M.n_troe + M.n_tb, b1 = min(re, e0);
+  for (int r = rb + lane; r < t1; r += kWarp)
+    rx_store<Sc, 2, DERIV>(M, r, rx_core<Sc, 2, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true, dq_off, d_off);
+  for (int r = max(rb, M.n_troe) + lane; r < b1; r += kWarp)
+    rx_store<Sc, 1, DERIV>(M, r, rx_core<Sc, 1, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true, dq_off, d_off);
+  for (int r = max(rb, e0) + lane; r < re; r += 2 * kWarp) {
+    const bool v2 = r + kWarp < re;
     const int r2 = v2 ? r + kWarp : r;
     const RxCore<Sc> a = rx_core<Sc, 0, DERIV>(M, r, C, eg, emg, hRT, sc);
     const RxCore<Sc> b = rx_core<Sc, 0, DERIV>(M, r2, C, eg, emg, hRT, sc);
-    rx_store<Sc, 0, DERIV>(M, r, a, s, L, sc, true);
-    rx_store<Sc, 0, DERIV>(M, r2, b, s, L, sc, v2);
+    rx_store<Sc, 0, DERIV>(M, r, a, s, L, sc, true, dq_off, d_off);
+    rx_store<Sc, 0, DERIV>(M, r2, b, s, L, sc, v2, dq_off, d_off);
   }
   __syncwarp();
 }
@@ -366,7 +335,7 @@ template <class Sc>
 __device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
                                             Sc* out, int lane) {
   ScalT<Sc> sc = eval_species<Sc, false>(M, s, L, y, p, lane);
-  eval_reactions<Sc, false>(M, s, L, sc, lane);
+  eval_reactions<Sc, false>(M, s, L, sc, lane, 0, M.R);
   const Sc* q = s + L.q;
   Sc* part = s + L.part;
   Sc* w = out + 1;   // production rates written in place, then scaled
@@ -383,24 +352,31 @@ __device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const Cell
   return sc;
 }
 
-// f(y) into f0[m], S[nnz_S] (internal order), u[m], v[m].  Scratch: C.., q, dqdT, D, x (w), z (w_T),
-// U1 (g), U2 (t).
+// f(y) into f0[m], S[nnz_S] (internal order), u[m], v[m].  Scratch: C.., q, the pass region D, x (w),
+// U1 (g), U2 (t).  The reactions run in passes (see MechView::jpass): each pass leaves dq/dT and the
+// derivative slots of its reactions in the region, and its gather adds them into the Y block of S
+// (Dtil) and into the T-column slots of S, which hold w_T until the T column is formed below.
 template <class Sc>
 __device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
                                               int lane) {
   ScalT<Sc> sc = eval_species<Sc, true>(M, s, L, y, p, lane);
-  eval_reactions<Sc, true>(M, s, L, sc, lane);
   Sc* part = s + L.part;
   Sc* w = s + L.x;      // w_k
-  Sc* wT = s + L.z;     // w_T,k
   Sc* gk = s + L.U1;
   Sc* tk = s + L.U2;
   Sc* S = s + L.S;
+  Sc* wT = S + M.nY;    // w_T,k, until overwritten by the T column
   const Sc* C = s + L.C;
   const Sc* hRT = s + L.hRT;
-  const Sc* Dsl = s + L.D;
-  run_gather2(M.g_omega, w, wT, part, s + L.q, s + L.dqdT, lane);
-  run_gather(M.g_dtil, S, part, [&](int a, int b) { return nu_of(b) * Dsl[a]; }, lane);
+  const Sc* reg = s + L.D;
+  for (int e = lane; e < M.nY + M.n; e += kWarp) S[e] = Sc(0.0);
+  for (int ps = 0; ps < M.n_jpass; ++ps) {
+    const int rb = M.jpass[ps][JP_RB], cnt = M.jpass[ps][JP_CNT];
+    eval_reactions<Sc, true>(M, s, L, sc, lane, rb, M.jpass[ps][JP_RE], L.D - rb, L.D + cnt - M.jpass[ps][JP_SB]);
+    run_gather<true>(M.g_jac[ps], S, part, [&](int a, int b) { return nu_of(b) * reg[a]; }, lane);
+  }
+  const Sc* q = s + L.q;
+  run_gather(M.g_omega, w, part, [&](int a, int b) { return nu_of(b) * q[a]; }, lane);
   run_gather(M.g_row, gk, part, [&](int a, int b) { return S[a] * C[b]; }, lane);
   run_gather(M.g_col, tk, part, [&](int a, int b) { return S[a] * hRT[b]; }, lane);
   Sc* f = s + L.f0;
@@ -412,14 +388,15 @@ __device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const Ce
   for (int k = lane; k < M.n; k += kWarp) {
     const double Wk = __ldg(M.sp + (size_t)k * SP_STRIDE + 1);
     const Sc om = w[k], g = gk[k];
+    const Sc dwT = sfma(-g, sc.invT, wT[k]);   // read before the T column overwrites w_T
     const Sc fk = Wk * om * sc.irho;
     f[1 + k] = fk;
     u[1 + k] = Wk * sc.irho * (om - g);
-    S[M.nY + k] = sfma(Wk * sc.irho, sfma(-g, sc.invT, wT[k]), fk * sc.invT);
+    S[M.nY + k] = sfma(Wk * sc.irho, dwT, fk * sc.invT);
     v[1 + k] = sc.Wbar * __ldg(M.sp + (size_t)k * SP_STRIDE);
     const Sc h = hRT[k];
     Qs = sfma(h, om, Qs);
-    A1 = sfma(s[L.cpR + k], om, sfma(T * h, sfma(-g, sc.invT, wT[k]), A1));
+    A1 = sfma(s[L.cpR + k], om, sfma(T * h, dwT, A1));
     A2 = sfma(h, g, A2);
   }
   Qs = warp_sum(Qs);

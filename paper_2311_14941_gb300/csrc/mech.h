@@ -62,6 +62,11 @@ struct Gather {
   int n_comb;
 };
 
+// The Jacobian's reaction loop runs in passes over consecutive reaction ranges so that a pass's
+// dq/dT values and derivative slots fit in the region the LU factor occupies during a step.
+constexpr int kMaxJPass = 8;
+enum : int { JP_RB = 0, JP_RE = 1, JP_SB = 2, JP_CNT = 3 };   // first/end reaction, first slot, reactions
+
 struct MechView {
   int n, R, m;
   int n_troe, n_tb;          // reactions [0, n_troe) Troe, [n_troe, n_troe + n_tb) third-body
@@ -81,7 +86,11 @@ struct MechView {
   const int* entry_col;      // [nY] species j
   const double* entry_wratio;// [nY] W_k / W_j
   Gather g_omega;            // species <- reactions (a = reaction, b = top 16 bits of double(nu))
-  Gather g_dtil;             // Y entries <- derivative slots (a = slot, b = top 16 bits of double(nu))
+  int n_jpass;               // Jacobian passes
+  int jpass[kMaxJPass][4];   // per pass: JP_RB, JP_RE, JP_SB, JP_CNT
+  Gather g_jac[kMaxJPass];   // per pass: S[0 .. nY + n) += nu * region[a] (a < cnt: dq/dT of reaction
+                             // rb + a into the T column; a >= cnt: derivative slot sb + a - cnt into the
+                             // Y block), b = top 16 bits of double(nu)
   Gather g_row;              // species k <- sum_j Dtil_kj C_j (a = entry, b = species j)
   Gather g_col;              // species i <- sum_k h_k Dtil_ki (a = entry, b = species k)
   const int* lu_src;         // [nnz_LU] S index feeding the slot (-1: fill)
@@ -103,10 +112,10 @@ struct MechView {
 struct CellLayout {
   int y, ytmp, f0, U1, U2, U3, U4, x, z, u, v;   // m-vectors
   int C, hRT, eg, emg, cpR;                       // n-vectors
-  int q, dqdT;                                    // R-vectors
+  int q;                                          // R-vector
   int S;                                          // nnz_S
-  int LU, dinv;                                   // nnz_LU, m (aliases the derivative slots)
-  int D;                                          // n_dslot
+  int LU, dinv;                                   // nnz_LU, m
+  int D;                                          // Jacobian pass region (aliases LU and dinv)
   int part;                                       // partial sums of the gathers
   int misc;                                       // 16 scalars
   int total;                                      // doubles per cell

@@ -4,7 +4,32 @@
 // forward integrator's arithmetic is unchanged by the templating.
 #pragma once
 
+#include "exp_table.h"
+
 namespace chemgb {
+
+// e^x by table-driven reduction (Tang, ACM TOMS 15(2), 1989), in a variant with 256 table entries:
+//   k = nearest integer to 256 x / ln2, read from the low word of x * 256/ln2 + 1.5 * 2^52;
+//   r = x - k ln2/256 in two fused steps (the first is exact because k * kExpCHi is), |r| <= ln2/512;
+//   e^r - 1 = r (1 + r/2 + r^2/6 + r^3/24), truncation below r^5/120 < 4e-17 relative;
+//   e^x = 2^m * T[j] * e^r with k = 256 m + j, the power of two added to the exponent field.
+// Nine FP64 operations; error about one ulp.  |x| >= 704 (results near overflow or in the subnormal
+// range) and NaN take the library exp.
+__device__ __forceinline__ double fast_exp(double x) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40860000) return exp(x);
+  constexpr double kShift = 0x1.8p52;
+  const double t = fma(x, kExpInvC, kShift);
+  const int k = __double2loint(t);
+  const double kd = t - kShift;
+  double r = fma(kd, -kExpCHi, x);
+  r = fma(kd, -kExpCLo, r);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  q = fma(r, q, 1.0);
+  const double tj = __ldg(kExpTab + (k & 255));
+  const double e = fma(tj, r * q, tj);
+  return __hiloint2double(__double2hiint(e) + (k >> 8) * (1 << 20), __double2loint(e));
+}
 
 struct Dual {
   double v, d;
@@ -42,9 +67,9 @@ __device__ __forceinline__ double sfma(double a, double b, double c) { return fm
 __device__ __forceinline__ Dual sfma(Dual a, Dual b, Dual c) {
   return Dual(fma(a.v, b.v, c.v), fma(a.v, b.d, fma(a.d, b.v, c.d)));
 }
-__device__ __forceinline__ double sexp(double a) { return exp(a); }
+__device__ __forceinline__ double sexp(double a) { return fast_exp(a); }
 __device__ __forceinline__ Dual sexp(Dual a) {
-  const double e = exp(a.v);
+  const double e = fast_exp(a.v);
   return Dual(e, a.d * e);
 }
 __device__ __forceinline__ double slog(double a) { return log(a); }

@@ -1,0 +1,84 @@
+"""Autotuner host logic (sample selection, search space, cache) on CPU, and on the GPU: a tuned launch
+shape is one of the candidates, and every launch shape gives bit-identical results."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2311_14941_gb300 import autotune, synth
+
+
+def test_sample_keeps_the_cost_distribution():
+    rng = np.random.default_rng(1)
+    cost = np.maximum(1, rng.lognormal(4, 1.2, 100000)).astype(np.int64)
+    idx = autotune.sample_cells(len(cost), cost, 4096)
+    assert len(idx) <= 4096 and len(idx) > 4000 and np.all(np.diff(idx) > 0)
+    qs = [0.1, 0.5, 0.9, 0.99]
+    assert np.allclose(np.quantile(cost[idx], qs), np.quantile(cost, qs), rtol=0.05)
+    assert cost[idx].max() == cost.max()
+
+
+def test_sample_without_counts_is_seeded_random_and_small_fields_are_whole():
+    a = autotune.sample_cells(50000, None, 1000)
+    b = autotune.sample_cells(50000, np.zeros(50000, np.int32), 1000)
+    assert np.array_equal(a, b) and len(a) == 1000
+    assert np.array_equal(autotune.sample_cells(500, None, 1000), np.arange(500))
+
+
+def test_search_space():
+    c = autotune.candidates(7)
+    assert {x["mode"] for x in c} == {0, 1}
+    assert {x["block_warps"] for x in c} == {1, 2, 4, 7}
+    assert all(x["chunk"] == 1 for x in c if x["mode"] == 0)
+    assert len({json.dumps(x, sort_keys=True) for x in c}) == len(c)
+    assert {x["block_warps"] for x in autotune.candidates(1)} == {1, 2, 4}
+
+
+def test_digest_depends_on_every_parameter():
+    m = synth.mechanism_small()
+    d0 = autotune.mechanism_digest(m)
+    assert d0 == autotune.mechanism_digest(synth.mechanism_small())
+    m.Ea[3] *= 1.0000001
+    assert autotune.mechanism_digest(m) != d0
+
+
+def test_cache_roundtrip(tmp_path, monkeypatch):
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "c.json"))
+    assert autotune._load() == {}
+    autotune._store("k1", {"mode": 1, "block_warps": 2, "chunk": 1})
+    autotune._store("k2", {"mode": 0, "block_warps": 1, "chunk": 1})
+    got = autotune._load()
+    assert got["k1"]["block_warps"] == 2 and got["k2"]["mode"] == 0
+    assert autotune.launch_options(got["k1"]) == {"mode": 1, "block_warps": 2, "chunk": 1}
+
+
+@pytest.mark.gpu
+def test_gpu_every_launch_shape_gives_identical_results_and_tune_picks_one(tmp_path, monkeypatch):
+    import torch
+    from paper_2311_14941_gb300 import chem
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "c.json"))
+    m = synth.mechanism_methane_sized()
+    F = synth.field_bimodal_jet(m, 48, 48, seed=3)
+    h = chem.create(m, 0)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    N = F.n_cells
+    ns_prev = torch.tensor(np.random.default_rng(2).integers(1, 300, N).astype(np.int32), device=dev)
+    ref = None
+    wmax = max(1, 227 * 1024 // h.info["smem_per_cell"])
+    for c in autotune.candidates(wmax):
+        T, Y = t(F.T), t(F.Y.reshape(-1))
+        hio = torch.zeros(N, dtype=torch.float64, device=dev)
+        ns = ns_prev.clone()
+        st = torch.zeros(N, dtype=torch.int32, device=dev)
+        h.integrate(T, t(F.p), Y, t(F.dt), hio, ns, st, **c)
+        out = (T.cpu().numpy(), Y.cpu().numpy(), hio.cpu().numpy(), ns.cpu().numpy(), st.cpu().numpy())
+        if ref is None:
+            ref = out
+        for a, b in zip(out, ref):
+            assert np.array_equal(a, b), c
+    r = autotune.tune(h, t(F.T), t(F.p), t(F.Y.reshape(-1)), t(F.dt), ns_prev, sample=1024)
+    assert autotune.launch_options(r) in autotune.candidates(wmax)
+    assert len(r["table"]) == len(autotune.candidates(wmax)) and r["ms"] > 0
+    assert autotune.tune(h, t(F.T), t(F.p), t(F.Y.reshape(-1)), t(F.dt), ns_prev, sample=1024) == \
+        json.loads(json.dumps(r))

@@ -105,6 +105,9 @@ typedef struct {
   int solve_steps;    /* warp-wide steps of one forward+backward solve */
   int smem_per_cell;  /* bytes of shared memory one cell needs in the integrator */
   int n_dslots;       /* per-reaction derivative slots used by the Jacobian */
+  int jac_passes;     /* passes of the Jacobian's reaction loop (their scratch shares the factor's space) */
+  int smem_adjoint_per_cell;  /* bytes of shared memory one cell needs in chem_adjoint's reverse pass
+                                 (checkpoint interval 16) */
 } chem_info_t;
 
 /* Options of chem_integrate (zero-initialise, then set; zero/negative fields take the defaults). */
@@ -228,10 +231,11 @@ chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double
 
 /* Diagnostic: evaluates an elementary function of the device code on N doubles (device pointers x, y,
    y[i] = f(x[i])): fn 0 = the library's table-driven exponential (used for every rate constant,
-   equilibrium constant and fall-off factor), fn 1 = the CUDA math library's exp on the same inputs.
-   It has no counterpart in the paper; it exists so that the library's exponential can be checked
-   against CUDA's.  Runs on the current device.  CHEM_EINVAL for fn outside {0, 1}, N < 0 or null
-   pointers with N > 0. */
+   equilibrium constant and fall-off factor), fn 1 = the CUDA math library's exp, fn 2 = the
+   library's table-driven logarithm (ln T, ln [M] and ln F_cent of the fall-off), fn 3 = the CUDA math
+   library's log.  It has no counterpart in the paper; it exists so that the library's functions can be
+   checked against CUDA's.  Runs on the current device.  CHEM_EINVAL for fn outside {0, 1, 2, 3},
+   N < 0 or null pointers with N > 0. */
 chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem_stream stream);
 
 #ifdef __cplusplus

@@ -37,7 +37,8 @@ class MechDescC(C.Structure):
 class InfoC(C.Structure):
     _fields_ = [("n_species", C.c_int), ("n_reactions", C.c_int), ("n_state", C.c_int), ("nnz_S", C.c_int),
                 ("nnz_LU", C.c_int), ("lu_steps", C.c_int), ("solve_steps", C.c_int),
-                ("smem_per_cell", C.c_int), ("n_dslots", C.c_int)]
+                ("smem_per_cell", C.c_int), ("n_dslots", C.c_int), ("jac_passes", C.c_int),
+                ("smem_adjoint_per_cell", C.c_int)]
 
 
 class OptsC(C.Structure):
@@ -256,7 +257,8 @@ class Mechanism:
 
 
 def eval_elementary(fn: int, x, y, stream=None):
-    """chem_eval_elementary: y = f(x) on the device (fn 0 library exp, 1 CUDA exp)."""
+    """chem_eval_elementary: y = f(x) on the device (fn 0 library exp, 1 CUDA exp, 2 library log,
+    3 CUDA log)."""
     import torch
     N = x.numel()
     _check(lib().chem_eval_elementary(fn, N, _dptr(x, torch.float64, N, "x"), _dptr(y, torch.float64, N, "y"),

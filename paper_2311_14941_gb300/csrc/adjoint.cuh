@@ -27,10 +27,11 @@ struct AdjLayout {
   int Y3, Y4, AU1, AU2, AU3, AU4, W1, W2, W3, W4, MU1, MU2, MU3, MU4, LAM, G, ZT, WS;   // m-vectors
   int SY, UY, VY;      // S, u, v at y (the step's own Jacobian)
   int A;               // n: participant coefficients of the parameter terms
-  int SEG;             // K*m: recomputed states of one segment
-  int GA, GE;          // R: gradient accumulators (compiled reaction order)
   int total;
 };
+// Per-warp global memory of the reverse pass (touched once per step, so kept out of shared memory):
+// the recomputed states of one segment (K*m) and the cell's gradient accumulators (2R, compiled
+// reaction order).
 
 // out = J^T w = S^T w + v (u . w) with S in the internal entry order
 template <class Sc>
@@ -82,9 +83,8 @@ __device__ __forceinline__ void lu_solveT(const MechView& M, const double* s, co
   const ElimOp* op = M.svT_ops + lane;
   for (int st = 0; st < M.svT_steps; ++st, op += kWarp) {
     const ElimOp o = ld_eop(op);
-    const int kind = __ldg(M.svT_kind + st);
     if (o.t != OP_IDLE) {
-      if (kind == K_UPDATE) x[o.t] = fma(-LU[o.a], x[o.b], x[o.t]);
+      if (o.kind == K_UPDATE) x[o.t] = fma(-LU[o.a], x[o.b], x[o.t]);
       else x[o.t] *= dinv[o.a];
     }
     __syncwarp();
@@ -109,10 +109,12 @@ __device__ __forceinline__ void vset(double* dst, const double* src, int m, int 
   __syncwarp();
 }
 
-// One adjoint step at state y (in A.SEG) with step h.  lambda (A.LAM) is updated in place.
-// Returns false if the factor is singular (cannot happen for a step the forward pass accepted).
+// One adjoint step at state y (a row of the segment) with step h.  lambda (A.LAM) is updated in place,
+// the parameter gradients accumulate into GA, GE.  Returns false if the factor is singular (cannot
+// happen for a step the forward pass accepted).
 __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
-                                             const CellLayout& Ld, const double* y, double p, double h, int lane) {
+                                             const CellLayout& Ld, const double* y, double p, double h,
+                                             double* GA, double* GE, int lane) {
   const CellLayout& L = A.L;
   const int m = M.m;
   const double ih = 1.0 / h;
@@ -120,7 +122,6 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
   double* W1 = s + A.W1; double* W2 = s + A.W2; double* W3 = s + A.W3; double* W4 = s + A.W4;
   double* MU1 = s + A.MU1; double* MU2 = s + A.MU2; double* MU3 = s + A.MU3; double* MU4 = s + A.MU4;
   double* LAM = s + A.LAM; double* G = s + A.G; double* Y3 = s + A.Y3; double* Y4 = s + A.Y4;
-  double* GA = s + A.GA; double* GE = s + A.GE;
   // ---- forward quantities of the step (same arithmetic as the forward attempt)
   vset(s + L.y, y, m, lane);
   eval_jac<double>(M, s, L, s + L.y, p, lane);
@@ -239,10 +240,9 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
 __device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
                                              const CellLayout& Ld, double p, int n_acc, const double* rec_h,
                                              const double* rec_ck, int K, int N, int cell, int lane,
-                                             const IntOpts& o) {
+                                             const IntOpts& o, double* seg, double* GA, double* GE) {
   const int m = M.m;
   const CellLayout& L = A.L;
-  double* seg = s + A.SEG;
   const int nseg = (n_acc + K - 1) / K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int n0 = sg * K, n1 = min(n_acc, n0 + K);
@@ -257,7 +257,8 @@ __device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const
       vset(seg + (size_t)(nn - n0 + 1) * m, s + L.ytmp, m, lane);
     }
     for (int nn = n1 - 1; nn >= n0; --nn)
-      if (!adjoint_step(M, s, A, dw, Ld, seg + (size_t)(nn - n0) * m, p, rec_h[(size_t)nn * N + cell], lane))
+      if (!adjoint_step(M, s, A, dw, Ld, seg + (size_t)(nn - n0) * m, p, rec_h[(size_t)nn * N + cell], GA, GE,
+                        lane))
         return false;
   }
   return true;

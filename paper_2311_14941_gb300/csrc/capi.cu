@@ -109,8 +109,6 @@ AdjLayout make_adj_layout(const HostMech& hm, int K) {
   A.MU3 = take(m); A.MU4 = take(m); A.LAM = take(m); A.G = take(m); A.ZT = take(m); A.WS = take(m);
   A.SY = take(hm.nnz_S); A.UY = take(m); A.VY = take(m);
   A.A = take(hm.n);
-  A.SEG = take(K * m);
-  A.GA = take(std::max(hm.R, 1)); A.GE = take(std::max(hm.R, 1));
   A.total = o;
   return A;
 }
@@ -316,34 +314,39 @@ __global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const d
                           const double* __restrict__ rec_h, const double* __restrict__ rec_ck,
                           const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
                           const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
-                          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head, Dual* dual_ws,
-                          IntOpts o) {
+                          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head,
+                          const int* __restrict__ perm, Dual* dual_ws, double* warp_ws, IntOpts o) {
   extern __shared__ double smem[];
   const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int gw = blockIdx.x * wpb + w;
   double* s = smem + (size_t)w * A.total;
-  Dual* dw = dual_ws + (size_t)(blockIdx.x * wpb + w) * Ld.total;
+  Dual* dw = dual_ws + (size_t)gw * Ld.total;
   const int m = M.m;
+  double* seg = warp_ws + (size_t)gw * ((size_t)K * m + 2 * (size_t)M.R);
+  double* GA = seg + (size_t)K * m;
+  double* GE = GA + M.R;
   while (true) {
     int c = 0;
     if (lane == 0) c = atomicAdd(head, 1);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= N) break;
+    c = perm[c];   // costliest cells (longest tapes) first
     const int na = rec_n[c];
     double* LAM = s + A.LAM;
     for (int i = lane; i < m; i += kWarp) LAM[i] = (i == 0) ? gT[c] : gY[(size_t)(i - 1) * N + c];
-    for (int r = lane; r < M.R; r += kWarp) { s[A.GA + r] = 0.0; s[A.GE + r] = 0.0; }
+    for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
     __syncwarp();
     bool ok = na >= 0;
-    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, lane, o);
+    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, lane, o, seg, GA, GE);
     if (!ok) {
       for (int i = lane; i < m; i += kWarp) LAM[i] = 0.0;
-      for (int r = lane; r < M.R; r += kWarp) { s[A.GA + r] = 0.0; s[A.GE + r] = 0.0; }
+      for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
       __syncwarp();
     }
     for (int r = lane; r < M.R; r += kWarp) {
       const int d = __ldg(M.rx_order + r);
-      grad_cell[(size_t)d * N + c] = s[A.GA + r];
-      grad_cell[(size_t)(M.R + d) * N + c] = s[A.GE + r];
+      grad_cell[(size_t)d * N + c] = GA[r];
+      grad_cell[(size_t)(M.R + d) * N + c] = GE[r];
     }
     if (gT0 && lane == 0) gT0[c] = LAM[0];
     if (gY0)
@@ -575,6 +578,8 @@ chem_status chem_info(chem_handle h, chem_info_t* info) {
   info->solve_steps = (int)h->hm.sv_kind.size();
   info->smem_per_cell = h->cell_bytes;
   info->n_dslots = h->hm.n_dslot;
+  info->jac_passes = (int)h->hm.g_jac.size();
+  info->smem_adjoint_per_cell = make_adj_layout(h->hm, 16).total * (int)sizeof(double);
   return CHEM_OK;
 }
 
@@ -799,7 +804,8 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   const size_t b_ns = align_up((size_t)N * 4, 256);
   const size_t b_gc = grad_cell ? 0 : align_up((size_t)2 * hm.R * N * 8, 256);
   const size_t b_dw = align_up((size_t)grid * h->L.total * sizeof(Dual), 256);
-  const size_t need = b_head + b_rh + b_ck + b_rn + b_hio + b_ns + b_gc + b_dw;
+  const size_t b_ww = align_up((size_t)grid * ((size_t)K * m + 2 * (size_t)hm.R) * 8, 256);
+  const size_t need = b_head + b_rh + b_ck + b_rn + b_hio + b_ns + b_gc + b_dw + b_ww;
   if (need > h->adj_scratch_bytes) {
     if (h->adj_scratch) cudaFree(h->adj_scratch);
     h->adj_scratch = nullptr;
@@ -819,7 +825,8 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   int* nsub = (int*)q; q += b_ns;
   double* gcell = grad_cell;
   if (!gcell) { gcell = (double*)q; q += b_gc; }
-  Dual* dws = (Dual*)q;
+  Dual* dws = (Dual*)q; q += b_dw;
+  double* wws = (double*)q;
   cudaStream_t strm = (cudaStream_t)stream;
   // forward pass with the tape
   io.rec_h = rec_h; io.rec_ck = rec_ck; io.rec_n = rec_n; io.rec_cap = cap; io.rec_K = K;
@@ -827,12 +834,19 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   k_integrate_plain<<<N, kWarp, h->cell_bytes, strm>>>(h->view, h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
                                                        io, nullptr, 0ull);
   if ((st = launch_check("chem_adjoint forward launch")) != CHEM_OK) return st;
-  // reverse pass
+  // reverse pass, cells ordered by tape length (longest first) as in the sorted work queue
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr;
+  if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
+  char* scr = (char*)h->scratch;
+  int* perm = (int*)(scr + kScrPerm);
+  if ((e = cudaMemsetAsync(scr, 0, kScrHead + 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
+  k_sort_count<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts));
+  k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts), (int*)(scr + kScrCursor), perm);
   if ((e = cudaMemsetAsync(head, 0, 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   CellLayout Ld = h->L;
   k_adjoint<<<grid, kWarp, adj_bytes, strm>>>(h->view, A, Ld, N, p, rec_h, rec_ck, rec_n, K, gT, gY, gcell, gT0, gY0,
-                                               status, head, dws, io);
+                                               status, head, perm, dws, wws, io);
   if ((st = launch_check("chem_adjoint reverse launch")) != CHEM_OK) return st;
   const int P = 2 * hm.R;
   if (P > 0) {
@@ -925,12 +939,14 @@ namespace {
 __global__ void k_elementary(int fn, int N, const double* __restrict__ x, double* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  y[i] = fn == 0 ? fast_exp(x[i]) : exp(x[i]);
+  const double v = x[i];
+  y[i] = fn == 0 ? fast_exp(v) : fn == 1 ? exp(v) : fn == 2 ? fast_log(v) : log(v);
 }
 }  // namespace
 
 extern "C" chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem_stream stream) {
-  if (fn < 0 || fn > 1) return fail(CHEM_EINVAL, "fn must be 0 (library exp) or 1 (CUDA exp)");
+  if (fn < 0 || fn > 3)
+    return fail(CHEM_EINVAL, "fn must be 0 (library exp), 1 (CUDA exp), 2 (library log) or 3 (CUDA log)");
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
   if (N == 0) return CHEM_OK;
   if (!x || !y) return fail(CHEM_EINVAL, "null array argument");

@@ -172,9 +172,10 @@ bool schedule(std::vector<DagOp>& ops, std::vector<ElimOp>& out, std::vector<uin
         keep.push_back(v);
       }
     }
-    for (int l = 0; l < kWarp; ++l) {
-      if (l < (int)step.size()) out.push_back(ops[step[l]].enc);
-      else out.push_back(ElimOp{OP_IDLE, 0, 0, 0});
+    for (int l = 0; l < kWarp; ++l) {   // every lane's op carries the step's kind
+      ElimOp e = l < (int)step.size() ? ops[step[l]].enc : ElimOp{OP_IDLE, 0, 0, 0};
+      e.kind = (uint16_t)K;
+      out.push_back(e);
     }
     kinds.push_back((uint8_t)K);
     newly.clear();

@@ -52,7 +52,7 @@ __device__ __forceinline__ ElimOp ld_eop(const ElimOp* p) {
   uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
   ElimOp o;
   o.t = (uint16_t)(v.x & 0xFFFF); o.a = (uint16_t)(v.x >> 16);
-  o.b = (uint16_t)(v.y & 0xFFFF); o.pad = 0;
+  o.b = (uint16_t)(v.y & 0xFFFF); o.kind = (uint16_t)(v.y >> 16);
   return o;
 }
 
@@ -74,8 +74,14 @@ template <bool ACC = false, class Sc, class F>
 __device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F valf, int lane) {
   Sc acc = Sc(0.0);
   const GatherOp* op = G.ops + lane;
-  for (int s = 0; s < G.steps; ++s, op += kWarp) {
-    GatherOp o = ld_gop(op);
+  const int NS = G.steps;
+  const GatherOp idle{0, 0, DST_NONE, 1};
+  GatherOp n1 = NS > 0 ? ld_gop(op) : idle;
+  GatherOp n2 = NS > 1 ? ld_gop(op + kWarp) : idle;
+  for (int s = 0; s < NS; ++s) {
+    const GatherOp o = n1;
+    n1 = n2;
+    if (s + 2 < NS) n2 = ld_gop(op + (size_t)(s + 2) * kWarp);
     if (!(o.flags & 1)) acc += valf(o.a, o.b);
     if (o.dst != DST_NONE) {
       if (o.dst & PARTIAL_BIT) part[o.dst & 0x7FFF] = acc;
@@ -220,11 +226,17 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
     const Sc nn = sfma(Sc(-1.27), Lc, Sc(0.75));
     const Sc xx = sfma(lnPr, Sc(kInvLn10), cc);
     const Sc den = sfma(Sc(-0.14), xx, nn);
-    const Sc iden = 1.0 / den;
+    // three reciprocals from one division: 1/den, 1/(1 + f1^2) = den^2/S2 with S2 = den^2 + xx^2, and
+    // 1/(1 + Pr), all from R = 1/(den S2 (1 + Pr))
+    const Sc pr1 = 1.0 + Pr;
+    const Sc S2 = sfma(xx, xx, den * den);
+    const Sc dp = den * pr1;
+    const Sc R = 1.0 / (dp * S2);
+    const Sc iden = S2 * pr1 * R;
     const Sc f1 = xx * iden;
-    const Sc ib = 1.0 / sfma(f1, f1, Sc(1.0));
+    const Sc ib = den * dp * R * den;
     const Sc F = sexp(Lc * ib * kLn10);
-    const Sc ipr1 = 1.0 / (1.0 + Pr);
+    const Sc ipr1 = den * S2 * R;
     kf = kf * (Pr * ipr1) * F;
     if (DERIV) {
       const Sc dlnk0_dT = sfma(Sc(__ldg(D + 5)), sc.invT, Sc(__ldg(D + 4))) * sc.invT;
@@ -446,7 +458,7 @@ __device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, co
     const ElimOp o = n1;
     n1 = n2;
     if (st + 2 < NS) n2 = ld_eop(op + (size_t)(st + 2) * kWarp);
-    const int kind = __ldg(M.lu_kind + st);
+    const int kind = o.kind;
     if (o.t != OP_IDLE) {
       if (kind == K_UPDATE) {
         LU[o.t] = fma(-LU[o.a], LU[o.b], LU[o.t]);
@@ -473,22 +485,25 @@ __device__ __forceinline__ void lu_solve_impl(const MechView& M, const double* s
   const double* dinv = s + L.dinv;
   const ElimOp* op = M.sv_ops + lane;
   const int S = M.sv_steps;
-  ElimOp n1 = S > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, 0};
-  ElimOp n2 = S > 1 ? ld_eop(op + kWarp) : ElimOp{OP_IDLE, 0, 0, 0};
+  // the factor does not change during the solve: each step's coefficient (L/U entry or 1/pivot; idle
+  // ops read entry 0) is loaded one step ahead, off the step-to-step dependence through x
+  auto coef = [&](const ElimOp& o) { return (o.kind == K_UPDATE ? LU : dinv)[o.a]; };
+  ElimOp n1 = S > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, K_SCALE};
+  ElimOp n2 = S > 1 ? ld_eop(op + kWarp) : ElimOp{OP_IDLE, 0, 0, K_SCALE};
+  double c1 = coef(n1);
   for (int st = 0; st < S; ++st) {
     const ElimOp o = n1;
+    const double c = c1;
     n1 = n2;
+    c1 = coef(n1);
     if (st + 2 < S) n2 = ld_eop(op + (size_t)(st + 2) * kWarp);
-    const int kind = __ldg(M.sv_kind + st);
     if (o.t != OP_IDLE) {
-      if (kind == K_UPDATE) {
-        const double l = LU[o.a];
-        x[o.t] = fma(-l, x[o.b], x[o.t]);
-        if (TWO) x2[o.t] = fma(-l, x2[o.b], x2[o.t]);
+      if (o.kind == K_UPDATE) {
+        x[o.t] = fma(-c, x[o.b], x[o.t]);
+        if (TWO) x2[o.t] = fma(-c, x2[o.b], x2[o.t]);
       } else {
-        const double d = dinv[o.a];
-        x[o.t] *= d;
-        if (TWO) x2[o.t] *= d;
+        x[o.t] *= c;
+        if (TWO) x2[o.t] *= c;
       }
     }
     __syncwarp();

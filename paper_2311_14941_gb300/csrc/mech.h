@@ -48,8 +48,9 @@ constexpr uint16_t PARTIAL_BIT = 0x8000;
 // Elimination / solve program: step s has one kind; lane l executes op[s*32 + l] (t == OP_IDLE: idle).
 //   LU:    K_RECIP  dinv[t] = 1 / LU[a]      K_SCALE  LU[t] *= dinv[a]     K_UPDATE LU[t] -= LU[a] * LU[b]
 //   solve: K_SCALE  x[t] *= dinv[a]          K_UPDATE x[t] -= LU[a] * x[b]
+// Every op of a step, idle ones included, carries the step's kind.
 struct ElimOp {
-  uint16_t t, a, b, pad;
+  uint16_t t, a, b, kind;
 };
 constexpr uint16_t OP_IDLE = 0xFFFF;
 enum : int { K_RECIP = 0, K_SCALE = 1, K_UPDATE = 2 };

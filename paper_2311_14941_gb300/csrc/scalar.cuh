@@ -4,7 +4,7 @@
 // forward integrator's arithmetic is unchanged by the templating.
 #pragma once
 
-#include "exp_table.h"
+#include "elementary_tables.h"
 
 namespace chemgb {
 
@@ -67,13 +67,43 @@ __device__ __forceinline__ double sfma(double a, double b, double c) { return fm
 __device__ __forceinline__ Dual sfma(Dual a, Dual b, Dual c) {
   return Dual(fma(a.v, b.v, c.v), fma(a.v, b.d, fma(a.d, b.v, c.d)));
 }
+// ln x by table-driven reduction (Tang, ACM TOMS 16(4), 1990), in a variant with 256 table entries:
+//   x = 2^k y, y in [1, 2); j = top 8 bits of y's fraction; u = y c_j - 1 with c_j the rounded reciprocal
+//   of the centre of y's interval (1 and 2 for the first and last intervals), |u| <= 2^-8;
+//   ln x = (k ln2_lead + lnF_lead_j) + (k ln2_trail + lnF_trail_j + log1p(u)), where lnF_j = -ln c_j
+//   (so the rounding of c_j needs no correction) and the first sum is exact (leads on the grid 2^-43);
+//   log1p(u) = u - u^2 (1/2 - u/3 + u^2/4 - u^3/5 + u^4/6 - u^5/7), truncation below 2^-59 relative.
+// Thirteen FP64 operations; error about one ulp; ln of values near 1 keeps full relative accuracy.
+// Zero, negative, subnormal, infinite and NaN arguments take the library log.
+__device__ __forceinline__ double fast_log(double x) {
+  const int hx = __double2hiint(x);
+  if (hx < 0x00100000 || hx >= 0x7ff00000) return log(x);
+  const int k = (hx >> 20) - 1023;
+  const int j = (hx >> 12) & 0xff;
+  const double y = __hiloint2double((hx & 0x000fffff) | 0x3ff00000, __double2loint(x));
+  const double* tb = kLogTab[j];
+  const double c = __ldg(tb), lead = __ldg(tb + 1), trail = __ldg(tb + 2);
+  const double u = fma(y, c, -1.0);
+  double q = fma(u, -1.0 / 7.0, 1.0 / 6.0);
+  q = fma(u, q, -1.0 / 5.0);
+  q = fma(u, q, 1.0 / 4.0);
+  q = fma(u, q, -1.0 / 3.0);
+  q = fma(u, q, 0.5);
+  const double p = fma(-(u * u), q, u);
+  // k as a double without a conversion instruction: 2^52 + 2^31 + k from its bits, minus 2^52 + 2^31
+  const double kd = __hiloint2double(0x43300000, k ^ (int)0x80000000) - 0x1.00000800p52;
+  const double t1 = fma(kd, kLn2Lead, lead);
+  const double t2 = fma(kd, kLn2Trail, trail) + p;
+  return t1 + t2;
+}
+
 __device__ __forceinline__ double sexp(double a) { return fast_exp(a); }
 __device__ __forceinline__ Dual sexp(Dual a) {
   const double e = fast_exp(a.v);
   return Dual(e, a.d * e);
 }
-__device__ __forceinline__ double slog(double a) { return log(a); }
-__device__ __forceinline__ Dual slog(Dual a) { return Dual(log(a.v), a.d / a.v); }
+__device__ __forceinline__ double slog(double a) { return fast_log(a); }
+__device__ __forceinline__ Dual slog(Dual a) { return Dual(fast_log(a.v), a.d / a.v); }
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(Dual a) { return a.v; }
 __device__ __forceinline__ double tangent(Dual a) { return a.d; }

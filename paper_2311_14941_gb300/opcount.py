@@ -3,9 +3,8 @@
 The path is bound by the FP64 pipe (2 DFMA lanes per clock per SM on GB300), not by memory or tensor
 cores.  Work is counted in FP64 pipe slots of an ideal implementation of the same algorithm: every
 useful add, multiply or fused multiply-add is one slot; a divide, exp or log is charged the slots it
-occupies on this GPU, measured relative to DFMA by a microbenchmark (divide 6, log 34, sqrt 6, pow 60;
-exp 11 for the library's table-driven exponential, whose nine FP64 operations plus integer and table
-work measure 11 slots, against 18 for the CUDA math library's exp).  Idle lanes, redundant recomputation and index arithmetic are not counted.  Reported
+occupies on this GPU, measured relative to DFMA by a microbenchmark (divide 6, sqrt 6, pow 60; exp 11
+and log 13 for the library's table-driven functions, against 18 and 34 for the CUDA math library's).  Idle lanes, redundant recomputation and index arithmetic are not counted.  Reported
 as TFLOP/s-equivalent = 2 x slots/s, so a kernel that kept the pipe busy with useful DFMAs would read
 the FP64 peak: 2 slots/clk/SM x 152 SMs x 2.07 GHz x 2 = 1.259 TFLOP/s.
 
@@ -23,7 +22,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-DIV, EXP, LOG, SQRT, POW = 6, 11, 34, 6, 60
+DIV, EXP, LOG, SQRT, POW = 6, 11, 13, 6, 60
 SLOTS_PER_CLK_SM = 2
 FLOP_PER_SLOT = 2
 

@@ -1,5 +1,6 @@
-"""The library's table-driven exponential (Tang's reduction, 256 entries) against CUDA's exp and against
-the host libm, in units in the last place, on random and boundary arguments."""
+"""The library's table-driven exponential and logarithm (Tang's reductions, 256 entries each) against
+CUDA's exp and log and against the host libm, in units in the last place, on random and boundary
+arguments."""
 import numpy as np
 import pytest
 
@@ -62,8 +63,51 @@ def test_library_exp_special_values():
     assert out[5] == 1.0
 
 
+def _log_args():
+    rng = np.random.default_rng(8)
+    parts = [np.exp(rng.uniform(-700.0, 700.0, 1 << 20)),
+             rng.uniform(200.0, 4000.0, 1 << 18),              # ln T
+             1.0 + rng.uniform(-1e-2, 1e-2, 1 << 18),          # near 1: ln F_cent, ln P_r
+             1.0 + rng.uniform(-1e-9, 1e-9, 1 << 16),
+             np.ldexp(1.0, np.arange(-1022, 1024)),
+             np.nextafter(np.ldexp(1.0, np.arange(-1021, 1024)), 0.0),
+             np.array([1.0, 0.5, 2.0, np.nextafter(1.0, 0.0), np.nextafter(1.0, 2.0), 1e-300, 1e300,
+                       np.finfo(np.float64).max, np.finfo(np.float64).tiny])]
+    return np.concatenate(parts)
+
+
+def test_library_log_matches_cuda_log_within_one_ulp():
+    from paper_2311_14941_gb300 import chem
+    x = _log_args()
+    xd = torch.tensor(x, device="cuda")
+    y0 = torch.empty_like(xd)
+    y1 = torch.empty_like(xd)
+    chem.eval_elementary(2, xd, y0)
+    chem.eval_elementary(3, xd, y1)
+    torch.cuda.synchronize()
+    ours, cuda = y0.cpu().numpy(), y1.cpu().numpy()
+    ref = np.log(x)
+    # same sign and within one ulp (ulp distance of the magnitudes; ln 1 = 0 exactly)
+    assert np.array_equal(np.sign(ours), np.sign(ref)) and ours[x == 1.0].tolist() == [0.0] * int(np.sum(x == 1.0))
+    d_cuda = _ulps(np.abs(ours), np.abs(cuda))
+    d_libm = _ulps(np.abs(ours), np.abs(ref))
+    assert d_cuda.max() <= 1, (x[np.argmax(d_cuda)], d_cuda.max())
+    assert d_libm.max() <= 1, (x[np.argmax(d_libm)], d_libm.max())
+    assert np.mean(d_libm == 0) > 0.9
+
+
+def test_library_log_special_values():
+    from paper_2311_14941_gb300 import chem
+    x = torch.tensor([0.0, -1.0, np.inf, np.nan, 5e-324, 1.0], device="cuda", dtype=torch.float64)
+    y = torch.empty_like(x)
+    chem.eval_elementary(2, x, y)
+    out = y.cpu().numpy()
+    assert out[0] == -np.inf and np.isnan(out[1]) and out[2] == np.inf and np.isnan(out[3])
+    assert out[4] == np.log(5e-324) and out[5] == 0.0
+
+
 def test_eval_elementary_rejects_bad_arguments():
     from paper_2311_14941_gb300 import chem
     x = torch.zeros(4, device="cuda", dtype=torch.float64)
     with pytest.raises(chem.ChemError):
-        chem.eval_elementary(2, x, x)
+        chem.eval_elementary(4, x, x)

@@ -418,7 +418,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "reactor-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(config(args.workload, args.mode), n_cells=N),
+        "config": dict(config(args.workload, args.mode), n_cells=N,
+                       warps_per_cell=int(h.info["auto_warps_per_cell"])),
         "e2e": {"value": world * N * e2e_steps / t_e2e, "unit": "reactor-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * (4 if args.mode == "persistent" else 1),

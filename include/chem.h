@@ -108,6 +108,11 @@ typedef struct {
   int jac_passes;     /* passes of the Jacobian's reaction loop (their scratch shares the factor's space) */
   int smem_adjoint_per_cell;  /* bytes of shared memory one cell needs in chem_adjoint's reverse pass
                                  (checkpoint interval 16) */
+  /* launch limits on the handle's device (0 for host-only handles), per warps-per-cell choice [1, 2]:
+     the largest block in cells, the most cells resident per SM, and the library's automatic choice */
+  int max_block_cells[2];
+  int resident_cells[2];
+  int auto_warps_per_cell;
 } chem_info_t;
 
 /* Options of chem_integrate (zero-initialise, then set; zero/negative fields take the defaults). */
@@ -119,9 +124,11 @@ typedef struct {
   double time_budget_s;   /* wall-clock budget of the call on the device; 0: none */
   int max_substeps;       /* default 100000 attempts per cell */
   int max_nonfinite;      /* default 10 consecutive non-finite attempts (each divides h by 10) */
-  int mode;               /* 0: plain one-warp-per-cell launch (reference form); 1: persistent
-                             work-queue kernel over cells sorted by their previous substep count */
-  int block_warps;        /* warps (cells in flight) per block; 0: automatic */
+  int mode;               /* 0: plain launch, one lane group per cell in index order (reference form);
+                             1: persistent work-queue kernel over cells sorted by their previous
+                             substep count */
+  int block_cells;        /* cells in flight per block (each takes warps_per_cell warps); 0: automatic;
+                             larger requests are reduced to the largest block that launches */
   int chunk;              /* cells taken per queue pull in mode 1; 0: automatic */
   int* naccept;           /* optional DEVICE array [N]: accepted steps per cell (NULL: not written) */
   double* trace;          /* optional DEVICE array [trace_cap*N]: attempt i of cell c at trace[i*N + c],
@@ -129,6 +136,12 @@ typedef struct {
   int trace_cap;          /* attempts recorded per cell */
   int ckpt_every;         /* chem_adjoint: accepted steps between checkpoints (default 16, at most 64) */
   int tape_steps;         /* chem_adjoint: accepted steps the tape holds per cell (default 4096) */
+  int warps_per_cell;     /* chem_integrate and chem_integrate_noalloc: lanes of one cell, 1 (one warp) or
+                             2 (two warps of a block; wider reaction and species loops and more warps in
+                             flight for mechanisms whose cells fill shared memory); 0: automatic (two when
+                             one-warp cells leave fewer than 6 per SM, see chem_info).  Results of the two
+                             choices agree to rounding, not bit for bit (different summation orders).
+                             chem_adjoint uses one warp per cell. */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,
@@ -157,7 +170,8 @@ chem_status chem_jacobian_pattern(chem_handle h, int* row_ptr, int* col_idx);
      4 factor slot sources: S entry (internal order) feeding each factor slot, -1 for fill (nnz_LU);
      5 internal S entry -> CSR position of chem_jacobian_pattern (nnz_S);
      6 transposed substitution program (A^T x = b), same encoding as 1;
-     7 compiled reaction order: description index of each compiled reaction (R).
+     7 compiled reaction order: description index of each compiled reaction (R);
+     8, 9, 10 the programs of 0, 1 and 6 for two warps per cell: 64 lane-ops per step.
    With out == NULL only *count is written.  *count: number of ints. */
 chem_status chem_export_plan(chem_handle h, int which, int* out, int* count);
 

@@ -1,18 +1,24 @@
 """Launch-shape autotuner for chem_integrate.
 
-Knobs searched (one warp always integrates one cell; the kernels are written for that mapping):
-  mode         0 = one grid over all cells, 1 = cells sorted by their previous substep count and pulled
-               by resident warps from an atomic queue (the on-chip form of the paper's dynamic load
-               balancing, Sec. 2.5)
-  block_warps  warps (cells) per block: changes how shared memory is carved up per SM and how many
-               blocks share an SM
-  chunk        cells a warp claims per queue operation (mode 1)
+Knobs searched:
+  warps_per_cell  1 (one warp integrates a cell) or 2 (two warps of a block share it: wider reaction and
+                  species loops and twice the warps in flight, at the price of more, emptier steps in the
+                  sparse factorisation and solves and of named-barrier synchronisation)
+  mode            0 = one grid over all cells, 1 = cells sorted by their previous substep count and
+                  pulled by resident lane groups from an atomic queue (the on-chip form of the paper's
+                  dynamic load balancing, Sec. 2.5)
+  block_cells     cells per block: changes how shared memory is carved up per SM and how many blocks
+                  share an SM
+  chunk           cells a group claims per queue operation (mode 1)
 
-Every candidate integrates the same sample of the caller's cells, starting from the same state, once
-untimed and then timed with CUDA events on the caller's stream; the fastest is kept.  The sample keeps
-the cost distribution of the whole field: cells are ordered by previous substep count and every k-th is
-taken (a seeded random pick when no counts are known yet).  Results are cached per (mechanism digest,
-cell-count bucket, device name, tolerances) in a JSON file next to the compiled library.
+The search is staged (coordinate descent): warps per cell with the library's default block shape and
+the sorted queue; then cells per block and queue chunk for that choice; then the plain grid with the
+best block shape against the best queue.  Every run integrates the same sample of the caller's cells,
+starting from the same state, once untimed and then timed with CUDA events on the caller's stream.  The
+sample keeps the cost distribution of the whole field: cells are ordered by previous substep count and
+every k-th is taken (a seeded random pick when no counts are known yet).  Results are cached per
+(mechanism digest, cell-count bucket, device name, tolerances) in a JSON file next to the compiled
+library.
 """
 from __future__ import annotations
 
@@ -25,6 +31,7 @@ import numpy as np
 from . import build as _build
 
 CACHE = os.path.join(_build.OUT, "autotune_cache.json")
+KEYS = ("warps_per_cell", "mode", "block_cells", "chunk")
 
 
 def mechanism_digest(desc) -> str:
@@ -35,11 +42,27 @@ def mechanism_digest(desc) -> str:
     return h.hexdigest()[:16]
 
 
-def candidates(max_block_warps: int):
-    """The search space: plain grids and sorted queues over a few block shapes and chunks."""
-    shapes = sorted({1, 2, 4, max(1, max_block_warps)})
-    out = [dict(mode=0, block_warps=w, chunk=1) for w in shapes]
-    out += [dict(mode=1, block_warps=w, chunk=c) for w in shapes for c in (1, 2, 4)]
+def max_block_cells(cell_bytes: int, smem_optin: int, warps_per_cell: int) -> int:
+    """Most cells a block can hold by shared memory, 1024 threads, at most 16, and 15 named barriers for
+    two-warp cells (the library also applies the kernels' register limit: chem_info max_block_cells)."""
+    c = max(1, smem_optin // max(cell_bytes, 1))
+    c = min(c, 1024 // (32 * warps_per_cell), 16)
+    if warps_per_cell > 1:
+        c = min(c, 15)
+    return max(1, c)
+
+
+def block_shapes(max_cells: int):
+    return sorted({c for c in (1, 2, 4, max_cells) if c <= max_cells})
+
+
+def candidates(max_cells: dict):
+    """The full launch-shape space; max_cells[w] = largest block (in cells) for w warps per cell."""
+    out = []
+    for wpc in sorted(max_cells):
+        shapes = block_shapes(max_cells[wpc])
+        out += [dict(warps_per_cell=wpc, mode=0, block_cells=c, chunk=1) for c in shapes]
+        out += [dict(warps_per_cell=wpc, mode=1, block_cells=c, chunk=k) for c in shapes for k in (1, 2, 4)]
     return out
 
 
@@ -81,7 +104,8 @@ def _store(key, value):
 
 def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int = 8192, use_cache: bool = True,
          repeats: int = 1, stream=None):
-    """Best launch shape for integrating these cells; returns {mode, block_warps, chunk, ms, table}.
+    """Best launch shape for integrating these cells; returns {warps_per_cell, mode, block_cells, chunk, ms,
+    sample, table}.
 
     T, p, dt: device tensors [N]; Y: [n*N] species-major; nsub_prev: previous substep counts (device or
     host, may be None).  The inputs are not modified."""
@@ -101,17 +125,16 @@ def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int =
     Ys = Y.view(n, N)[:, ii].contiguous().view(-1)
     ns0 = torch.zeros(len(idx), dtype=torch.int32, device=T.device) if ns_host is None else \
         torch.as_tensor(ns_host[idx].astype(np.int32), device=T.device)
-    cell_bytes = mech.info["smem_per_cell"]
-    props = torch.cuda.get_device_properties(mech.device)
-    optin = getattr(props, "shared_memory_per_block_optin", 227 * 1024)
-    wmax = max(1, min(32, optin // max(cell_bytes, 1)))
+    info = mech.info
+    maxc = {w: int(info["max_block_cells"][w - 1]) for w in (1, 2)}
     strm = stream or torch.cuda.current_stream(T.device)
     Tw, Yw = torch.empty_like(Ts), torch.empty_like(Ys)
     hio = torch.empty(len(idx), dtype=torch.float64, device=T.device)
     ns = torch.empty_like(ns0)
     st = torch.empty_like(ns0)
     table = []
-    for c in candidates(wmax):
+
+    def timed(c):
         times = []
         for r in range(1 + repeats):
             with torch.cuda.stream(strm):
@@ -126,10 +149,25 @@ def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int =
             strm.synchronize()
             if r > 0:
                 times.append(e0.elapsed_time(e1))
-        table.append(dict(c, ms=float(min(times))))
-    best = min(table, key=lambda d: d["ms"])
-    out = dict(mode=best["mode"], block_warps=best["block_warps"], chunk=best["chunk"], ms=best["ms"],
-               sample=int(len(idx)), table=table)
+        row = dict(c, ms=float(min(times)))
+        table.append(row)
+        return row
+
+    # 1) warps per cell, library default block shape, sorted queue
+    best = min((timed(dict(warps_per_cell=w, mode=1, block_cells=0, chunk=1)) for w in (1, 2)),
+               key=lambda d: d["ms"])
+    w = best["warps_per_cell"]
+    # 2) block shape and chunk for that choice
+    for c in block_shapes(maxc[w]):
+        for k in (1, 2, 4):
+            row = timed(dict(warps_per_cell=w, mode=1, block_cells=c, chunk=k))
+            if row["ms"] < best["ms"]:
+                best = row
+    # 3) the plain grid with that block shape
+    row = timed(dict(warps_per_cell=w, mode=0, block_cells=best["block_cells"], chunk=1))
+    if row["ms"] < best["ms"]:
+        best = row
+    out = dict({k: best[k] for k in KEYS}, ms=best["ms"], sample=int(len(idx)), table=table)
     if use_cache:
         _store(key, out)
     return out
@@ -137,4 +175,4 @@ def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int =
 
 def launch_options(result) -> dict:
     """The chem_integrate keyword arguments of a `tune` result."""
-    return dict(mode=int(result["mode"]), block_warps=int(result["block_warps"]), chunk=int(result["chunk"]))
+    return {k: int(result[k]) for k in KEYS}

@@ -36,18 +36,18 @@ struct AdjLayout {
 // out = J^T w = S^T w + v (u . w) with S in the internal entry order
 template <class Sc>
 __device__ __forceinline__ void vjp(const MechView& M, const Sc* S, const Sc* u, const Sc* v, const double* w, Sc* out,
-                                    Sc* part, int lane) {
-  run_gather(M.g_col, out + 1, part, [&](int a, int b) { return S[a] * w[1 + b]; }, lane);
+                                    Sc* part, const Grp1& g) {
+  run_gather(M.g_col, out + 1, part, [&](int a, int b) { return S[a] * w[1 + b]; }, g);
   Sc t0 = Sc(0.0), uw = Sc(0.0);
-  for (int k = lane; k < M.n; k += kWarp) t0 = sfma(S[M.nY + k], Sc(w[1 + k]), t0);
-  for (int i = lane; i < M.m; i += kWarp) uw = sfma(u[i], Sc(w[i]), uw);
-  t0 = warp_sum(t0);
-  uw = warp_sum(uw);
-  for (int c = lane; c < M.m; c += kWarp) {
+  for (int k = g.lane; k < M.n; k += g.size) t0 = sfma(S[M.nY + k], Sc(w[1 + k]), t0);
+  for (int i = g.lane; i < M.m; i += g.size) uw = sfma(u[i], Sc(w[i]), uw);
+  t0 = gsum(g, t0);
+  uw = gsum(g, uw);
+  for (int c = g.lane; c < M.m; c += g.size) {
     const Sc base = (c == 0) ? t0 : out[c];
     out[c] = sfma(v[c], uw, sfma(S[M.nY + M.n + c], Sc(w[0]), base));
   }
-  __syncwarp();
+  g.sync();
 }
 
 __device__ __forceinline__ void acc_theta(double& g, double c) { g += c; }
@@ -57,13 +57,13 @@ __device__ __forceinline__ void acc_theta(double& g, const Dual& c) { g += c.d; 
 // for reaction r, q_r * E_r with E_r = sum_products a_k - sum_reactants a_k.
 template <class Sc>
 __device__ __forceinline__ void theta_terms(const MechView& M, const Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
-                                            const double* w, Sc* a, double* GA, double* GE, int lane) {
+                                            const double* w, Sc* a, double* GA, double* GE, const Grp1& g) {
   const Sc c1 = (w[0] * kRu) * sc.T / (sc.rho * sc.cp);
-  for (int k = lane; k < M.n; k += kWarp)
+  for (int k = g.lane; k < M.n; k += g.size)
     a[k] = sfma(Sc(__ldg(M.sp + (size_t)k * SP_STRIDE + 1) * w[1 + k]), sc.irho, -(c1 * s[L.hRT + k]));
-  __syncwarp();
+  g.sync();
   const Sc iRT = 1.0 / (kRu * sc.T);
-  for (int r = lane; r < M.R; r += kWarp) {
+  for (int r = g.lane; r < M.R; r += g.size) {
     const int* I = M.rxi + (size_t)r * RX_I;
     const int nro = __ldg(I + 2), npo = __ldg(I + 3);
     Sc E = Sc(0.0);
@@ -73,40 +73,40 @@ __device__ __forceinline__ void theta_terms(const MechView& M, const Sc* s, cons
     acc_theta(GA[r], qE);
     acc_theta(GE[r], -(qE * iRT));
   }
-  __syncwarp();
+  g.sync();
 }
 
 // x <- A^-T x (transposed substitution with the same factor)
-__device__ __forceinline__ void lu_solveT(const MechView& M, const double* s, const CellLayout& L, double* x, int lane) {
+__device__ __forceinline__ void lu_solveT(const MechView& M, const double* s, const CellLayout& L, double* x, const Grp1& g) {
   const double* LU = s + L.LU;
   const double* dinv = s + L.dinv;
-  const ElimOp* op = M.svT_ops + lane;
-  for (int st = 0; st < M.svT_steps; ++st, op += kWarp) {
+  const ElimOp* op = M.svT_ops + g.lane;
+  for (int st = 0; st < M.svT_steps; ++st, op += g.size) {
     const ElimOp o = ld_eop(op);
     if (o.t != OP_IDLE) {
       if (o.kind == K_UPDATE) x[o.t] = fma(-LU[o.a], x[o.b], x[o.t]);
       else x[o.t] *= dinv[o.a];
     }
-    __syncwarp();
+    g.sync();
   }
 }
 
 // x <- M^-T x with M^T = A^T - v u^T:  x = A^-T x + zt (u . A^-T x) / (1 - u . zt),  zt = A^-T v
 __device__ __forceinline__ void smT_solve(const MechView& M, const double* s, const AdjLayout& A, double* x,
-                                          double idenT, int lane) {
-  lu_solveT(M, s, A.L, x, lane);
+                                          double idenT, const Grp1& g) {
+  lu_solveT(M, s, A.L, x, g);
   const double* u = s + A.UY;
   const double* zt = s + A.ZT;
   double d = 0.0;
-  for (int i = lane; i < M.m; i += kWarp) d = fma(u[i], x[i], d);
-  d = warp_sum(d) * idenT;
-  for (int i = lane; i < M.m; i += kWarp) x[i] = fma(zt[i], d, x[i]);
-  __syncwarp();
+  for (int i = g.lane; i < M.m; i += g.size) d = fma(u[i], x[i], d);
+  d = gsum(g, d) * idenT;
+  for (int i = g.lane; i < M.m; i += g.size) x[i] = fma(zt[i], d, x[i]);
+  g.sync();
 }
 
-__device__ __forceinline__ void vset(double* dst, const double* src, int m, int lane) {
-  for (int i = lane; i < m; i += kWarp) dst[i] = src[i];
-  __syncwarp();
+__device__ __forceinline__ void vset(double* dst, const double* src, int m, const Grp1& g) {
+  for (int i = g.lane; i < m; i += g.size) dst[i] = src[i];
+  g.sync();
 }
 
 // One adjoint step at state y (a row of the segment) with step h.  lambda (A.LAM) is updated in place,
@@ -114,7 +114,7 @@ __device__ __forceinline__ void vset(double* dst, const double* src, int m, int 
 // happen for a step the forward pass accepted).
 __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
                                              const CellLayout& Ld, const double* y, double p, double h,
-                                             double* GA, double* GE, int lane) {
+                                             double* GA, double* GE, const Grp1& g) {
   const CellLayout& L = A.L;
   const int m = M.m;
   const double ih = 1.0 / h;
@@ -123,115 +123,115 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
   double* MU1 = s + A.MU1; double* MU2 = s + A.MU2; double* MU3 = s + A.MU3; double* MU4 = s + A.MU4;
   double* LAM = s + A.LAM; double* G = s + A.G; double* Y3 = s + A.Y3; double* Y4 = s + A.Y4;
   // ---- forward quantities of the step (same arithmetic as the forward attempt)
-  vset(s + L.y, y, m, lane);
-  eval_jac<double>(M, s, L, s + L.y, p, lane);
-  vset(s + A.SY, s + L.S, M.nnz_S, lane);
-  vset(s + A.UY, s + L.u, m, lane);
-  vset(s + A.VY, s + L.v, m, lane);
-  if (!lu_build_factor(M, s, L, ih * (1.0 / RG), lane)) return false;
+  vset(s + L.y, y, m, g);
+  eval_jac<double>(M, s, L, s + L.y, p, g);
+  vset(s + A.SY, s + L.S, M.nnz_S, g);
+  vset(s + A.UY, s + L.u, m, g);
+  vset(s + A.VY, s + L.v, m, g);
+  if (!lu_build_factor(M, s, L, ih * (1.0 / RG), g)) return false;
   double* z = s + L.z;
   const double* u = s + A.UY;
   const double* v = s + A.VY;
   const double* f0 = s + L.f0;
-  for (int i = lane; i < m; i += kWarp) { z[i] = u[i]; U1[i] = f0[i]; }
-  __syncwarp();
-  lu_solve_impl<true>(M, s, L, z, U1, lane);
+  for (int i = g.lane; i < m; i += g.size) { z[i] = u[i]; U1[i] = f0[i]; }
+  g.sync();
+  lu_solve_impl<true>(M, s, L, z, U1, g);
   double vz = 0.0, vx = 0.0;
-  for (int i = lane; i < m; i += kWarp) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
-  vz = warp_sum(vz);
-  vx = warp_sum(vx);
+  for (int i = g.lane; i < m; i += g.size) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
+  vz = gsum(g, vz);
+  vx = gsum(g, vx);
   const double iden = 1.0 / (1.0 - vz);
   vx *= iden;
-  for (int i = lane; i < m; i += kWarp) U1[i] = fma(z[i], vx, U1[i]);
-  __syncwarp();
-  for (int i = lane; i < m; i += kWarp) U2[i] = fma(C21 * ih, U1[i], f0[i]);
-  __syncwarp();
-  sm_solve(M, s, L, U2, iden, lane);
-  for (int i = lane; i < m; i += kWarp) Y3[i] = fma(A31, U1[i], y[i]);
-  __syncwarp();
-  eval_f<double>(M, s, L, Y3, p, U3, lane);
-  for (int i = lane; i < m; i += kWarp) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
-  __syncwarp();
-  sm_solve(M, s, L, U3, iden, lane);
-  for (int i = lane; i < m; i += kWarp) Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
-  __syncwarp();
-  eval_f<double>(M, s, L, Y4, p, U4, lane);
-  for (int i = lane; i < m; i += kWarp) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
-  __syncwarp();
-  sm_solve(M, s, L, U4, iden, lane);
+  for (int i = g.lane; i < m; i += g.size) U1[i] = fma(z[i], vx, U1[i]);
+  g.sync();
+  for (int i = g.lane; i < m; i += g.size) U2[i] = fma(C21 * ih, U1[i], f0[i]);
+  g.sync();
+  sm_solve(M, s, L, U2, iden, g);
+  for (int i = g.lane; i < m; i += g.size) Y3[i] = fma(A31, U1[i], y[i]);
+  g.sync();
+  eval_f<double>(M, s, L, Y3, p, U3, g);
+  for (int i = g.lane; i < m; i += g.size) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
+  g.sync();
+  sm_solve(M, s, L, U3, iden, g);
+  for (int i = g.lane; i < m; i += g.size) Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
+  g.sync();
+  eval_f<double>(M, s, L, Y4, p, U4, g);
+  for (int i = g.lane; i < m; i += g.size) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
+  g.sync();
+  sm_solve(M, s, L, U4, iden, g);
   // transposed Sherman-Morrison vector
   double* zt = s + A.ZT;
-  vset(zt, v, m, lane);
-  lu_solveT(M, s, L, zt, lane);
+  vset(zt, v, m, g);
+  lu_solveT(M, s, L, zt, g);
   double uz = 0.0;
-  for (int i = lane; i < m; i += kWarp) uz = fma(u[i], zt[i], uz);
-  uz = warp_sum(uz);
+  for (int i = g.lane; i < m; i += g.size) uz = fma(u[i], zt[i], uz);
+  uz = gsum(g, uz);
   const double idenT = 1.0 / (1.0 - uz);
   // ---- reverse sweep over the stages
-  for (int i = lane; i < m; i += kWarp) {
+  for (int i = g.lane; i < m; i += g.size) {
     MU1[i] = M1 * LAM[i]; MU2[i] = 0.0; MU3[i] = M3 * LAM[i]; MU4[i] = M4 * LAM[i];
   }
-  __syncwarp();
+  g.sync();
   // stage 4: r4 = f(Y4) + (c41 U1 + c42 U2 + c43 U3)/h, Y4 = y + a41 U1 + a43 U3
-  vset(W4, MU4, m, lane);
-  smT_solve(M, s, A, W4, idenT, lane);
+  vset(W4, MU4, m, g);
+  smT_solve(M, s, A, W4, idenT, g);
   {
-    ScalT<double> sc = eval_jac<double>(M, s, L, Y4, p, lane);
-    theta_terms<double>(M, s, L, sc, W4, s + A.A, GA, GE, lane);
-    vjp<double>(M, s + L.S, s + L.u, s + L.v, W4, G, s + L.part, lane);
+    ScalT<double> sc = eval_jac<double>(M, s, L, Y4, p, g);
+    theta_terms<double>(M, s, L, sc, W4, s + A.A, GA, GE, g);
+    vjp<double>(M, s + L.S, s + L.u, s + L.v, W4, G, s + L.part, g);
   }
-  for (int i = lane; i < m; i += kWarp) {
+  for (int i = g.lane; i < m; i += g.size) {
     MU1[i] = fma(C41 * ih, W4[i], fma(A41, G[i], MU1[i]));
     MU2[i] = fma(C42 * ih, W4[i], MU2[i]);
     MU3[i] = fma(C43 * ih, W4[i], fma(A43, G[i], MU3[i]));
     LAM[i] += G[i];
   }
-  __syncwarp();
+  g.sync();
   // stage 3: r3 = f(Y3) + (c31 U1 + c32 U2)/h, Y3 = y + a31 U1
-  vset(W3, MU3, m, lane);
-  smT_solve(M, s, A, W3, idenT, lane);
+  vset(W3, MU3, m, g);
+  smT_solve(M, s, A, W3, idenT, g);
   {
-    ScalT<double> sc = eval_jac<double>(M, s, L, Y3, p, lane);
-    theta_terms<double>(M, s, L, sc, W3, s + A.A, GA, GE, lane);
-    vjp<double>(M, s + L.S, s + L.u, s + L.v, W3, G, s + L.part, lane);
+    ScalT<double> sc = eval_jac<double>(M, s, L, Y3, p, g);
+    theta_terms<double>(M, s, L, sc, W3, s + A.A, GA, GE, g);
+    vjp<double>(M, s + L.S, s + L.u, s + L.v, W3, G, s + L.part, g);
   }
-  for (int i = lane; i < m; i += kWarp) {
+  for (int i = g.lane; i < m; i += g.size) {
     MU1[i] = fma(C31 * ih, W3[i], fma(A31, G[i], MU1[i]));
     MU2[i] = fma(C32 * ih, W3[i], MU2[i]);
     LAM[i] += G[i];
   }
-  __syncwarp();
+  g.sync();
   // stage 2: r2 = f(y) + (c21/h) U1;  stage 1: r1 = f(y)
-  vset(W2, MU2, m, lane);
-  smT_solve(M, s, A, W2, idenT, lane);
-  for (int i = lane; i < m; i += kWarp) MU1[i] = fma(C21 * ih, W2[i], MU1[i]);
-  __syncwarp();
-  vset(W1, MU1, m, lane);
-  smT_solve(M, s, A, W1, idenT, lane);
+  vset(W2, MU2, m, g);
+  smT_solve(M, s, A, W2, idenT, g);
+  for (int i = g.lane; i < m; i += g.size) MU1[i] = fma(C21 * ih, W2[i], MU1[i]);
+  g.sync();
+  vset(W1, MU1, m, g);
+  smT_solve(M, s, A, W1, idenT, g);
   double* WS = s + A.WS;
-  for (int i = lane; i < m; i += kWarp) WS[i] = W1[i] + W2[i];
-  __syncwarp();
-  vjp<double>(M, s + A.SY, s + A.UY, s + A.VY, WS, G, s + L.part, lane);
-  for (int i = lane; i < m; i += kWarp) LAM[i] += G[i];
-  __syncwarp();
+  for (int i = g.lane; i < m; i += g.size) WS[i] = W1[i] + W2[i];
+  g.sync();
+  vjp<double>(M, s + A.SY, s + A.UY, s + A.VY, WS, G, s + L.part, g);
+  for (int i = g.lane; i < m; i += g.size) LAM[i] += G[i];
+  g.sync();
   {
-    vset(s + L.y, y, m, lane);
-    ScalT<double> sc = eval_f<double>(M, s, L, s + L.y, p, s + L.f0, lane);
-    theta_terms<double>(M, s, L, sc, WS, s + A.A, GA, GE, lane);
+    vset(s + L.y, y, m, g);
+    ScalT<double> sc = eval_f<double>(M, s, L, s + L.y, p, s + L.f0, g);
+    theta_terms<double>(M, s, L, sc, WS, s + A.A, GA, GE, g);
   }
   // ---- Hessian and mixed parameter terms: derivative of J(y) along U_i, contracted with w_i
   const double* Us[4] = {U1, U2, U3, U4};
   const double* Ws[4] = {W1, W2, W3, W4};
   for (int st = 0; st < 4; ++st) {
     Dual* yd = dw + Ld.y;
-    for (int i = lane; i < m; i += kWarp) yd[i] = Dual(y[i], Us[st][i]);
-    __syncwarp();
-    ScalT<Dual> scd = eval_jac<Dual>(M, dw, Ld, yd, p, lane);
+    for (int i = g.lane; i < m; i += g.size) yd[i] = Dual(y[i], Us[st][i]);
+    g.sync();
+    ScalT<Dual> scd = eval_jac<Dual>(M, dw, Ld, yd, p, g);
     Dual* Gd = dw + Ld.x;
-    vjp<Dual>(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws[st], Gd, dw + Ld.part, lane);
-    for (int i = lane; i < m; i += kWarp) LAM[i] += Gd[i].d;
-    __syncwarp();
-    theta_terms<Dual>(M, dw, Ld, scd, Ws[st], dw + Ld.z, GA, GE, lane);
+    vjp<Dual>(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws[st], Gd, dw + Ld.part, g);
+    for (int i = g.lane; i < m; i += g.size) LAM[i] += Gd[i].d;
+    g.sync();
+    theta_terms<Dual>(M, dw, Ld, scd, Ws[st], dw + Ld.z, GA, GE, g);
   }
   return true;
 }
@@ -239,26 +239,26 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
 // Reverse pass of one cell from its tape.  Returns false on a singular factor.
 __device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
                                              const CellLayout& Ld, double p, int n_acc, const double* rec_h,
-                                             const double* rec_ck, int K, int N, int cell, int lane,
+                                             const double* rec_ck, int K, int N, int cell, const Grp1& g,
                                              const IntOpts& o, double* seg, double* GA, double* GE) {
   const int m = M.m;
   const CellLayout& L = A.L;
   const int nseg = (n_acc + K - 1) / K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int n0 = sg * K, n1 = min(n_acc, n0 + K);
-    for (int i = lane; i < m; i += kWarp) seg[i] = rec_ck[((size_t)sg * m + i) * N + cell];
-    __syncwarp();
+    for (int i = g.lane; i < m; i += g.size) seg[i] = rec_ck[((size_t)sg * m + i) * N + cell];
+    g.sync();
     // recompute the segment's states with the forward arithmetic
     for (int nn = n0; nn < n1 - 1; ++nn) {
-      vset(s + L.y, seg + (size_t)(nn - n0) * m, m, lane);
-      eval_jac<double>(M, s, L, s + L.y, p, lane);
-      const StepOut so = ros_attempt(M, s, L, p, rec_h[(size_t)nn * N + cell], o.rtol, o.atol, lane);
+      vset(s + L.y, seg + (size_t)(nn - n0) * m, m, g);
+      eval_jac<double>(M, s, L, s + L.y, p, g);
+      const StepOut so = ros_attempt(M, s, L, p, rec_h[(size_t)nn * N + cell], o.rtol, o.atol, g);
       if (!so.good) return false;
-      vset(seg + (size_t)(nn - n0 + 1) * m, s + L.ytmp, m, lane);
+      vset(seg + (size_t)(nn - n0 + 1) * m, s + L.ytmp, m, g);
     }
     for (int nn = n1 - 1; nn >= n0; --nn)
       if (!adjoint_step(M, s, A, dw, Ld, seg + (size_t)(nn - n0) * m, p, rec_h[(size_t)nn * N + cell], GA, GE,
-                        lane))
+                        g))
         return false;
   }
   return true;

@@ -35,7 +35,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct chem_handle_s {
   int device = 0;
   HostMech hm;
-  MechView view{};
+  MechView view[kMaxWarpsPerCell]{};   // view[w - 1]: the tables with the programs for w warps per cell
   void* blob = nullptr;
   CellLayout L{};
   int cell_bytes = 0;
@@ -49,10 +49,15 @@ struct chem_handle_s {
   size_t scratch_bytes = 0;
   void* adj_scratch = nullptr;     // adjoint tape, gradients, dual workspaces (grows on demand)
   size_t adj_scratch_bytes = 0;
-  int default_wpb = 1;             // warps per block that fit the most cells per SM (set with the attributes)
+  // per warps-per-cell choice (set with the attributes): the largest block that launches (in cells), the
+  // block size that fits the most cells per SM, and that number of cells
+  int max_cells[kMaxWarpsPerCell] = {1, 1};
+  int default_cells[kMaxWarpsPerCell] = {1, 1};
+  int resident_cells[kMaxWarpsPerCell] = {0, 0};
+  int auto_wpc = 1;                // warps per cell when the caller leaves the choice to the library
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
-    int N, mode, wpb, chunk;
+    int N, mode, cpb, chunk, wpc;
     const void* ptr[10];
     double d[5];
     int i[3];
@@ -90,8 +95,10 @@ CellLayout make_layout(const HostMech& hm, bool separate_lu = false) {
     o += reuse;
   }
   int np = 1;
-  for (const HostGather* g : {&hm.g_omega, &hm.g_row, &hm.g_col}) np = std::max(np, g->n_partial);
-  for (const HostGather& g : hm.g_jac) np = std::max(np, g.n_partial);
+  for (const HostProg& P : hm.prog) {
+    for (const HostGather* g : {&P.g_omega, &P.g_row, &P.g_col}) np = std::max(np, g->n_partial);
+    for (const HostGather& g : P.g_jac) np = std::max(np, g.n_partial);
+  }
   L.part = take(np);
   L.misc = take(16);
   L.total = o;
@@ -130,13 +137,33 @@ __device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long 
                                                  unsigned long long budget_ns);
 
 // Load one cell's state into y (lanes over state components).
-__device__ __forceinline__ void load_state(double* y, int m, int N, int c, const double* T, const double* Y, int lane) {
-  for (int i = lane; i < m; i += kWarp) y[i] = (i == 0) ? T[c] : Y[(size_t)(i - 1) * N + c];
-  __syncwarp();
+template <class Gp>
+__device__ __forceinline__ void load_state(double* y, int m, int N, int c, const double* T, const double* Y,
+                                           const Gp& g) {
+  for (int i = g.lane; i < m; i += g.size) y[i] = (i == 0) ? T[c] : Y[(size_t)(i - 1) * N + c];
+  g.sync();
+}
+
+// The lane group of this thread when each cell of a block takes W warps; s = the cell's memory.
+__device__ __forceinline__ void cell_slot(int gs, const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
+  cell_in_block = threadIdx.x / gs;
+  s = smem + (size_t)cell_in_block * L.total;
+}
+template <int W>
+__device__ __forceinline__ GrpW<W> cell_group(const CellLayout& L, double* smem, int& cell_in_block, double*& s);
+template <>
+__device__ __forceinline__ Grp1 cell_group<1>(const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
+  cell_slot(Grp1::size, L, smem, cell_in_block, s);
+  return Grp1{(int)threadIdx.x - cell_in_block * Grp1::size};
+}
+template <>
+__device__ __forceinline__ Grp2 cell_group<2>(const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
+  cell_slot(Grp2::size, L, smem, cell_in_block, s);
+  return Grp2{(int)threadIdx.x - cell_in_block * Grp2::size, 1 + cell_in_block, s + L.misc};
 }
 
 // Block-cooperative coalesced load of the block's consecutive cells: adjacent threads read adjacent
-// cells of the same state row (structure of arrays), then each warp owns its cell's copy.
+// cells of the same state row (structure of arrays), then each lane group owns its cell's copy.
 __device__ __forceinline__ void load_tile(double* smem, const CellLayout& L, int m, int N, int c0, int wpb,
                                           const double* T, const double* Y) {
   const int total = wpb * m;
@@ -158,8 +185,9 @@ __global__ void k_rates(MechView M, CellLayout L, int N, const double* __restric
   load_tile(smem, L, M.m, N, c0, wpb, T, Y);
   const int c = c0 + w;
   if (c >= N) return;
+  const Grp1 g{lane};
   double* f = s + L.f0;
-  Scal sc = eval_f<double>(M, s, L, s + L.y, p[c], f, lane);
+  Scal sc = eval_f<double>(M, s, L, s + L.y, p[c], f, g);
   for (int i = lane; i < M.m; i += kWarp) {
     if (i == 0) dTdt[c] = f[0];
     else dYdt[(size_t)(i - 1) * N + c] = f[i];
@@ -179,7 +207,7 @@ __global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __rest
   load_tile(smem, L, M.m, N, c0, wpb, T, Y);
   const int c = c0 + w;
   if (c >= N) return;
-  eval_jac<double>(M, s, L, s + L.y, p[c], lane);
+  eval_jac<double>(M, s, L, s + L.y, p[c], Grp1{lane});
   for (int e = lane; e < M.nnz_S; e += kWarp) Sv[(size_t)__ldg(M.s_out + e) * N + c] = s[L.S + e];
   for (int i = lane; i < M.m; i += kWarp) {
     u[(size_t)i * N + c] = s[L.u + i];
@@ -187,27 +215,30 @@ __global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __rest
   }
 }
 
-// Plain form: one warp per cell, cells in index order, one launch.
+// Plain form: one lane group (W warps) per cell, cells in index order, one launch.
+template <int W>
 __global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __restrict__ T, const double* __restrict__ p,
                                   double* __restrict__ Y, const double* __restrict__ dt, double* __restrict__ h_io,
                                   int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
                                   IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
   extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int c0 = blockIdx.x * wpb;
-  double* s = smem + (size_t)w * L.total;
-  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
+  const int cpb = blockDim.x / (W * kWarp);
+  int w = 0;
+  double* s = nullptr;
+  const GrpW<W> g = cell_group<W>(L, smem, w, s);
+  const int c0 = blockIdx.x * cpb;
+  load_tile(smem, L, M.m, N, c0, cpb, T, Y);
   const int c = c0 + w;
   if (c >= N) return;
   double h = h_io[c];
   int ns = 0, na = 0, st = 0;
-  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, with_deadline(o, stamp, budget_ns), lane, c);
+  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, with_deadline(o, stamp, budget_ns), g, c);
   const double* y = s + L.y;
-  for (int i = lane; i < M.m; i += kWarp) {
+  for (int i = g.lane; i < M.m; i += g.size) {
     if (i == 0) T[c] = y[0];
     else Y[(size_t)(i - 1) * N + c] = y[i];
   }
-  if (lane == 0) {
+  if (g.lane == 0) {
     h_io[c] = h;
     nsub[c] = ns;
     status[c] = st;
@@ -270,6 +301,7 @@ __device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long 
 // Persistent form: grid sized to the resident capacity; every warp pulls `chunk` cells at a time from
 // the sorted queue with one atomicAdd and integrates them one after the other.  No block-wide barrier:
 // warps of a block finish independently.
+template <int W>
 __global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* __restrict__ T,
                                        const double* __restrict__ p, double* __restrict__ Y,
                                        const double* __restrict__ dt, double* __restrict__ h_io,
@@ -277,33 +309,32 @@ __global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* 
                                        const int* __restrict__ perm, int* __restrict__ head, int chunk, IntOpts o,
                                        const unsigned long long* stamp, unsigned long long budget_ns) {
   extern __shared__ double smem[];
-  const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  double* s = smem + (size_t)w * L.total;
+  int w = 0;
+  double* s = nullptr;
+  const GrpW<W> g = cell_group<W>(L, smem, w, s);
   const IntOpts oo = with_deadline(o, stamp, budget_ns);
   while (true) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(head, chunk);
-    base = __shfl_sync(0xffffffffu, base, 0);
+    const int base = (int)gbcast(g, g.lane == 0 ? atomicAdd(head, chunk) : 0);
     if (base >= N) break;
     const int end = min(base + chunk, N);
     for (int j = base; j < end; ++j) {
       const int c = perm[j];
-      load_state(s + L.y, M.m, N, c, T, Y, lane);
+      load_state(s + L.y, M.m, N, c, T, Y, g);
       double h = h_io[c];
       int ns = 0, na = 0, st = 0;
-      integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, oo, lane, c);
+      integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, oo, g, c);
       const double* y = s + L.y;
-      for (int i = lane; i < M.m; i += kWarp) {
+      for (int i = g.lane; i < M.m; i += g.size) {
         if (i == 0) T[c] = y[0];
         else Y[(size_t)(i - 1) * N + c] = y[i];
       }
-      if (lane == 0) {
+      if (g.lane == 0) {
         h_io[c] = h;
         nsub[c] = ns;
         status[c] = st;
         if (nacc_out) nacc_out[c] = na;
       }
-      __syncwarp();
+      g.sync();
     }
   }
 }
@@ -337,7 +368,7 @@ __global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const d
     for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
     __syncwarp();
     bool ok = na >= 0;
-    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, lane, o, seg, GA, GE);
+    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, Grp1{lane}, o, seg, GA, GE);
     if (!ok) {
       for (int i = lane; i < m; i += kWarp) LAM[i] = 0.0;
       for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
@@ -401,35 +432,64 @@ chem_status check_handle(chem_handle h) {
   return CHEM_OK;
 }
 
+int max_cells_per_block(const chem_handle h, int wpc) { return h->max_cells[wpc - 1]; }
+
 chem_status set_attrs(chem_handle h) {
   if (h->attr_set) return CHEM_OK;
   const int bytes = h->smem_optin;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+      (e = cudaFuncSetAttribute(k_integrate_plain<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_integrate_plain<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_integrate_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_integrate_persistent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute");
-  // default block shape: the most resident cells per SM (each block also reserves some shared memory,
-  // so a few cells per block can fit one more cell per SM than single-cell blocks); ties -> fewer warps
-  int best_w = 1, best_cells = 0;
-  for (int w = 1; w <= 16 && w * h->cell_bytes <= h->smem_optin; ++w) {
-    int blocks = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_integrate_persistent, w * kWarp,
-                                                           (size_t)w * h->cell_bytes)) != cudaSuccess)
-      return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (blocks * w > best_cells) { best_cells = blocks * w; best_w = w; }
+  // largest block per warps-per-cell choice: shared memory, the threads the kernels' registers allow
+  // (both forms), at most 16 cells, and for two-warp cells the 15 named barriers besides barrier 0
+  for (int wpc = 1; wpc <= kMaxWarpsPerCell; ++wpc) {
+    cudaFuncAttributes fa1, fa2;
+    if ((e = cudaFuncGetAttributes(&fa1, wpc == 1 ? k_integrate_plain<1> : k_integrate_plain<2>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa2, wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>)) !=
+            cudaSuccess)
+      return cuda_fail(e, "cudaFuncGetAttributes");
+    int c = std::max(1, h->smem_optin / std::max(h->cell_bytes, 1));
+    c = std::min(c, std::min(fa1.maxThreadsPerBlock, fa2.maxThreadsPerBlock) / (wpc * kWarp));
+    if (wpc > 1) c = std::min(c, 15);
+    h->max_cells[wpc - 1] = std::max(1, std::min(c, 16));
   }
-  h->default_wpb = best_w;
+  // default block shape per warps-per-cell choice: the most resident cells per SM (each block also
+  // reserves some shared memory, so a few cells per block can fit one more cell per SM than single-cell
+  // blocks); ties -> fewer cells per block
+  for (int wpc = 1; wpc <= kMaxWarpsPerCell; ++wpc) {
+    int best_c = 1, best_cells = 0;
+    for (int c = 1; c <= max_cells_per_block(h, wpc); ++c) {
+      int blocks = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &blocks, wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>, c * wpc * kWarp,
+               (size_t)c * h->cell_bytes)) != cudaSuccess)
+        return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      if (blocks * c > best_cells) { best_cells = blocks * c; best_c = c; }
+    }
+    h->default_cells[wpc - 1] = best_c;
+    h->resident_cells[wpc - 1] = best_cells;
+  }
+  // automatic choice: two warps per cell when one-warp cells leave fewer than 6 warps per SM (a cell
+  // larger than ~35 KB of shared memory) and two-warp cells fit as many cells
+  h->auto_wpc = (h->resident_cells[0] < 6 && h->resident_cells[1] >= h->resident_cells[0]) ? 2 : 1;
   h->attr_set = true;
   return CHEM_OK;
 }
 
-int warps_per_block(const chem_handle h, int requested) {
-  int wpb = requested > 0 ? requested : 1;
-  while (wpb > 1 && wpb * h->cell_bytes > h->smem_optin) --wpb;
-  return wpb;
+// Cells per block: the request (0: the default of the warps-per-cell choice) bounded by the largest block
+// that launches.
+int cells_per_block(const chem_handle h, int requested, int wpc) {
+  int c = requested > 0 ? requested : h->default_cells[wpc - 1];
+  return std::max(1, std::min(c, max_cells_per_block(h, wpc)));
 }
 
 chem_status ensure_scratch(chem_handle h, int N) {
@@ -506,16 +566,20 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
          o_eam = put(buf, hm.eff_am1), o_dsp = put(buf, hm.dslot_sp), o_dmask = put(buf, hm.dslot_mask),
          o_dam = put(buf, hm.dslot_am1), o_er = put(buf, hm.entry_row), o_ec = put(buf, hm.entry_col),
          o_ew = put(buf, hm.entry_wratio), o_lsrc = put(buf, hm.lu_src), o_ldiag = put(buf, hm.lu_diag),
-         o_lops = put(buf, hm.lu_ops), o_lkind = put(buf, hm.lu_kind), o_sops = put(buf, hm.sv_ops),
-         o_skind = put(buf, hm.sv_kind), o_sout = put(buf, hm.s_out), o_tops = put(buf, hm.svT_ops),
-         o_tkind = put(buf, hm.svT_kind), o_rxo = put(buf, hm.rx_order), o_rxd0 = put(buf, hm.rxd);
-  const int n_jp = (int)hm.g_jac.size();
+         o_sout = put(buf, hm.s_out), o_rxo = put(buf, hm.rx_order), o_rxd0 = put(buf, hm.rxd);
+  const int n_jp = (int)hm.jpass.size() / 4;
   if (n_jp > kMaxJPass) { delete h; return fail(CHEM_EUNSUPPORTED, "too many Jacobian passes"); }
   constexpr int kMaxG = 3 + kMaxJPass;
-  size_t o_g[kMaxG][2];
-  const HostGather* gs[kMaxG] = {&hm.g_omega, &hm.g_row, &hm.g_col};
-  for (int i = 0; i < n_jp; ++i) gs[3 + i] = &hm.g_jac[i];
-  for (int i = 0; i < 3 + n_jp; ++i) { o_g[i][0] = put(buf, gs[i]->ops); o_g[i][1] = put(buf, gs[i]->comb); }
+  size_t o_g[kMaxWarpsPerCell][kMaxG][2], o_lops[kMaxWarpsPerCell], o_sops[kMaxWarpsPerCell],
+      o_tops[kMaxWarpsPerCell];
+  const HostGather* gs[kMaxWarpsPerCell][kMaxG];
+  for (int w = 0; w < kMaxWarpsPerCell; ++w) {
+    const HostProg& P = hm.prog[w];
+    gs[w][0] = &P.g_omega; gs[w][1] = &P.g_row; gs[w][2] = &P.g_col;
+    for (int i = 0; i < n_jp; ++i) gs[w][3 + i] = &P.g_jac[i];
+    for (int i = 0; i < 3 + n_jp; ++i) { o_g[w][i][0] = put(buf, gs[w][i]->ops); o_g[w][i][1] = put(buf, gs[w][i]->comb); }
+    o_lops[w] = put(buf, P.lu_ops); o_sops[w] = put(buf, P.sv_ops); o_tops[w] = put(buf, P.svT_ops);
+  }
   if ((e = cudaMalloc(&h->blob, buf.size())) != cudaSuccess) { delete h; return fail(CHEM_ENOMEM, "cudaMalloc of mechanism tables failed"); }
   if ((e = cudaMemcpy(h->blob, buf.data(), buf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(h->blob);
@@ -523,32 +587,37 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
     return cuda_fail(e, "cudaMemcpy of mechanism tables");
   }
   char* b = (char*)h->blob;
-  MechView& V = h->view;
-  V.n = hm.n; V.R = hm.R; V.m = hm.m; V.n_troe = hm.n_troe; V.n_tb = hm.n_tb; V.nY = hm.nY; V.nnz_S = hm.nnz_S;
-  V.nnz_LU = hm.nnz_LU; V.n_dslot = hm.n_dslot;
-  V.sp = (const double*)(b + o_sp); V.rxd = (const double*)(b + o_rxd); V.rxi = (const int*)(b + o_rxi);
-  V.eff_sp = (const int*)(b + o_esp); V.eff_am1 = (const double*)(b + o_eam);
-  V.dslot_sp = (const int*)(b + o_dsp); V.dslot_mask = (const int*)(b + o_dmask); V.dslot_am1 = (const double*)(b + o_dam);
-  V.entry_row = (const int*)(b + o_er); V.entry_col = (const int*)(b + o_ec); V.entry_wratio = (const double*)(b + o_ew);
-  V.lu_src = (const int*)(b + o_lsrc); V.lu_diag = (const int*)(b + o_ldiag);
-  V.lu_ops = (const ElimOp*)(b + o_lops); V.lu_kind = (const uint8_t*)(b + o_lkind); V.lu_steps = (int)hm.lu_kind.size();
-  V.sv_ops = (const ElimOp*)(b + o_sops); V.sv_kind = (const uint8_t*)(b + o_skind); V.sv_steps = (int)hm.sv_kind.size();
-  V.s_out = (const int*)(b + o_sout);
-  V.svT_ops = (const ElimOp*)(b + o_tops); V.svT_kind = (const uint8_t*)(b + o_tkind);
-  V.svT_steps = (int)hm.svT_kind.size();
-  V.rx_order = (const int*)(b + o_rxo);
   h->rxd0 = (const double*)(b + o_rxd0);
-  V.n_jpass = n_jp;
-  for (int i = 0; i < n_jp; ++i)
-    for (int j = 0; j < 4; ++j) V.jpass[i][j] = hm.jpass[(size_t)i * 4 + j];
-  Gather* vg[kMaxG] = {&V.g_omega, &V.g_row, &V.g_col};
-  for (int i = 0; i < n_jp; ++i) vg[3 + i] = &V.g_jac[i];
-  for (int i = 0; i < 3 + n_jp; ++i) {
-    vg[i]->ops = (const GatherOp*)(b + o_g[i][0]);
-    vg[i]->steps = gs[i]->steps;
-    vg[i]->n_partial = gs[i]->n_partial;
-    vg[i]->comb = (const int*)(b + o_g[i][1]);
-    vg[i]->n_comb = (int)gs[i]->comb.size() / 3;
+  for (int w = 0; w < kMaxWarpsPerCell; ++w) {
+    const HostProg& P = hm.prog[w];
+    MechView& V = h->view[w];
+    V.width = P.width;
+    V.n = hm.n; V.R = hm.R; V.m = hm.m; V.n_troe = hm.n_troe; V.n_tb = hm.n_tb; V.nY = hm.nY; V.nnz_S = hm.nnz_S;
+    V.nnz_LU = hm.nnz_LU; V.n_dslot = hm.n_dslot;
+    V.sp = (const double*)(b + o_sp); V.rxd = (const double*)(b + o_rxd); V.rxi = (const int*)(b + o_rxi);
+    V.eff_sp = (const int*)(b + o_esp); V.eff_am1 = (const double*)(b + o_eam);
+    V.dslot_sp = (const int*)(b + o_dsp); V.dslot_mask = (const int*)(b + o_dmask);
+    V.dslot_am1 = (const double*)(b + o_dam);
+    V.entry_row = (const int*)(b + o_er); V.entry_col = (const int*)(b + o_ec);
+    V.entry_wratio = (const double*)(b + o_ew);
+    V.lu_src = (const int*)(b + o_lsrc); V.lu_diag = (const int*)(b + o_ldiag);
+    V.lu_ops = (const ElimOp*)(b + o_lops[w]); V.lu_steps = (int)P.lu_kind.size();
+    V.sv_ops = (const ElimOp*)(b + o_sops[w]); V.sv_steps = (int)P.sv_kind.size();
+    V.svT_ops = (const ElimOp*)(b + o_tops[w]); V.svT_steps = (int)P.svT_kind.size();
+    V.s_out = (const int*)(b + o_sout);
+    V.rx_order = (const int*)(b + o_rxo);
+    V.n_jpass = n_jp;
+    for (int i = 0; i < n_jp; ++i)
+      for (int j = 0; j < 4; ++j) V.jpass[i][j] = hm.jpass[(size_t)i * 4 + j];
+    Gather* vg[kMaxG] = {&V.g_omega, &V.g_row, &V.g_col};
+    for (int i = 0; i < n_jp; ++i) vg[3 + i] = &V.g_jac[i];
+    for (int i = 0; i < 3 + n_jp; ++i) {
+      vg[i]->ops = (const GatherOp*)(b + o_g[w][i][0]);
+      vg[i]->steps = gs[w][i]->steps;
+      vg[i]->n_partial = gs[w][i]->n_partial;
+      vg[i]->comb = (const int*)(b + o_g[w][i][1]);
+      vg[i]->n_comb = (int)gs[w][i]->comb.size() / 3;
+    }
   }
   *out = h;
   return CHEM_OK;
@@ -574,12 +643,24 @@ chem_status chem_info(chem_handle h, chem_info_t* info) {
   info->n_state = h->hm.m;
   info->nnz_S = h->hm.nnz_S;
   info->nnz_LU = h->hm.nnz_LU;
-  info->lu_steps = (int)h->hm.lu_kind.size();
-  info->solve_steps = (int)h->hm.sv_kind.size();
+  info->lu_steps = (int)h->hm.prog[0].lu_kind.size();
+  info->solve_steps = (int)h->hm.prog[0].sv_kind.size();
   info->smem_per_cell = h->cell_bytes;
   info->n_dslots = h->hm.n_dslot;
-  info->jac_passes = (int)h->hm.g_jac.size();
+  info->jac_passes = (int)h->hm.jpass.size() / 4;
   info->smem_adjoint_per_cell = make_adj_layout(h->hm, 16).total * (int)sizeof(double);
+  for (int w = 0; w < kMaxWarpsPerCell; ++w) { info->max_block_cells[w] = 0; info->resident_cells[w] = 0; }
+  info->auto_warps_per_cell = 0;
+  if (h->device >= 0) {
+    chem_status st = check_handle(h);
+    if (st == CHEM_OK) st = set_attrs(h);
+    if (st != CHEM_OK) return st;
+    for (int w = 0; w < kMaxWarpsPerCell; ++w) {
+      info->max_block_cells[w] = h->max_cells[w];
+      info->resident_cells[w] = h->resident_cells[w];
+    }
+    info->auto_warps_per_cell = h->auto_wpc;
+  }
   return CHEM_OK;
 }
 
@@ -594,22 +675,27 @@ chem_status chem_export_plan(chem_handle h, int which, int* out, int* count) {
   if (!h || !count) return fail(CHEM_EINVAL, "null argument");
   const HostMech& hm = h->hm;
   std::vector<int> v;
-  auto prog = [&](const std::vector<ElimOp>& ops, const std::vector<uint8_t>& kinds) {
+  auto prog = [&](const std::vector<ElimOp>& ops, const std::vector<uint8_t>& kinds, int width) {
     for (size_t st = 0; st < kinds.size(); ++st)
-      for (int l = 0; l < kWarp; ++l) {
-        const ElimOp& o = ops[st * kWarp + l];
+      for (int l = 0; l < width; ++l) {
+        const ElimOp& o = ops[st * width + l];
         v.push_back(kinds[st]); v.push_back(o.t); v.push_back(o.a); v.push_back(o.b);
       }
   };
+  const HostProg& P1 = hm.prog[0];
+  const HostProg& P2 = hm.prog[1];
   switch (which) {
-    case 0: prog(hm.lu_ops, hm.lu_kind); break;
-    case 1: prog(hm.sv_ops, hm.sv_kind); break;
+    case 0: prog(P1.lu_ops, P1.lu_kind, P1.width); break;
+    case 1: prog(P1.sv_ops, P1.sv_kind, P1.width); break;
     case 2: v = hm.perm; break;
     case 3: v = hm.lu_rowptr; v.insert(v.end(), hm.lu_col.begin(), hm.lu_col.end()); break;
     case 4: v = hm.lu_src; break;
     case 5: v = hm.s_out; break;
-    case 6: prog(hm.svT_ops, hm.svT_kind); break;
+    case 6: prog(P1.svT_ops, P1.svT_kind, P1.width); break;
     case 7: v = hm.rx_order; break;
+    case 8: prog(P2.lu_ops, P2.lu_kind, P2.width); break;
+    case 9: prog(P2.sv_ops, P2.sv_kind, P2.width); break;
+    case 10: prog(P2.svT_ops, P2.svT_kind, P2.width); break;
     default: return fail(CHEM_EINVAL, "unknown plan part");
   }
   if (out) std::copy(v.begin(), v.end(), out);
@@ -625,8 +711,8 @@ chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, c
   if (N == 0) return CHEM_OK;
   if (!T || !p || !Y || !dTdt || !dYdt) return fail(CHEM_EINVAL, "null array argument");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
-  const int wpb = warps_per_block(h, 4);
-  k_rates<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view, h->L, N, T, p, Y,
+  const int wpb = cells_per_block(h, 4, 1);
+  k_rates<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view[0], h->L, N, T, p, Y,
                                                                                            dTdt, dYdt, wdot);
   return launch_check("chem_rates launch");
 }
@@ -639,8 +725,8 @@ chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p
   if (N == 0) return CHEM_OK;
   if (!T || !p || !Y || !S_vals || !u || !v) return fail(CHEM_EINVAL, "null array argument");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
-  const int wpb = warps_per_block(h, 4);
-  k_jacobian<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view, h->L, N, T, p,
+  const int wpb = cells_per_block(h, 4, 1);
+  k_jacobian<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view[0], h->L, N, T, p,
                                                                                               Y, S_vals, u, v);
   return launch_check("chem_jacobian launch");
 }
@@ -670,30 +756,34 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
     return fail(CHEM_EINVAL, "non-finite option");
   if (o.mode != 0 && o.mode != 1) return fail(CHEM_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
+  if (o.warps_per_cell < 0 || o.warps_per_cell > kMaxWarpsPerCell)
+    return fail(CHEM_EINVAL, "warps_per_cell must be 0 (automatic), 1 or 2");
   if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
   const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
   cudaStream_t strm = (cudaStream_t)stream;
   cudaError_t e;
+  const int wpc = o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc;
+  const MechView& V = h->view[wpc - 1];
+  const int cpb = cells_per_block(h, o.block_cells, wpc);
   if (o.mode == 0) {
-    const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : h->default_wpb);
     unsigned long long* stamp = nullptr;
     if (budget_ns) {
       if ((st = ensure_scratch(h, 1)) != CHEM_OK) return st;
       stamp = (unsigned long long*)((char*)h->scratch + kScrStamp);
       k_stamp<<<1, 32, 0, strm>>>(stamp);
     }
-    k_integrate_plain<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, strm>>>(
-        h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns);
+    auto kern = wpc == 1 ? k_integrate_plain<1> : k_integrate_plain<2>;
+    kern<<<(N + cpb - 1) / cpb, cpb * wpc * kWarp, cpb * h->cell_bytes, strm>>>(
+        V, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns);
     return launch_check("chem_integrate launch");
   }
   // persistent mode: sort by previous cost, then one resident grid pulling from the queue; the whole
   // sequence is one CUDA graph, captured once per argument set and replayed on `stream`
   if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
-  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : h->default_wpb);
   const int chunk = o.chunk > 0 ? o.chunk : 1;
   chem_handle_s::GraphKey key{};
-  key.N = N; key.mode = 1; key.wpb = wpb; key.chunk = chunk;
+  key.N = N; key.mode = 1; key.cpb = cpb; key.chunk = chunk; key.wpc = wpc;
   const void* ptrs[10] = {T, p, Y, dt, h_io, nsub, status, o.naccept, o.trace, h->scratch};
   for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
   key.d[0] = io.rtol; key.d[1] = io.atol; key.d[2] = io.h_init; key.d[3] = io.h_min; key.d[4] = o.time_budget_s;
@@ -703,11 +793,12 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
     if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamCreate");
     int bps = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_integrate_persistent, wpb * kWarp,
-                                                           (size_t)wpb * h->cell_bytes)) != cudaSuccess)
+    auto kern = wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cpb * wpc * kWarp,
+                                                           (size_t)cpb * h->cell_bytes)) != cudaSuccess)
       return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     bps = std::max(bps, 1);
-    const int grid = std::min(h->num_sms * bps, (N + wpb - 1) / wpb);
+    const int grid = std::min(h->num_sms * bps, (N + cpb - 1) / cpb);
     char* scr = (char*)h->scratch;
     int* counts = (int*)(scr + kScrCounts);
     int* cursor = (int*)(scr + kScrCursor);
@@ -722,8 +813,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
     k_stamp<<<1, 32, 0, cs>>>(stamp);
     k_sort_count<<<sblocks, 256, 0, cs>>>(N, nsub, counts);
     k_sort_scatter<<<sblocks, 256, 0, cs>>>(N, nsub, counts, cursor, perm);
-    k_integrate_persistent<<<grid, wpb * kWarp, wpb * h->cell_bytes, cs>>>(
-        h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+    kern<<<grid, cpb * wpc * kWarp, cpb * h->cell_bytes, cs>>>(
+        V, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
     cudaGraph_t graph = nullptr;
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &graph);
@@ -744,7 +835,7 @@ extern "C" chem_status chem_set_params(chem_handle h, const double* dlnA, const 
   chem_status st = check_handle(h);
   if (st != CHEM_OK) return st;
   if (h->hm.R == 0) return CHEM_OK;
-  k_set_params<<<(h->hm.R + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->view, h->rxd0, (double*)h->view.rxd,
+  k_set_params<<<(h->hm.R + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->view[0], h->rxd0, (double*)h->view[0].rxd,
                                                                          dlnA, dEa);
   return launch_check("chem_set_params launch");
 }
@@ -831,7 +922,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   // forward pass with the tape
   io.rec_h = rec_h; io.rec_ck = rec_ck; io.rec_n = rec_n; io.rec_cap = cap; io.rec_K = K;
   if ((e = cudaMemsetAsync(hio, 0, (size_t)N * 8, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  k_integrate_plain<<<N, kWarp, h->cell_bytes, strm>>>(h->view, h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
+  k_integrate_plain<1><<<N, kWarp, h->cell_bytes, strm>>>(h->view[0], h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
                                                        io, nullptr, 0ull);
   if ((st = launch_check("chem_adjoint forward launch")) != CHEM_OK) return st;
   // reverse pass, cells ordered by tape length (longest first) as in the sorted work queue
@@ -845,7 +936,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts), (int*)(scr + kScrCursor), perm);
   if ((e = cudaMemsetAsync(head, 0, 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   CellLayout Ld = h->L;
-  k_adjoint<<<grid, kWarp, adj_bytes, strm>>>(h->view, A, Ld, N, p, rec_h, rec_ck, rec_n, K, gT, gY, gcell, gT0, gY0,
+  k_adjoint<<<grid, kWarp, adj_bytes, strm>>>(h->view[0], A, Ld, N, p, rec_h, rec_ck, rec_n, K, gT, gY, gcell, gT0, gY0,
                                                status, head, perm, dws, wws, io);
   if ((st = launch_check("chem_adjoint reverse launch")) != CHEM_OK) return st;
   const int P = 2 * hm.R;
@@ -910,10 +1001,14 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   char* scr = nullptr;
   if ((st = noalloc_scratch_address(h->device, &scr)) != CHEM_OK) return st;
   const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-  const int wpb = warps_per_block(h, o.block_warps > 0 ? o.block_warps : h->default_wpb);
+  if (o.warps_per_cell < 0 || o.warps_per_cell > kMaxWarpsPerCell)
+    return fail(CHEM_EINVAL, "warps_per_cell must be 0 (automatic), 1 or 2");
+  const int wpc = o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc;
+  const int wpb = cells_per_block(h, o.block_cells, wpc);
   const int chunk = o.chunk > 0 ? o.chunk : 1;
   int bps = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_integrate_persistent, wpb * kWarp,
+  auto kern = wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, wpb * wpc * kWarp,
                                                                 (size_t)wpb * h->cell_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   bps = std::max(bps, 1);
@@ -930,8 +1025,8 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   k_stamp<<<1, 32, 0, strm>>>(stamp);
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, nsub, counts);
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, nsub, counts, cursor, perm);
-  k_integrate_persistent<<<grid, wpb * kWarp, wpb * h->cell_bytes, strm>>>(
-      h->view, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+  kern<<<grid, wpb * wpc * kWarp, wpb * h->cell_bytes, strm>>>(
+      h->view[wpc - 1], h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
   return launch_check("chem_integrate_noalloc launch");
 }
 

@@ -44,12 +44,12 @@ int enc_nu(int nu) {
 // outputs without terms are left untouched (programs that accumulate into their outputs); otherwise
 // they are written with 0.
 bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, HostGather& G, std::string& err,
-                  bool skip_empty = false) {
+                  int width, bool skip_empty = false) {
   G = HostGather();
   long total = 0;
   for (auto& g : groups) total += skip_empty ? (long)g.size() : (long)std::max<size_t>(g.size(), 1);
   if (groups.empty()) return true;
-  const long cap = std::max<long>(1, (total + kWarp - 1) / kWarp);
+  const long cap = std::max<long>(1, (total + width - 1) / width);
   struct Piece { int g; int first; int count; int partial; };
   std::vector<Piece> pieces;
   int n_partial = 0;
@@ -76,16 +76,16 @@ bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, H
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return std::max(pieces[x].count, 1) > std::max(pieces[y].count, 1); });
-  std::vector<std::vector<int>> lane(kWarp);
-  std::vector<long> load(kWarp, 0);
+  std::vector<std::vector<int>> lane(width);
+  std::vector<long> load(width, 0);
   for (int pi : order) {
     int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     lane[l].push_back(pi);
     load[l] += std::max(pieces[pi].count, 1);
   }
   G.steps = (int)*std::max_element(load.begin(), load.end());
-  G.ops.assign((size_t)G.steps * kWarp, GatherOp{0, 0, DST_NONE, 1});
-  for (int l = 0; l < kWarp; ++l) {
+  G.ops.assign((size_t)G.steps * width, GatherOp{0, 0, DST_NONE, 1});
+  for (int l = 0; l < width; ++l) {
     int s = 0;
     for (int pi : lane[l]) {
       const Piece& P = pieces[pi];
@@ -108,7 +108,7 @@ bool build_gather(const std::vector<std::vector<std::pair<int, int>>>& groups, H
           if (P.partial < 0 && P.g >= PARTIAL_BIT) { err = "too many gather outputs"; return false; }
           op.dst = (uint16_t)dst;
         }
-        G.ops[(size_t)s * kWarp + l] = op;
+        G.ops[(size_t)s * width + l] = op;
       }
     }
   }
@@ -127,7 +127,8 @@ struct DagOp {
 
 // Steps of one kind, at most 32 ops, distinct targets; ops become ready when all predecessors are done.
 // Priority = longest path to the end of the DAG (critical path first).
-bool schedule(std::vector<DagOp>& ops, std::vector<ElimOp>& out, std::vector<uint8_t>& kinds, std::string& err) {
+bool schedule(std::vector<DagOp>& ops, std::vector<ElimOp>& out, std::vector<uint8_t>& kinds, std::string& err,
+              int width) {
   const int N = (int)ops.size();
   std::vector<int> indeg(N, 0), topo;
   topo.reserve(N);
@@ -165,14 +166,14 @@ bool schedule(std::vector<DagOp>& ops, std::vector<ElimOp>& out, std::vector<uin
     std::set<int> used;
     std::vector<int> keep;
     for (int v : ready) {
-      if ((int)step.size() < kWarp && ops[v].kind == K && !used.count(ops[v].target)) {
+      if ((int)step.size() < width && ops[v].kind == K && !used.count(ops[v].target)) {
         step.push_back(v);
         used.insert(ops[v].target);
       } else {
         keep.push_back(v);
       }
     }
-    for (int l = 0; l < kWarp; ++l) {   // every lane's op carries the step's kind
+    for (int l = 0; l < width; ++l) {   // every lane's op carries the step's kind
       ElimOp e = l < (int)step.size() ? ops[step[l]].enc : ElimOp{OP_IDLE, 0, 0, 0};
       e.kind = (uint16_t)K;
       out.push_back(e);
@@ -219,6 +220,7 @@ std::vector<int> min_degree_order(int m, const std::vector<std::vector<char>>& a
 
 chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string& err) {
   hm = HostMech();
+  for (int w = 1; w <= kMaxWarpsPerCell; ++w) hm.prog[w - 1].width = w * kWarp;
   const int n = d.n_species, R = d.n_reactions;
   if (n < 1 || R < 0) { err = "n_species must be >= 1 and n_reactions >= 0"; return CHEM_EINVAL; }
   if (!d.W || !d.nasa_lo || !d.nasa_hi || !d.T_mid) { err = "species arrays must not be NULL"; return CHEM_EINVAL; }
@@ -418,8 +420,10 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       gr[hm.entry_row[e]].push_back({e, hm.entry_col[e]});
       gc[hm.entry_col[e]].push_back({e, hm.entry_row[e]});
     }
-    if (!build_gather(gw, hm.g_omega, err) || !build_gather(gr, hm.g_row, err) || !build_gather(gc, hm.g_col, err))
-      return CHEM_EUNSUPPORTED;
+    for (HostProg& P : hm.prog)
+      if (!build_gather(gw, P.g_omega, err, P.width) || !build_gather(gr, P.g_row, err, P.width) ||
+          !build_gather(gc, P.g_col, err, P.width))
+        return CHEM_EUNSUPPORTED;
   }
 
   // ---- ordering (minimum degree, T last) and symbolic LU
@@ -501,7 +505,10 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       ops[scale_of[a]].succ.push_back((int)v);
       for (int u : upd_to[b]) ops[u].succ.push_back((int)v);
     }
-    if (!schedule(ops, hm.lu_ops, hm.lu_kind, err)) return CHEM_EINVAL;
+    for (HostProg& P : hm.prog) {
+      std::vector<DagOp> work = ops;
+      if (!schedule(work, P.lu_ops, P.lu_kind, err, P.width)) return CHEM_EINVAL;
+    }
   }
   // ---- substitution program (forward with unit L, backward with U and 1/diag), state-order indices
   {
@@ -540,7 +547,10 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       }
     }
     for (auto& pr : bw) ops[sc[pr.second]].succ.push_back(pr.first);           // RAW backward
-    if (!schedule(ops, hm.sv_ops, hm.sv_kind, err)) return CHEM_EINVAL;
+    for (HostProg& P : hm.prog) {
+      std::vector<DagOp> work = ops;
+      if (!schedule(work, P.sv_ops, P.sv_kind, err, P.width)) return CHEM_EINVAL;
+    }
   }
   // ---- transposed substitution (A^T x = b): forward with U^T (scaled by 1/diag), then backward with
   //      the unit L^T.  In factor positions: x_p -= U_qp x_q (q < p), x_p *= 1/U_pp; then x_p -= L_qp x_q
@@ -579,7 +589,10 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       ops[sc[q]].succ.push_back(pr.first);                     // x_q forward-final
       for (int w : b_w[q]) ops[w].succ.push_back(pr.first);    // x_q backward-final
     }
-    if (!schedule(ops, hm.svT_ops, hm.svT_kind, err)) return CHEM_EINVAL;
+    for (HostProg& P : hm.prog) {
+      std::vector<DagOp> work = ops;
+      if (!schedule(work, P.svT_ops, P.svT_kind, err, P.width)) return CHEM_EINVAL;
+    }
   }
 
   // ---- Jacobian passes.  A reaction leaves one dq/dT value and one derivative slot per column species;
@@ -611,7 +624,7 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
     }
     const int P = (int)cut.size() - 1;
     hm.jpass.clear();
-    hm.g_jac.assign(P, HostGather());
+    for (HostProg& Pg : hm.prog) Pg.g_jac.assign(P, HostGather());
     for (int p = 0; p < P; ++p) {
       const int rb = cut[p], re = cut[p + 1];
       const int sb = R > 0 && rb < R ? hm.rxi[(size_t)rb * RX_I + 13] : hm.n_dslot;
@@ -628,7 +641,8 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
             gj[eidx[kv.first][slots_sp[r][c]]].push_back({cnt + base + (int)c - sb, nu});
         }
       }
-      if (!build_gather(gj, hm.g_jac[p], err, true)) return CHEM_EUNSUPPORTED;
+      for (HostProg& Pg : hm.prog)
+        if (!build_gather(gj, Pg.g_jac[p], err, Pg.width, true)) return CHEM_EUNSUPPORTED;
     }
   }
   return CHEM_OK;

@@ -9,10 +9,20 @@
 namespace chemgb {
 
 struct HostGather {
-  std::vector<GatherOp> ops;
+  std::vector<GatherOp> ops;   // [steps * width]
   int steps = 0;
   int n_partial = 0;
   std::vector<int> comb;   // triples
+};
+
+// The warp programs for one group width (lanes that share a cell: 32 per warp times the warps per
+// cell).
+struct HostProg {
+  int width = kWarp;
+  HostGather g_omega, g_row, g_col;
+  std::vector<HostGather> g_jac;       // one gather program per Jacobian pass
+  std::vector<ElimOp> lu_ops, sv_ops, svT_ops;   // [steps * width]
+  std::vector<uint8_t> lu_kind, sv_kind, svT_kind;
 };
 
 struct HostMech {
@@ -20,15 +30,12 @@ struct HostMech {
   std::vector<int> rx_order;           // compiled reaction index -> description index
   std::vector<double> sp, rxd, eff_am1, dslot_am1, entry_wratio;
   std::vector<int> rxi, eff_sp, dslot_sp, dslot_mask, entry_row, entry_col;
-  HostGather g_omega, g_row, g_col;
-  std::vector<HostGather> g_jac;       // one gather program per Jacobian pass
+  HostProg prog[kMaxWarpsPerCell];     // prog[w - 1]: programs for w warps per cell
   std::vector<int> jpass;              // [passes * 4]: first reaction, end reaction, first slot, reactions
   int jreg = 0;                        // doubles of the largest pass (dq/dT values + derivative slots)
   std::vector<int> perm, iperm;        // LU position -> state index, and back
   std::vector<int> lu_src, lu_diag, s_out;
   std::vector<int> lu_rowptr, lu_col;  // factor pattern, CSR in LU (permuted) order
-  std::vector<ElimOp> lu_ops, sv_ops, svT_ops;
-  std::vector<uint8_t> lu_kind, sv_kind, svT_kind;
   std::vector<int> csr_ptr, csr_col;   // S pattern in natural state order
   long long lu_flops = 0;              // multiply-adds of one factorisation (algorithmic)
 };

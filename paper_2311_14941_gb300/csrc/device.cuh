@@ -27,6 +27,74 @@
 
 namespace chemgb {
 
+// -------------------------------------------------------------------------------------- lane groups
+// The lanes that integrate one cell: one warp (GrpW<1>), or two consecutive warps of a block (GrpW<2>).
+// Work inside a cell is strided over the group's lanes; shared-memory ordering inside the group is a
+// warp barrier for one warp and a named barrier (bar.sync id, 64) for two.  Reductions add each warp's
+// butterfly sum in warp order, so every lane of the group holds the same, reproducible value.  The
+// group size is a compile-time constant: the one-warp code is the plain warp code.
+template <int W>
+struct GrpW;
+
+template <>
+struct GrpW<1> {
+  static constexpr int size = kWarp;
+  int lane;
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
+template <>
+struct GrpW<2> {
+  static constexpr int size = 2 * kWarp;
+  int lane;     // 0 .. 63
+  int bar;      // named barrier of the group: 1 + the cell's index in its block
+  double* xch;  // one exchange slot per warp in the cell's shared memory
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(size) : "memory");
+  }
+};
+
+using Grp1 = GrpW<1>;
+using Grp2 = GrpW<2>;
+
+__device__ __forceinline__ double gsum(const Grp1&, double v) { return warp_sum(v); }
+__device__ __forceinline__ double gsum(const Grp2& g, double v) {
+  v = warp_sum(v);
+  g.sync();   // earlier readers of the slots are done
+  if ((g.lane & (kWarp - 1)) == 0) g.xch[g.lane / kWarp] = v;
+  g.sync();
+  return g.xch[0] + g.xch[1];
+}
+template <class G>
+__device__ __forceinline__ Dual gsum(const G& g, Dual v) { return Dual(gsum(g, v.v), gsum(g, v.d)); }
+template <class G, int K>
+__device__ __forceinline__ DualN<K> gsum(const G& g, DualN<K> v) {
+  v.v = gsum(g, v.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) v.d[i] = gsum(g, v.d[i]);
+  return v;
+}
+
+__device__ __forceinline__ bool gall(const Grp1&, bool ok) { return __all_sync(0xffffffffu, ok); }
+__device__ __forceinline__ bool gall(const Grp2& g, bool ok) {
+  ok = __all_sync(0xffffffffu, ok);
+  g.sync();
+  if ((g.lane & (kWarp - 1)) == 0) g.xch[g.lane / kWarp] = ok ? 1.0 : 0.0;
+  g.sync();
+  return g.xch[0] != 0.0 && g.xch[1] != 0.0;
+}
+
+// The value of lane 0, on every lane of the group.
+__device__ __forceinline__ long long gbcast(const Grp1&, long long v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ long long gbcast(const Grp2& g, long long v) {
+  g.sync();
+  if (g.lane == 0) g.xch[0] = __longlong_as_double(v);
+  g.sync();
+  const long long r = __double_as_longlong(g.xch[0]);
+  g.sync();   // everyone has read the slot before it is reused
+  return r;
+}
+
 // RODAS3 in transformed form.  a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1, m = b Gamma^-1,
 // e = (b - bhat) Gamma^-1, obtained from the published alpha_ij, gamma_ij, b, bhat (gamma = 1/2).
 // Zero coefficients are exploited below: a21 = a32 = a42 = 0 (stage 2 reuses f(y)), m2 = 0,
@@ -70,18 +138,18 @@ __device__ __forceinline__ double nu_of(int b) { return __hiloint2double(b << 16
 // -------------------------------------------------------------------------------------- gathers
 // out[g] = sum over the group's terms of val(a, b); partial sums of split groups are combined after.
 // ACC: out[g] += sum instead (outputs without terms in the program are left as they are).
-template <bool ACC = false, class Sc, class F>
-__device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F valf, int lane) {
+template <bool ACC = false, class Sc, class F, class Gp>
+__device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F valf, const Gp& g) {
   Sc acc = Sc(0.0);
-  const GatherOp* op = G.ops + lane;
+  const GatherOp* op = G.ops + g.lane;
   const int NS = G.steps;
   const GatherOp idle{0, 0, DST_NONE, 1};
   GatherOp n1 = NS > 0 ? ld_gop(op) : idle;
-  GatherOp n2 = NS > 1 ? ld_gop(op + kWarp) : idle;
+  GatherOp n2 = NS > 1 ? ld_gop(op + g.size) : idle;
   for (int s = 0; s < NS; ++s) {
     const GatherOp o = n1;
     n1 = n2;
-    if (s + 2 < NS) n2 = ld_gop(op + (size_t)(s + 2) * kWarp);
+    if (s + 2 < NS) n2 = ld_gop(op + (size_t)(s + 2) * g.size);
     if (!(o.flags & 1)) acc += valf(o.a, o.b);
     if (o.dst != DST_NONE) {
       if (o.dst & PARTIAL_BIT) part[o.dst & 0x7FFF] = acc;
@@ -90,14 +158,14 @@ __device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F
       acc = Sc(0.0);
     }
   }
-  __syncwarp();
-  for (int c = lane; c < G.n_comb; c += kWarp) {
+  g.sync();
+  for (int c = g.lane; c < G.n_comb; c += g.size) {
     const int dst = __ldg(G.comb + 3 * c), f = __ldg(G.comb + 3 * c + 1), cnt = __ldg(G.comb + 3 * c + 2);
     Sc s = Sc(0.0);
     for (int i = 0; i < cnt; ++i) s += part[f + i];
     if (ACC) out[dst] += s; else out[dst] = s;
   }
-  __syncwarp();
+  g.sync();
 }
 
 // -------------------------------------------------------------------------------------- thermo
@@ -130,9 +198,9 @@ __device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, cons
 
 // NASA-7 at T for every species, two species per lane at a time (independent exp chains in flight);
 // fills C, hRT, eg = exp(g), emg = 1/eg, cpR.
-template <class Sc, bool DERIV>
+template <class Sc, bool DERIV, class Gp>
 __device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, const CellLayout& L, const Sc* y,
-                                                  double p, int lane) {
+                                                  double p, const Gp& g) {
   ScalT<Sc> sc;
   sc.T = y[0];
   sc.lnT = slog(sc.T);
@@ -144,9 +212,9 @@ __device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, cons
   Sc* __restrict__ emg = s + L.emg;
   Sc* __restrict__ cpv = s + L.cpR;
   Sc* __restrict__ C = s + L.C;
-  for (int k = lane; k < M.n; k += 2 * kWarp) {
-    const bool v2 = k + kWarp < M.n;
-    const int k2 = v2 ? k + kWarp : k;
+  for (int k = g.lane; k < M.n; k += 2 * g.size) {
+    const bool v2 = k + g.size < M.n;
+    const int k2 = v2 ? k + g.size : k;
     const SpOut<Sc> a = species_item<Sc, DERIV>(M, k, y, T, sc.lnT, sc.invT);
     const SpOut<Sc> b = species_item<Sc, DERIV>(M, k2, y, T, sc.lnT, sc.invT);
     const Sc ia = 1.0 / a.eg, ib = 1.0 / b.eg;
@@ -160,9 +228,9 @@ __device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, cons
     hRT[k] = a.hRT; egv[k] = a.eg; emg[k] = ia; cpv[k] = a.cpR; C[k] = a.yw;
     if (v2) { hRT[k2] = b.hRT; egv[k2] = b.eg; emg[k2] = ib; cpv[k2] = b.cpR; C[k2] = b.yw; }
   }
-  sig = warp_sum(sig);
-  cps = warp_sum(cps);
-  if (DERIV) dcps = warp_sum(dcps);
+  sig = gsum(g, sig);
+  cps = gsum(g, cps);
+  if (DERIV) dcps = gsum(g, dcps);
   sc.Wbar = 1.0 / sig;
   sc.ctot = p * sc.invT * (1.0 / kRu);
   sc.rho = sc.ctot * sc.Wbar;
@@ -171,9 +239,9 @@ __device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, cons
   sc.dcps = dcps;
   sc.rtp = kRu * T * (1.0 / kP0);
   sc.irtp = 1.0 / sc.rtp;
-  __syncwarp();
-  for (int k = lane; k < M.n; k += kWarp) C[k] *= sc.rho;
-  __syncwarp();
+  g.sync();
+  for (int k = g.lane; k < M.n; k += g.size) C[k] *= sc.rho;
+  g.sync();
   return sc;
 }
 
@@ -318,49 +386,49 @@ __device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<
 
 // Rates of progress of reactions [rb, re).  Reactions are ordered Troe, third-body, elementary, so every
 // segment has warp-uniform control flow; elementary reactions go two per lane (two exp chains).
-template <class Sc, bool DERIV>
+template <class Sc, bool DERIV, class Gp>
 __device__ __forceinline__ void eval_reactions(const MechView& M, Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
-                                               int lane, int rb, int re, int dq_off = 0, int d_off = 0) {
+                                               const Gp& g, int rb, int re, int dq_off = 0, int d_off = 0) {
   const Sc* C = s + L.C;
   const Sc* eg = s + L.eg;
   const Sc* emg = s + L.emg;
   const Sc* hRT = s + L.hRT;
   const int t1 = min(re, M.n_troe), e0 = M.n_troe + M.n_tb, b1 = min(re, e0);
-  for (int r = rb + lane; r < t1; r += kWarp)
+  for (int r = rb + g.lane; r < t1; r += g.size)
     rx_store<Sc, 2, DERIV>(M, r, rx_core<Sc, 2, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true, dq_off, d_off);
-  for (int r = max(rb, M.n_troe) + lane; r < b1; r += kWarp)
+  for (int r = max(rb, M.n_troe) + g.lane; r < b1; r += g.size)
     rx_store<Sc, 1, DERIV>(M, r, rx_core<Sc, 1, DERIV>(M, r, C, eg, emg, hRT, sc), s, L, sc, true, dq_off, d_off);
-  for (int r = max(rb, e0) + lane; r < re; r += 2 * kWarp) {
-    const bool v2 = r + kWarp < re;
-    const int r2 = v2 ? r + kWarp : r;
+  for (int r = max(rb, e0) + g.lane; r < re; r += 2 * g.size) {
+    const bool v2 = r + g.size < re;
+    const int r2 = v2 ? r + g.size : r;
     const RxCore<Sc> a = rx_core<Sc, 0, DERIV>(M, r, C, eg, emg, hRT, sc);
     const RxCore<Sc> b = rx_core<Sc, 0, DERIV>(M, r2, C, eg, emg, hRT, sc);
     rx_store<Sc, 0, DERIV>(M, r, a, s, L, sc, true, dq_off, d_off);
     rx_store<Sc, 0, DERIV>(M, r2, b, s, L, sc, v2, dq_off, d_off);
   }
-  __syncwarp();
+  g.sync();
 }
 
 // -------------------------------------------------------------------------------------- f and J
 // f(y) into out[m].  Uses C/hRT/eg/emg/cpR/q scratch.  Returns the scalars of the evaluation.
-template <class Sc>
+template <class Sc, class Gp>
 __device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
-                                            Sc* out, int lane) {
-  ScalT<Sc> sc = eval_species<Sc, false>(M, s, L, y, p, lane);
-  eval_reactions<Sc, false>(M, s, L, sc, lane, 0, M.R);
+                                            Sc* out, const Gp& g) {
+  ScalT<Sc> sc = eval_species<Sc, false>(M, s, L, y, p, g);
+  eval_reactions<Sc, false>(M, s, L, sc, g, 0, M.R);
   const Sc* q = s + L.q;
   Sc* part = s + L.part;
   Sc* w = out + 1;   // production rates written in place, then scaled
-  run_gather(M.g_omega, w, part, [&](int a, int b) { return nu_of(b) * q[a]; }, lane);
+  run_gather(M.g_omega, w, part, [&](int a, int b) { return nu_of(b) * q[a]; }, g);
   Sc Qs = Sc(0.0);
-  for (int k = lane; k < M.n; k += kWarp) {
+  for (int k = g.lane; k < M.n; k += g.size) {
     const Sc om = w[k];
     Qs = sfma(s[L.hRT + k], om, Qs);
     w[k] = om * __ldg(M.sp + (size_t)k * SP_STRIDE + 1) * sc.irho;
   }
-  Qs = warp_sum(Qs);
-  if (lane == 0) out[0] = -kRu * sc.T * Qs / (sc.rho * sc.cp);
-  __syncwarp();
+  Qs = gsum(g, Qs);
+  if (g.lane == 0) out[0] = -kRu * sc.T * Qs / (sc.rho * sc.cp);
+  g.sync();
   return sc;
 }
 
@@ -368,10 +436,10 @@ __device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const Cell
 // U1 (g), U2 (t).  The reactions run in passes (see MechView::jpass): each pass leaves dq/dT and the
 // derivative slots of its reactions in the region, and its gather adds them into the Y block of S
 // (Dtil) and into the T-column slots of S, which hold w_T until the T column is formed below.
-template <class Sc>
+template <class Sc, class Gp>
 __device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
-                                              int lane) {
-  ScalT<Sc> sc = eval_species<Sc, true>(M, s, L, y, p, lane);
+                                              const Gp& g) {
+  ScalT<Sc> sc = eval_species<Sc, true>(M, s, L, y, p, g);
   Sc* part = s + L.part;
   Sc* w = s + L.x;      // w_k
   Sc* gk = s + L.U1;
@@ -381,23 +449,23 @@ __device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const Ce
   const Sc* C = s + L.C;
   const Sc* hRT = s + L.hRT;
   const Sc* reg = s + L.D;
-  for (int e = lane; e < M.nY + M.n; e += kWarp) S[e] = Sc(0.0);
+  for (int e = g.lane; e < M.nY + M.n; e += g.size) S[e] = Sc(0.0);
   for (int ps = 0; ps < M.n_jpass; ++ps) {
     const int rb = M.jpass[ps][JP_RB], cnt = M.jpass[ps][JP_CNT];
-    eval_reactions<Sc, true>(M, s, L, sc, lane, rb, M.jpass[ps][JP_RE], L.D - rb, L.D + cnt - M.jpass[ps][JP_SB]);
-    run_gather<true>(M.g_jac[ps], S, part, [&](int a, int b) { return nu_of(b) * reg[a]; }, lane);
+    eval_reactions<Sc, true>(M, s, L, sc, g, rb, M.jpass[ps][JP_RE], L.D - rb, L.D + cnt - M.jpass[ps][JP_SB]);
+    run_gather<true>(M.g_jac[ps], S, part, [&](int a, int b) { return nu_of(b) * reg[a]; }, g);
   }
   const Sc* q = s + L.q;
-  run_gather(M.g_omega, w, part, [&](int a, int b) { return nu_of(b) * q[a]; }, lane);
-  run_gather(M.g_row, gk, part, [&](int a, int b) { return S[a] * C[b]; }, lane);
-  run_gather(M.g_col, tk, part, [&](int a, int b) { return S[a] * hRT[b]; }, lane);
+  run_gather(M.g_omega, w, part, [&](int a, int b) { return nu_of(b) * q[a]; }, g);
+  run_gather(M.g_row, gk, part, [&](int a, int b) { return S[a] * C[b]; }, g);
+  run_gather(M.g_col, tk, part, [&](int a, int b) { return S[a] * hRT[b]; }, g);
   Sc* f = s + L.f0;
   Sc* u = s + L.u;
   Sc* v = s + L.v;
   const Sc T = sc.T;
   // f, u and the T column; partial sums for the T row scalars
   Sc Qs = Sc(0.0), A1 = Sc(0.0), A2 = Sc(0.0);
-  for (int k = lane; k < M.n; k += kWarp) {
+  for (int k = g.lane; k < M.n; k += g.size) {
     const double Wk = __ldg(M.sp + (size_t)k * SP_STRIDE + 1);
     const Sc om = w[k], g = gk[k];
     const Sc dwT = sfma(-g, sc.invT, wT[k]);   // read before the T column overwrites w_T
@@ -411,53 +479,54 @@ __device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const Ce
     A1 = sfma(s[L.cpR + k], om, sfma(T * h, dwT, A1));
     A2 = sfma(h, g, A2);
   }
-  Qs = warp_sum(Qs);
-  A1 = warp_sum(A1);
-  A2 = warp_sum(A2);
+  Qs = gsum(g, Qs);
+  A1 = gsum(g, A1);
+  A2 = gsum(g, A2);
   const Sc rcp = sc.rho * sc.cp;
   const Sc fT = -kRu * T * Qs / rcp;
   // T row: S_Tj for species j, then S_TT; u_T; v_T
-  for (int j = lane; j < M.n; j += kWarp) {
+  for (int j = g.lane; j < M.n; j += g.size) {
     const double iw = __ldg(M.sp + (size_t)j * SP_STRIDE);
     S[M.nY + M.n + 1 + j] = -kRu * sfma(T, tk[j], fT * s[L.cpR + j]) * iw / sc.cp;
   }
-  if (lane == 0) {
+  if (g.lane == 0) {
     f[0] = fT;
     S[M.nY + M.n] = -kRu * A1 / rcp + fT * (sc.invT - kRu * sc.dcps / sc.cp);
     u[0] = kRu * T * A2 / rcp + fT;
     v[0] = Sc(0.0);
   }
-  __syncwarp();
+  g.sync();
   // species block: S_kj = (W_k / W_j) Dtil_kj (after the row and column sums used Dtil)
-  for (int e = lane; e < M.nY; e += kWarp) S[e] *= __ldg(M.entry_wratio + e);
-  __syncwarp();
+  for (int e = g.lane; e < M.nY; e += g.size) S[e] *= __ldg(M.entry_wratio + e);
+  g.sync();
   return sc;
 }
 
 // -------------------------------------------------------------------------------------- linear algebra
 // LU of A = I/(h gamma) - S, in place, by the precomputed elimination program.  false if a pivot is 0
 // or not finite.
+template <class Gp>
 __device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, const CellLayout& L, double gh,
-                                                int lane) {
+                                                const Gp& g) {
   double* LU = s + L.LU;
   double* dinv = s + L.dinv;
   const double* S = s + L.S;
-  for (int l = lane; l < M.nnz_LU; l += kWarp) {
+  for (int l = g.lane; l < M.nnz_LU; l += g.size) {
     const int src = __ldg(M.lu_src + l);
     LU[l] = src >= 0 ? -S[src] : 0.0;
   }
-  __syncwarp();
-  for (int i = lane; i < M.m; i += kWarp) LU[__ldg(M.lu_diag + i)] += gh;
-  __syncwarp();
+  g.sync();
+  for (int i = g.lane; i < M.m; i += g.size) LU[__ldg(M.lu_diag + i)] += gh;
+  g.sync();
   bool ok = true;
-  const ElimOp* op = M.lu_ops + lane;
+  const ElimOp* op = M.lu_ops + g.lane;
   const int NS = M.lu_steps;
   ElimOp n1 = NS > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, 0};
-  ElimOp n2 = NS > 1 ? ld_eop(op + kWarp) : ElimOp{OP_IDLE, 0, 0, 0};
+  ElimOp n2 = NS > 1 ? ld_eop(op + g.size) : ElimOp{OP_IDLE, 0, 0, 0};
   for (int st = 0; st < NS; ++st) {
     const ElimOp o = n1;
     n1 = n2;
-    if (st + 2 < NS) n2 = ld_eop(op + (size_t)(st + 2) * kWarp);
+    if (st + 2 < NS) n2 = ld_eop(op + (size_t)(st + 2) * g.size);
     const int kind = o.kind;
     if (o.t != OP_IDLE) {
       if (kind == K_UPDATE) {
@@ -471,32 +540,32 @@ __device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, co
         dinv[o.t] = r;
       }
     }
-    __syncwarp();
+    g.sync();
   }
-  return __all_sync(0xffffffffu, ok);
+  return gall(g, ok);
 }
 
 // x <- A^{-1} x (forward and backward substitution by the precomputed program; state-order vector).
 // With x2 != nullptr the same program solves a second right-hand side in the same steps.
-template <bool TWO>
+template <bool TWO, class Gp>
 __device__ __forceinline__ void lu_solve_impl(const MechView& M, const double* s, const CellLayout& L, double* x,
-                                              double* x2, int lane) {
+                                              double* x2, const Gp& g) {
   const double* LU = s + L.LU;
   const double* dinv = s + L.dinv;
-  const ElimOp* op = M.sv_ops + lane;
+  const ElimOp* op = M.sv_ops + g.lane;
   const int S = M.sv_steps;
   // the factor does not change during the solve: each step's coefficient (L/U entry or 1/pivot; idle
   // ops read entry 0) is loaded one step ahead, off the step-to-step dependence through x
   auto coef = [&](const ElimOp& o) { return (o.kind == K_UPDATE ? LU : dinv)[o.a]; };
   ElimOp n1 = S > 0 ? ld_eop(op) : ElimOp{OP_IDLE, 0, 0, K_SCALE};
-  ElimOp n2 = S > 1 ? ld_eop(op + kWarp) : ElimOp{OP_IDLE, 0, 0, K_SCALE};
+  ElimOp n2 = S > 1 ? ld_eop(op + g.size) : ElimOp{OP_IDLE, 0, 0, K_SCALE};
   double c1 = coef(n1);
   for (int st = 0; st < S; ++st) {
     const ElimOp o = n1;
     const double c = c1;
     n1 = n2;
     c1 = coef(n1);
-    if (st + 2 < S) n2 = ld_eop(op + (size_t)(st + 2) * kWarp);
+    if (st + 2 < S) n2 = ld_eop(op + (size_t)(st + 2) * g.size);
     if (o.t != OP_IDLE) {
       if (o.kind == K_UPDATE) {
         x[o.t] = fma(-c, x[o.b], x[o.t]);
@@ -506,26 +575,28 @@ __device__ __forceinline__ void lu_solve_impl(const MechView& M, const double* s
         if (TWO) x2[o.t] *= c;
       }
     }
-    __syncwarp();
+    g.sync();
   }
 }
 
+template <class Gp>
 __device__ __forceinline__ void lu_solve(const MechView& M, const double* s, const CellLayout& L, double* x,
-                                         int lane) {
-  lu_solve_impl<false>(M, s, L, x, nullptr, lane);
+                                         const Gp& g) {
+  lu_solve_impl<false>(M, s, L, x, nullptr, g);
 }
 
 // x <- M^{-1} x with M = A - u v^T:  x = A^-1 x + z (v . A^-1 x) / (1 - v . z),  z = A^-1 u
+template <class Gp>
 __device__ __forceinline__ void sm_solve(const MechView& M, const double* s, const CellLayout& L, double* x,
-                                         double iden, int lane) {
-  lu_solve(M, s, L, x, lane);
+                                         double iden, const Gp& g) {
+  lu_solve(M, s, L, x, g);
   const double* v = s + L.v;
   const double* z = s + L.z;
   double d = 0.0;
-  for (int i = lane; i < M.m; i += kWarp) d = fma(v[i], x[i], d);
-  d = warp_sum(d) * iden;
-  for (int i = lane; i < M.m; i += kWarp) x[i] = fma(z[i], d, x[i]);
-  __syncwarp();
+  for (int i = g.lane; i < M.m; i += g.size) d = fma(v[i], x[i], d);
+  d = gsum(g, d) * iden;
+  for (int i = g.lane; i < M.m; i += g.size) x[i] = fma(z[i], d, x[i]);
+  g.sync();
 }
 
 // -------------------------------------------------------------------------------------- step
@@ -536,12 +607,13 @@ struct StepOut {
 
 // One RODAS3 attempt of size h from y (f0, S, u, v already evaluated at y).  ynew into ytmp, err into
 // the return value.  U1..U4, x, z, LU are scratch.
+template <class Gp>
 __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, const CellLayout& L, double p, double h,
-                                               double rtol, double atol, int lane) {
+                                               double rtol, double atol, const Gp& g) {
   StepOut so{false, 0.0};
   const int m = M.m;
   const double ih = 1.0 / h;
-  if (!lu_build_factor(M, s, L, ih * (1.0 / RG), lane)) return so;
+  if (!lu_build_factor(M, s, L, ih * (1.0 / RG), g)) return so;
   double* y = s + L.y;
   double* yt = s + L.ytmp;
   double* f0 = s + L.f0;
@@ -553,42 +625,42 @@ __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, con
   const double* u = s + L.u;
   const double* v = s + L.v;
   // z = A^-1 u (the Sherman-Morrison vector) and stage 1's A^-1 f0, in one pass of the solve program
-  for (int i = lane; i < m; i += kWarp) { z[i] = u[i]; U1[i] = f0[i]; }
-  __syncwarp();
-  lu_solve_impl<true>(M, s, L, z, U1, lane);
+  for (int i = g.lane; i < m; i += g.size) { z[i] = u[i]; U1[i] = f0[i]; }
+  g.sync();
+  lu_solve_impl<true>(M, s, L, z, U1, g);
   double vz = 0.0, vx = 0.0;
-  for (int i = lane; i < m; i += kWarp) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
-  vz = warp_sum(vz);
-  vx = warp_sum(vx);
+  for (int i = g.lane; i < m; i += g.size) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
+  vz = gsum(g, vz);
+  vx = gsum(g, vx);
   const double den = 1.0 - vz;
   if (!(den != 0.0) || !isfinite(den)) return so;
   const double iden = 1.0 / den;
   // stage 1: Sherman-Morrison correction of A^-1 f0
   vx *= iden;
-  for (int i = lane; i < m; i += kWarp) U1[i] = fma(z[i], vx, U1[i]);
-  __syncwarp();
+  for (int i = g.lane; i < m; i += g.size) U1[i] = fma(z[i], vx, U1[i]);
+  g.sync();
   // stage 2 (a21 = 0: f(y) again)
-  for (int i = lane; i < m; i += kWarp) U2[i] = fma(C21 * ih, U1[i], f0[i]);
-  __syncwarp();
-  sm_solve(M, s, L, U2, iden, lane);
+  for (int i = g.lane; i < m; i += g.size) U2[i] = fma(C21 * ih, U1[i], f0[i]);
+  g.sync();
+  sm_solve(M, s, L, U2, iden, g);
   // stage 3
-  for (int i = lane; i < m; i += kWarp) yt[i] = fma(A31, U1[i], y[i]);
-  __syncwarp();
-  eval_f<double>(M, s, L, yt, p, U3, lane);
-  for (int i = lane; i < m; i += kWarp) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
-  __syncwarp();
-  sm_solve(M, s, L, U3, iden, lane);
+  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(A31, U1[i], y[i]);
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U3, g);
+  for (int i = g.lane; i < m; i += g.size) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
+  g.sync();
+  sm_solve(M, s, L, U3, iden, g);
   // stage 4
-  for (int i = lane; i < m; i += kWarp) yt[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
-  __syncwarp();
-  eval_f<double>(M, s, L, yt, p, U4, lane);
-  for (int i = lane; i < m; i += kWarp) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
-  __syncwarp();
-  sm_solve(M, s, L, U4, iden, lane);
+  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U4, g);
+  for (int i = g.lane; i < m; i += g.size) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
+  g.sync();
+  sm_solve(M, s, L, U4, iden, g);
   // solution, embedded error, scaled RMS norm
   double e2 = 0.0;
   bool fin = true;
-  for (int i = lane; i < m; i += kWarp) {
+  for (int i = g.lane; i < m; i += g.size) {
     const double yn = fma(M4, U4[i], fma(M3, U3[i], fma(M1, U1[i], y[i])));
     yt[i] = yn;
     const double sc = fma(rtol, fmax(fabs(y[i]), fabs(yn)), atol);
@@ -596,9 +668,9 @@ __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, con
     e2 = fma(e, e, e2);
     fin = fin && isfinite(yn);
   }
-  e2 = warp_sum(e2);
-  fin = __all_sync(0xffffffffu, fin);
-  __syncwarp();
+  e2 = gsum(g, e2);
+  fin = gall(g, fin);
+  g.sync();
   so.err = sqrt(e2 / (double)m);
   so.good = fin;
   return so;
@@ -627,26 +699,27 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Adaptive integration of the cell whose state sits in y (shared memory) over [0, dt].
+template <class Gp>
 __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, const CellLayout& L, double p, double dt,
                                                double& h_io, int& nsub, int& nacc, int& status, const IntOpts& o,
-                                               int lane, int cell) {
+                                               const Gp& g, int cell) {
   double* y = s + L.y;
   const int m = M.m;
   // input check
   bool ok = isfinite(p) && p > 0.0 && isfinite(dt) && dt >= 0.0 && isfinite(y[0]) && y[0] > 0.0;
   double sig = 0.0;
-  for (int k = lane; k < M.n; k += kWarp) {
+  for (int k = g.lane; k < M.n; k += g.size) {
     const double yk = y[1 + k];
     ok = ok && isfinite(yk);
     sig = fma(yk, __ldg(M.sp + (size_t)k * SP_STRIDE), sig);
   }
-  sig = warp_sum(sig);
-  ok = __all_sync(0xffffffffu, ok) && sig > 0.0;
+  sig = gsum(g, sig);
+  ok = gall(g, ok) && sig > 0.0;
   nsub = 0;
   nacc = 0;
   if (!ok) {
     status = CHEM_CELL_BADINPUT;
-    if (o.rec_h && lane == 0) o.rec_n[cell] = -1;
+    if (o.rec_h && g.lane == 0) o.rec_n[cell] = -1;
     return;
   }
   double h = (h_io > 0.0 && isfinite(h_io)) ? h_io : o.h_init;
@@ -655,12 +728,11 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
   bool rejected_last = false, needJ = true;
   int nonfinite = 0, ns = 0, na = 0, st = CHEM_CELL_OK;
   if (o.rec_h)
-    for (int i = lane; i < m; i += kWarp) o.rec_ck[(size_t)i * o.N + cell] = y[i];
+    for (int i = g.lane; i < m; i += g.size) o.rec_ck[(size_t)i * o.N + cell] = y[i];
   while (t < dt) {
     if (ns >= o.max_substeps) { st = CHEM_CELL_MAXSTEPS; break; }
     if (o.deadline_ns) {
-      unsigned long long now = lane == 0 ? global_ns() : 0ull;
-      now = __shfl_sync(0xffffffffu, now, 0);
+      const unsigned long long now = (unsigned long long)gbcast(g, g.lane == 0 ? (long long)global_ns() : 0ll);
       if (now > o.deadline_ns) { st = CHEM_CELL_TIMEOUT; break; }
     }
     const bool last = (t + h >= dt * (1.0 - 1e-14));
@@ -668,11 +740,11 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
     if (hu < o.h_min) { st = CHEM_CELL_HMIN; break; }
     ++ns;
     if (needJ) {
-      eval_jac<double>(M, s, L, y, p, lane);
+      eval_jac<double>(M, s, L, y, p, g);
       needJ = false;
     }
-    const StepOut so = ros_attempt(M, s, L, p, hu, o.rtol, o.atol, lane);
-    if (o.trace && lane == 0 && ns <= o.trace_cap)
+    const StepOut so = ros_attempt(M, s, L, p, hu, o.rtol, o.atol, g);
+    if (o.trace && g.lane == 0 && ns <= o.trace_cap)
       o.trace[(size_t)(ns - 1) * o.N + cell] = (so.good && isfinite(so.err) && so.err <= 1.0) ? hu : -hu;
     if (!so.good || !isfinite(so.err)) {
       if (++nonfinite >= o.max_nonfinite) { st = CHEM_CELL_NONFINITE; break; }
@@ -686,12 +758,12 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       t = last ? dt : t + hu;
       ++na;
       const double* yt = s + L.ytmp;
-      for (int i = lane; i < m; i += kWarp) y[i] = yt[i];
-      __syncwarp();
+      for (int i = g.lane; i < m; i += g.size) y[i] = yt[i];
+      g.sync();
       if (o.rec_h && na <= o.rec_cap) {
-        if (lane == 0) o.rec_h[(size_t)(na - 1) * o.N + cell] = hu;
+        if (g.lane == 0) o.rec_h[(size_t)(na - 1) * o.N + cell] = hu;
         if (na % o.rec_K == 0)
-          for (int i = lane; i < m; i += kWarp) o.rec_ck[((size_t)(na / o.rec_K) * m + i) * o.N + cell] = y[i];
+          for (int i = g.lane; i < m; i += g.size) o.rec_ck[((size_t)(na / o.rec_K) * m + i) * o.N + cell] = y[i];
       }
       h = hu * fmin(rejected_last ? 1.0 : 6.0, fac);
       rejected_last = false;
@@ -701,8 +773,8 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       rejected_last = true;
     }
   }
-  if (o.trace && lane == 0 && ns < o.trace_cap) o.trace[(size_t)ns * o.N + cell] = 0.0;
-  if (o.rec_h && lane == 0) o.rec_n[cell] = (na <= o.rec_cap && st == CHEM_CELL_OK) ? na : -1;
+  if (o.trace && g.lane == 0 && ns < o.trace_cap) o.trace[(size_t)ns * o.N + cell] = 0.0;
+  if (o.rec_h && g.lane == 0) o.rec_n[cell] = (na <= o.rec_cap && st == CHEM_CELL_OK) ? na : -1;
   h_io = h;
   nsub = ns;
   nacc = na;

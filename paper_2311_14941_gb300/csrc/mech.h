@@ -11,6 +11,7 @@ namespace chemgb {
 constexpr double kRu = 8.314462618;   // J/(mol K)
 constexpr double kP0 = 101325.0;      // Pa, standard state of Kc
 constexpr int kWarp = 32;
+constexpr int kMaxWarpsPerCell = 2;   // a cell is integrated by one warp or by two
 
 // ---- species table: SP_STRIDE doubles per species
 //   [0] 1/W  [1] W  [2] T_mid  [3] unused
@@ -35,8 +36,8 @@ constexpr int RX_D = 12;
 //   [12] efficiency count  [13] derivative-slot offset  [14] derivative-slot count  [15] unused
 constexpr int RX_I = 16;
 
-// ---- warp programs
-// Gather ("flattened segmented reduction"): step s, lane l executes op[s*32 + l]:
+// ---- warp programs, compiled for a group of `width` lanes (one warp per cell: 32, two: 64)
+// Gather ("flattened segmented reduction"): step s, lane l executes op[s*width + l]:
 //   acc = fma(value(a, b), acc); if dst != NONE: out[dst] = acc, acc = 0.
 // dst >= PARTIAL_BIT selects the partial-sum buffer; a combine list then adds partials into outputs.
 struct GatherOp {
@@ -45,7 +46,7 @@ struct GatherOp {
 constexpr uint16_t DST_NONE = 0xFFFF;
 constexpr uint16_t PARTIAL_BIT = 0x8000;
 
-// Elimination / solve program: step s has one kind; lane l executes op[s*32 + l] (t == OP_IDLE: idle).
+// Elimination / solve program: step s has one kind; lane l executes op[s*width + l] (t == OP_IDLE: idle).
 //   LU:    K_RECIP  dinv[t] = 1 / LU[a]      K_SCALE  LU[t] *= dinv[a]     K_UPDATE LU[t] -= LU[a] * LU[b]
 //   solve: K_SCALE  x[t] *= dinv[a]          K_UPDATE x[t] -= LU[a] * x[b]
 // Every op of a step, idle ones included, carries the step's kind.
@@ -69,6 +70,7 @@ constexpr int kMaxJPass = 8;
 enum : int { JP_RB = 0, JP_RE = 1, JP_SB = 2, JP_CNT = 3 };   // first/end reaction, first slot, reactions
 
 struct MechView {
+  int width;                 // lanes of the programs below: 32 x warps per cell
   int n, R, m;
   int n_troe, n_tb;          // reactions [0, n_troe) Troe, [n_troe, n_troe + n_tb) third-body
   int nY;                    // Y-block entries of S (row-major by species, diagonal included)
@@ -96,14 +98,11 @@ struct MechView {
   Gather g_col;              // species i <- sum_k h_k Dtil_ki (a = entry, b = species k)
   const int* lu_src;         // [nnz_LU] S index feeding the slot (-1: fill)
   const int* lu_diag;        // [m] LU slot of the diagonal of state index s (natural order)
-  const ElimOp* lu_ops;      // [lu_steps * 32]
-  const uint8_t* lu_kind;    // [lu_steps]
+  const ElimOp* lu_ops;      // [lu_steps * width]
   int lu_steps;
   const ElimOp* sv_ops;      // forward + backward substitution program, vector indices in state order
-  const uint8_t* sv_kind;
   int sv_steps;
   const ElimOp* svT_ops;     // transposed substitution program (A^T x = b)
-  const uint8_t* svT_kind;
   int svT_steps;
   const int* rx_order;       // [R] compiled reaction -> description index
   const int* s_out;          // [nnz_S] position of internal S entry in the CSR output order

@@ -102,10 +102,127 @@ __device__ __forceinline__ Dual sexp(Dual a) {
   const double e = fast_exp(a.v);
   return Dual(e, a.d * e);
 }
+template <int K>
+__device__ __forceinline__ DualN<K> sfma(const DualN<K>& a, const DualN<K>& b, const DualN<K>& c) {
+  DualN<K> r; r.v = fma(a.v, b.v, c.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = fma(a.v, b.d[i], fma(a.d[i], b.v, c.d[i]));
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> sexp(const DualN<K>& a) {
+  DualN<K> r; r.v = fast_exp(a.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * r.v;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> slog(const DualN<K>& a) {
+  DualN<K> r; r.v = fast_log(a.v);
+  const double ia = 1.0 / a.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * ia;
+  return r;
+}
 __device__ __forceinline__ double slog(double a) { return fast_log(a); }
 __device__ __forceinline__ Dual slog(Dual a) { return Dual(fast_log(a.v), a.d / a.v); }
+// ---- several directional derivatives at once: value and K tangents.  The discrete adjoint needs the
+// Jacobian's derivative along the four stage vectors of a step at the same point; one evaluation with
+// K = 4 tangents shares the value arithmetic (and every exp, log and division) among the four.
+template <int K>
+struct DualN {
+  double v, d[K];
+  __device__ __forceinline__ DualN() = default;
+  __device__ __forceinline__ DualN(double x) : v(x) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) d[i] = 0.0;
+  }
+};
+using Dual4 = DualN<4>;
+
+template <int K>
+__device__ __forceinline__ DualN<K> operator+(const DualN<K>& a, const DualN<K>& b) {
+  DualN<K> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator-(const DualN<K>& a, const DualN<K>& b) {
+  DualN<K> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator-(const DualN<K>& a) {
+  DualN<K> r; r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator*(const DualN<K>& a, const DualN<K>& b) {
+  DualN<K> r; r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = fma(a.v, b.d[i], a.d[i] * b.v);
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator*(const DualN<K>& a, double b) {
+  DualN<K> r; r.v = a.v * b;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator*(double a, const DualN<K>& b) { return b * a; }
+template <int K>
+__device__ __forceinline__ DualN<K> operator+(const DualN<K>& a, double b) { DualN<K> r = a; r.v += b; return r; }
+template <int K>
+__device__ __forceinline__ DualN<K> operator+(double a, const DualN<K>& b) { return b + a; }
+template <int K>
+__device__ __forceinline__ DualN<K> operator-(const DualN<K>& a, double b) { DualN<K> r = a; r.v -= b; return r; }
+template <int K>
+__device__ __forceinline__ DualN<K> operator-(double a, const DualN<K>& b) { return (-b) + a; }
+template <int K>
+__device__ __forceinline__ DualN<K> operator/(const DualN<K>& a, const DualN<K>& b) {
+  const double ib = 1.0 / b.v;
+  DualN<K> r; r.v = a.v * ib;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator/(const DualN<K>& a, double b) {
+  const double ib = 1.0 / b;
+  DualN<K> r; r.v = a.v * ib;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * ib;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> operator/(double a, const DualN<K>& b) {
+  const double ib = 1.0 / b.v;
+  DualN<K> r; r.v = a * ib;
+  const double s = -r.v * ib;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = s * b.d[i];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K>& operator+=(DualN<K>& a, const DualN<K>& b) { a = a + b; return a; }
+template <int K>
+__device__ __forceinline__ DualN<K>& operator-=(DualN<K>& a, const DualN<K>& b) { a = a - b; return a; }
+template <int K>
+__device__ __forceinline__ DualN<K>& operator*=(DualN<K>& a, const DualN<K>& b) { a = a * b; return a; }
+template <int K>
+__device__ __forceinline__ DualN<K>& operator*=(DualN<K>& a, double b) { a = a * b; return a; }
+
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(Dual a) { return a.v; }
+template <int K>
+__device__ __forceinline__ double val(const DualN<K>& a) { return a.v; }
 __device__ __forceinline__ double tangent(Dual a) { return a.d; }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -114,5 +231,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;   // identical on every lane (each butterfly stage adds the same pair of operands)
 }
 __device__ __forceinline__ Dual warp_sum(Dual a) { return Dual(warp_sum(a.v), warp_sum(a.d)); }
+template <int K>
+__device__ __forceinline__ DualN<K> warp_sum(DualN<K> a) {
+  a.v = warp_sum(a.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) a.d[i] = warp_sum(a.d[i]);
+  return a;
+}
 
 }  // namespace chemgb

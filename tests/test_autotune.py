@@ -26,12 +26,22 @@ def test_sample_without_counts_is_seeded_random_and_small_fields_are_whole():
 
 
 def test_search_space():
-    c = autotune.candidates(7)
-    assert {x["mode"] for x in c} == {0, 1}
-    assert {x["block_warps"] for x in c} == {1, 2, 4, 7}
+    c = autotune.candidates({1: 7, 2: 3})
+    assert {x["mode"] for x in c} == {0, 1} and {x["warps_per_cell"] for x in c} == {1, 2}
+    assert {x["block_cells"] for x in c if x["warps_per_cell"] == 1} == {1, 2, 4, 7}
+    assert {x["block_cells"] for x in c if x["warps_per_cell"] == 2} == {1, 2, 3}
     assert all(x["chunk"] == 1 for x in c if x["mode"] == 0)
     assert len({json.dumps(x, sort_keys=True) for x in c}) == len(c)
-    assert {x["block_warps"] for x in autotune.candidates(1)} == {1, 2, 4}
+    assert {x["block_cells"] for x in autotune.candidates({1: 1})} == {1}
+
+
+def test_block_bounds():
+    # 24.6 KB cells in 227 KB: 9 per block; two-warp cells are also capped by 15 named barriers and 1024
+    # threads
+    assert autotune.max_block_cells(24592, 232448, 1) == 9
+    assert autotune.max_block_cells(3616, 232448, 1) == 16
+    assert autotune.max_block_cells(3616, 232448, 2) == 15
+    assert autotune.max_block_cells(71048, 232448, 2) == 3
 
 
 def test_digest_depends_on_every_parameter():
@@ -45,15 +55,17 @@ def test_digest_depends_on_every_parameter():
 def test_cache_roundtrip(tmp_path, monkeypatch):
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "c.json"))
     assert autotune._load() == {}
-    autotune._store("k1", {"mode": 1, "block_warps": 2, "chunk": 1})
-    autotune._store("k2", {"mode": 0, "block_warps": 1, "chunk": 1})
+    autotune._store("k1", {"warps_per_cell": 2, "mode": 1, "block_cells": 2, "chunk": 1})
+    autotune._store("k2", {"warps_per_cell": 1, "mode": 0, "block_cells": 1, "chunk": 1})
     got = autotune._load()
-    assert got["k1"]["block_warps"] == 2 and got["k2"]["mode"] == 0
-    assert autotune.launch_options(got["k1"]) == {"mode": 1, "block_warps": 2, "chunk": 1}
+    assert got["k1"]["block_cells"] == 2 and got["k2"]["mode"] == 0
+    assert autotune.launch_options(got["k1"]) == {"warps_per_cell": 2, "mode": 1, "block_cells": 2, "chunk": 1}
 
 
 @pytest.mark.gpu
-def test_gpu_every_launch_shape_gives_identical_results_and_tune_picks_one(tmp_path, monkeypatch):
+def test_gpu_launch_shapes_agree_and_tune_picks_one(tmp_path, monkeypatch):
+    """Within one warps-per-cell choice every launch shape gives bit-identical results (a cell's arithmetic
+    does not depend on where or when it runs); the two choices agree to rounding."""
     import torch
     from paper_2311_14941_gb300 import chem
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "c.json"))
@@ -64,21 +76,31 @@ def test_gpu_every_launch_shape_gives_identical_results_and_tune_picks_one(tmp_p
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     N = F.n_cells
     ns_prev = torch.tensor(np.random.default_rng(2).integers(1, 300, N).astype(np.int32), device=dev)
-    ref = None
-    wmax = max(1, 227 * 1024 // h.info["smem_per_cell"])
-    for c in autotune.candidates(wmax):
+    space = autotune.candidates({w: h.info["max_block_cells"][w - 1] for w in (1, 2)})
+    optin = torch.cuda.get_device_properties(0).shared_memory_per_block_optin
+    assert all(h.info["max_block_cells"][w - 1] <= autotune.max_block_cells(h.info["smem_per_cell"], optin, w)
+               for w in (1, 2))
+    assert h.info["auto_warps_per_cell"] == 1 and h.info["resident_cells"][0] >= 8
+    ref = {}
+    for c in space:
         T, Y = t(F.T), t(F.Y.reshape(-1))
         hio = torch.zeros(N, dtype=torch.float64, device=dev)
         ns = ns_prev.clone()
         st = torch.zeros(N, dtype=torch.int32, device=dev)
         h.integrate(T, t(F.p), Y, t(F.dt), hio, ns, st, **c)
         out = (T.cpu().numpy(), Y.cpu().numpy(), hio.cpu().numpy(), ns.cpu().numpy(), st.cpu().numpy())
-        if ref is None:
-            ref = out
-        for a, b in zip(out, ref):
+        w = c["warps_per_cell"]
+        if w not in ref:
+            ref[w] = out
+        for a, b in zip(out, ref[w]):
             assert np.array_equal(a, b), c
+    assert np.all(ref[1][4] == 0) and np.array_equal(ref[1][4], ref[2][4])
+    big = np.abs(ref[1][1]) > 1e-12
+    assert np.allclose(ref[1][0], ref[2][0], rtol=1e-6, atol=0)
+    assert np.allclose(ref[1][1][big], ref[2][1][big], rtol=1e-5, atol=0)
     r = autotune.tune(h, t(F.T), t(F.p), t(F.Y.reshape(-1)), t(F.dt), ns_prev, sample=1024)
-    assert autotune.launch_options(r) in autotune.candidates(wmax)
-    assert len(r["table"]) == len(autotune.candidates(wmax)) and r["ms"] > 0
+    opts = autotune.launch_options(r)
+    assert opts in [dict((k, x[k]) for k in autotune.KEYS) for x in space] or opts["block_cells"] == 0
+    assert r["ms"] == min(x["ms"] for x in r["table"]) and r["ms"] > 0
     assert autotune.tune(h, t(F.T), t(F.p), t(F.Y.reshape(-1)), t(F.dt), ns_prev, sample=1024) == \
         json.loads(json.dumps(r))

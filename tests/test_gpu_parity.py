@@ -178,35 +178,40 @@ def _compare_integration(o, g, r, F, max_flip_frac):
     return len(flips)
 
 
-def test_integrate_parity_small_full_config(dev):
-    """1024 cells, 10 species / 27 reactions, p = 1 atm, T ~ U(900, 2200) K, Dirichlet Y, dt = 1e-5 s."""
+@pytest.mark.parametrize("wpc", [1, 2])
+def test_integrate_parity_small_full_config(dev, wpc):
+    """1024 cells, 10 species / 27 reactions, p = 1 atm, T ~ U(900, 2200) K, Dirichlet Y, dt = 1e-5 s;
+    one or two warps per cell."""
     m, h, o = mech("small")
     F = synth.field_uniform_random(m, 1024, seed=1)
     r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=4000)
-    g = _integrate_gpu(h, F, dev, trace_cap=4000)
+    g = _integrate_gpu(h, F, dev, trace_cap=4000, warps_per_cell=wpc)
     _compare_integration(o, g, r, F, 0.02)
     assert np.all(g["status"] == 0)
 
 
-def test_integrate_parity_methane_sized_sample(dev):
-    """128 cells of the bimodal jet field (cold, burnt and mixing-layer cells), 53/325 mechanism."""
+@pytest.mark.parametrize("wpc", [1, 2])
+def test_integrate_parity_methane_sized_sample(dev, wpc):
+    """120 cells of the bimodal jet field (cold, burnt and mixing-layer cells), 53/325 mechanism; one or
+    two warps per cell."""
     m, h, o = mech("mid")
     F = synth.field_bimodal_jet(m, 256, 256, seed=2)
     rng = np.random.default_rng(7)
     idx = np.sort(np.concatenate([rng.choice(np.where(F.kind == k)[0], 40, replace=False) for k in (0, 1, 2)]))
     S = F.subset(idx)
     r = o.integrate_batch(S.T, S.p, S.Y, S.dt, trace_cap=2000)
-    g = _integrate_gpu(h, S, dev, trace_cap=2000)
+    g = _integrate_gpu(h, S, dev, trace_cap=2000, warps_per_cell=wpc)
     _compare_integration(o, g, r, S, 0.03)
 
 
-def test_integrate_parity_large_sample(dev):
-    """16 cells of the 150/1000 mechanism with LTS-like dt in 1e-6..1e-4 s."""
+@pytest.mark.parametrize("wpc", [1, 2])
+def test_integrate_parity_large_sample(dev, wpc):
+    """16 cells of the 150/1000 mechanism with LTS-like dt in 1e-6..1e-4 s; one or two warps per cell."""
     m, h, o = mech("large")
     F = synth.field_bimodal_jet(m, 16, 16, seed=5, dt_range=(1e-6, 1e-4))
     S = F.subset(np.arange(0, 256, 16))
     r = o.integrate_batch(S.T, S.p, S.Y, S.dt, trace_cap=2000)
-    g = _integrate_gpu(h, S, dev, trace_cap=2000)
+    g = _integrate_gpu(h, S, dev, trace_cap=2000, warps_per_cell=wpc)
     _compare_integration(o, g, r, S, 0.07)
 
 

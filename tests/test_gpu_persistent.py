@@ -48,7 +48,7 @@ def test_persistent_equals_plain_bitwise(mid, dev):
     pers = _run(h, F, dev, mode=1)
     _same(plain, pers)
     # second flow step: the previous counts become the sort key
-    again = _run(h, F, dev, nsub_in=plain["nsub"], mode=1, chunk=2, block_warps=2)
+    again = _run(h, F, dev, nsub_in=plain["nsub"], mode=1, chunk=2, block_cells=2)
     _same(plain, again)
     assert len(np.unique(plain["nsub"])) > 5   # a real spread of costs was sorted
 
@@ -91,3 +91,15 @@ def test_bad_mode_rejected(mid, dev):
     F = synth.field_bimodal_jet(m, 4, 4, seed=9)
     with pytest.raises(chem.ChemError):
         _run(h, F, dev, mode=7)
+
+
+def test_two_warps_per_cell_plain_equals_persistent(mid, dev):
+    """With two warps per cell, the plain and the sorted-queue launches give bit-identical results."""
+    m, h = mid
+    F = synth.field_lts_mix(m, 1500, seed=5, dt_range=(1e-7, 1e-4))
+    plain = _run(h, F, dev, mode=0, warps_per_cell=2)
+    pers = _run(h, F, dev, mode=1, warps_per_cell=2, block_cells=3)
+    _same(plain, pers)
+    assert np.all(plain["status"] == 0)
+    one = _run(h, F, dev, mode=0, warps_per_cell=1)
+    assert np.array_equal(one["status"], plain["status"])

@@ -37,8 +37,8 @@ def _internal_S_dense(h, S_csr):
     return S_csr[s_out], dense
 
 
-def _run_elimination(prog, LU, dinv):
-    P = prog.reshape(-1, 32, 4)
+def _run_elimination(prog, LU, dinv, width=32):
+    P = prog.reshape(-1, width, 4)
     for st in P:
         kind = st[0, 0]
         live = st[st[:, 1] != 65535]
@@ -52,8 +52,8 @@ def _run_elimination(prog, LU, dinv):
             dinv[t] = 1.0 / LU[a]
 
 
-def _run_solve(prog, LU, dinv, x):
-    P = prog.reshape(-1, 32, 4)
+def _run_solve(prog, LU, dinv, x, width=32):
+    P = prog.reshape(-1, width, 4)
     for st in P:
         kind = st[0, 0]
         live = st[st[:, 1] != 65535]
@@ -65,9 +65,12 @@ def _run_solve(prog, LU, dinv, x):
             x[t] = x[t] * dinv[a]
 
 
-def test_programs_reproduce_dense_solve(compiled):
-    """I/(h gamma) - S factored and solved by the warp programs equals numpy's dense solve."""
+@pytest.mark.parametrize("wpc", [1, 2])
+def test_programs_reproduce_dense_solve(compiled, wpc):
+    """I/(h gamma) - S factored and solved by the warp programs (one or two warps per cell) equals numpy's
+    dense solve."""
     m_, h = compiled
+    width, plan_lu, plan_sv = (32, 0, 1) if wpc == 1 else (64, 8, 9)
     rng = np.random.default_rng(1)
     info = h.info
     S_csr = rng.standard_normal(info["nnz_S"])
@@ -84,19 +87,21 @@ def test_programs_reproduce_dense_solve(compiled):
             if col[sl] == p:
                 LU[sl] += gh
     dinv = np.zeros(h.m)
-    _run_elimination(h.export_plan(0), LU, dinv)
+    _run_elimination(h.export_plan(plan_lu), LU, dinv, width)
     assert sorted(perm.tolist()) == list(range(h.m)) and perm[-1] == 0      # T eliminated last
     for _ in range(3):
         bvec = rng.standard_normal(h.m)
         x = bvec.copy()
-        _run_solve(h.export_plan(1), LU, dinv, x)
+        _run_solve(h.export_plan(plan_sv), LU, dinv, x, width)
         ref = np.linalg.solve(A, bvec)
         assert np.max(np.abs(x - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-def test_transposed_program_solves_the_transpose(compiled):
+@pytest.mark.parametrize("wpc", [1, 2])
+def test_transposed_program_solves_the_transpose(compiled, wpc):
     """The transposed substitution program applied to the same factor solves A^T x = b."""
     m_, h = compiled
+    width, plan_lu, plan_t = (32, 0, 6) if wpc == 1 else (64, 8, 10)
     rng = np.random.default_rng(2)
     S_csr = rng.standard_normal(h.info["nnz_S"])
     S_int, S_dense = _internal_S_dense(h, S_csr)
@@ -111,11 +116,11 @@ def test_transposed_program_solves_the_transpose(compiled):
             if col[sl] == p:
                 LU[sl] += gh
     dinv = np.zeros(h.m)
-    _run_elimination(h.export_plan(0), LU, dinv)
+    _run_elimination(h.export_plan(plan_lu), LU, dinv, width)
     for _ in range(3):
         bvec = rng.standard_normal(h.m)
         x = bvec.copy()
-        _run_solve(h.export_plan(6), LU, dinv, x)
+        _run_solve(h.export_plan(plan_t), LU, dinv, x, width)
         ref = np.linalg.solve(A.T, bvec)
         assert np.max(np.abs(x - ref)) <= 1e-12 * np.max(np.abs(ref))
 

@@ -1,5 +1,5 @@
-// scalar.cuh -- scalar types of the device code: double, and a forward-mode dual number (value plus one
-// directional derivative) used by the discrete adjoint for exact Hessian-vector and mixed
+// scalar.cuh -- scalar types of the device code: double, and forward-mode dual numbers (value plus one
+// or K directional derivatives) used by the discrete adjoint for exact Hessian-vector and mixed
 // parameter-state terms.  The helpers below reduce to the plain double operations for double, so the
 // forward integrator's arithmetic is unchanged by the templating.
 #pragma once
@@ -62,70 +62,6 @@ __device__ __forceinline__ Dual& operator-=(Dual& a, Dual b) { a = a - b; return
 __device__ __forceinline__ Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
 __device__ __forceinline__ Dual& operator*=(Dual& a, double b) { a = a * b; return a; }
 
-// fused multiply-add, exp, log, value part, and the warp-level all-reduce sum
-__device__ __forceinline__ double sfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ Dual sfma(Dual a, Dual b, Dual c) {
-  return Dual(fma(a.v, b.v, c.v), fma(a.v, b.d, fma(a.d, b.v, c.d)));
-}
-// ln x by table-driven reduction (Tang, ACM TOMS 16(4), 1990), in a variant with 256 table entries:
-//   x = 2^k y, y in [1, 2); j = top 8 bits of y's fraction; u = y c_j - 1 with c_j the rounded reciprocal
-//   of the centre of y's interval (1 and 2 for the first and last intervals), |u| <= 2^-8;
-//   ln x = (k ln2_lead + lnF_lead_j) + (k ln2_trail + lnF_trail_j + log1p(u)), where lnF_j = -ln c_j
-//   (so the rounding of c_j needs no correction) and the first sum is exact (leads on the grid 2^-43);
-//   log1p(u) = u - u^2 (1/2 - u/3 + u^2/4 - u^3/5 + u^4/6 - u^5/7), truncation below 2^-59 relative.
-// Thirteen FP64 operations; error about one ulp; ln of values near 1 keeps full relative accuracy.
-// Zero, negative, subnormal, infinite and NaN arguments take the library log.
-__device__ __forceinline__ double fast_log(double x) {
-  const int hx = __double2hiint(x);
-  if (hx < 0x00100000 || hx >= 0x7ff00000) return log(x);
-  const int k = (hx >> 20) - 1023;
-  const int j = (hx >> 12) & 0xff;
-  const double y = __hiloint2double((hx & 0x000fffff) | 0x3ff00000, __double2loint(x));
-  const double* tb = kLogTab[j];
-  const double c = __ldg(tb), lead = __ldg(tb + 1), trail = __ldg(tb + 2);
-  const double u = fma(y, c, -1.0);
-  double q = fma(u, -1.0 / 7.0, 1.0 / 6.0);
-  q = fma(u, q, -1.0 / 5.0);
-  q = fma(u, q, 1.0 / 4.0);
-  q = fma(u, q, -1.0 / 3.0);
-  q = fma(u, q, 0.5);
-  const double p = fma(-(u * u), q, u);
-  // k as a double without a conversion instruction: 2^52 + 2^31 + k from its bits, minus 2^52 + 2^31
-  const double kd = __hiloint2double(0x43300000, k ^ (int)0x80000000) - 0x1.00000800p52;
-  const double t1 = fma(kd, kLn2Lead, lead);
-  const double t2 = fma(kd, kLn2Trail, trail) + p;
-  return t1 + t2;
-}
-
-__device__ __forceinline__ double sexp(double a) { return fast_exp(a); }
-__device__ __forceinline__ Dual sexp(Dual a) {
-  const double e = fast_exp(a.v);
-  return Dual(e, a.d * e);
-}
-template <int K>
-__device__ __forceinline__ DualN<K> sfma(const DualN<K>& a, const DualN<K>& b, const DualN<K>& c) {
-  DualN<K> r; r.v = fma(a.v, b.v, c.v);
-#pragma unroll
-  for (int i = 0; i < K; ++i) r.d[i] = fma(a.v, b.d[i], fma(a.d[i], b.v, c.d[i]));
-  return r;
-}
-template <int K>
-__device__ __forceinline__ DualN<K> sexp(const DualN<K>& a) {
-  DualN<K> r; r.v = fast_exp(a.v);
-#pragma unroll
-  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * r.v;
-  return r;
-}
-template <int K>
-__device__ __forceinline__ DualN<K> slog(const DualN<K>& a) {
-  DualN<K> r; r.v = fast_log(a.v);
-  const double ia = 1.0 / a.v;
-#pragma unroll
-  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * ia;
-  return r;
-}
-__device__ __forceinline__ double slog(double a) { return fast_log(a); }
-__device__ __forceinline__ Dual slog(Dual a) { return Dual(fast_log(a.v), a.d / a.v); }
 // ---- several directional derivatives at once: value and K tangents.  The discrete adjoint needs the
 // Jacobian's derivative along the four stage vectors of a step at the same point; one evaluation with
 // K = 4 tangents shares the value arithmetic (and every exp, log and division) among the four.
@@ -219,6 +155,70 @@ __device__ __forceinline__ DualN<K>& operator*=(DualN<K>& a, const DualN<K>& b) 
 template <int K>
 __device__ __forceinline__ DualN<K>& operator*=(DualN<K>& a, double b) { a = a * b; return a; }
 
+// fused multiply-add, exp, log, value part, and the warp-level all-reduce sum
+__device__ __forceinline__ double sfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ Dual sfma(Dual a, Dual b, Dual c) {
+  return Dual(fma(a.v, b.v, c.v), fma(a.v, b.d, fma(a.d, b.v, c.d)));
+}
+// ln x by table-driven reduction (Tang, ACM TOMS 16(4), 1990), in a variant with 256 table entries:
+//   x = 2^k y, y in [1, 2); j = top 8 bits of y's fraction; u = y c_j - 1 with c_j the rounded reciprocal
+//   of the centre of y's interval (1 and 2 for the first and last intervals), |u| <= 2^-8;
+//   ln x = (k ln2_lead + lnF_lead_j) + (k ln2_trail + lnF_trail_j + log1p(u)), where lnF_j = -ln c_j
+//   (so the rounding of c_j needs no correction) and the first sum is exact (leads on the grid 2^-43);
+//   log1p(u) = u - u^2 (1/2 - u/3 + u^2/4 - u^3/5 + u^4/6 - u^5/7), truncation below 2^-59 relative.
+// Thirteen FP64 operations; error about one ulp; ln of values near 1 keeps full relative accuracy.
+// Zero, negative, subnormal, infinite and NaN arguments take the library log.
+__device__ __forceinline__ double fast_log(double x) {
+  const int hx = __double2hiint(x);
+  if (hx < 0x00100000 || hx >= 0x7ff00000) return log(x);
+  const int k = (hx >> 20) - 1023;
+  const int j = (hx >> 12) & 0xff;
+  const double y = __hiloint2double((hx & 0x000fffff) | 0x3ff00000, __double2loint(x));
+  const double* tb = kLogTab[j];
+  const double c = __ldg(tb), lead = __ldg(tb + 1), trail = __ldg(tb + 2);
+  const double u = fma(y, c, -1.0);
+  double q = fma(u, -1.0 / 7.0, 1.0 / 6.0);
+  q = fma(u, q, -1.0 / 5.0);
+  q = fma(u, q, 1.0 / 4.0);
+  q = fma(u, q, -1.0 / 3.0);
+  q = fma(u, q, 0.5);
+  const double p = fma(-(u * u), q, u);
+  // k as a double without a conversion instruction: 2^52 + 2^31 + k from its bits, minus 2^52 + 2^31
+  const double kd = __hiloint2double(0x43300000, k ^ (int)0x80000000) - 0x1.00000800p52;
+  const double t1 = fma(kd, kLn2Lead, lead);
+  const double t2 = fma(kd, kLn2Trail, trail) + p;
+  return t1 + t2;
+}
+
+__device__ __forceinline__ double sexp(double a) { return fast_exp(a); }
+__device__ __forceinline__ Dual sexp(Dual a) {
+  const double e = fast_exp(a.v);
+  return Dual(e, a.d * e);
+}
+template <int K>
+__device__ __forceinline__ DualN<K> sfma(const DualN<K>& a, const DualN<K>& b, const DualN<K>& c) {
+  DualN<K> r; r.v = fma(a.v, b.v, c.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = fma(a.v, b.d[i], fma(a.d[i], b.v, c.d[i]));
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> sexp(const DualN<K>& a) {
+  DualN<K> r; r.v = fast_exp(a.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * r.v;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ DualN<K> slog(const DualN<K>& a) {
+  DualN<K> r; r.v = fast_log(a.v);
+  const double ia = 1.0 / a.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * ia;
+  return r;
+}
+__device__ __forceinline__ double slog(double a) { return fast_log(a); }
+__device__ __forceinline__ Dual slog(Dual a) { return Dual(fast_log(a.v), a.d / a.v); }
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(Dual a) { return a.v; }
 template <int K>

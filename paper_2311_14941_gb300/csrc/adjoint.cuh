@@ -109,10 +109,97 @@ __device__ __forceinline__ void vset(double* dst, const double* src, int m, cons
   g.sync();
 }
 
+// sum_st (d_st J)^T W_st into out (m), J = S + u v^T at the dual point (d_st: tangent st):
+//   d(J^T w) = dS^T w + dv (u . w) + v (du . w).
+__device__ __forceinline__ void vjp_tangents(const MechView& M, const Dual4* S, const Dual4* u, const Dual4* v,
+                                             const double* const* Ws, double* out, double* part, const Grp1& g) {
+  run_gather(M.g_col, out + 1, part, [&](int a, int b) {
+    double acc = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) acc = fma(S[a].d[st], Ws[st][1 + b], acc);
+    return acc;
+  }, g);
+  double t0 = 0.0, uw[4] = {0.0, 0.0, 0.0, 0.0}, duw[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = g.lane; k < M.n; k += g.size)
+#pragma unroll
+    for (int st = 0; st < 4; ++st) t0 = fma(S[M.nY + k].d[st], Ws[st][1 + k], t0);
+  for (int i = g.lane; i < M.m; i += g.size)
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      uw[st] = fma(u[i].v, Ws[st][i], uw[st]);
+      duw[st] = fma(u[i].d[st], Ws[st][i], duw[st]);
+    }
+  t0 = gsum(g, t0);
+#pragma unroll
+  for (int st = 0; st < 4; ++st) { uw[st] = gsum(g, uw[st]); duw[st] = gsum(g, duw[st]); }
+  for (int c = g.lane; c < M.m; c += g.size) {
+    double acc = (c == 0) ? t0 : out[c];
+    const Dual4& vc = v[c];
+    const Dual4& sT = S[M.nY + M.n + c];
+#pragma unroll
+    for (int st = 0; st < 4; ++st)
+      acc += fma(vc.d[st], uw[st], fma(vc.v, duw[st], sT.d[st] * Ws[st][0]));
+    out[c] = acc;
+  }
+  g.sync();
+}
+
+__device__ __forceinline__ Dual tangent_of(const Dual4& x, int st) { return Dual(x.v, x.d[st]); }
+
+// The mixed parameter terms of the four stages: GA_r, GE_r += sum_st d_st [q_r E_r(W_st)] with the
+// parameter contraction of theta_terms evaluated in the dual number of tangent st.
+__device__ __forceinline__ void theta_tangents(const MechView& M, const Dual4* s, const CellLayout& L,
+                                               const ScalT<Dual4>& sc, const double* const* Ws, Dual* a,
+                                               double* GA, double* GE, const Grp1& g) {
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const double* w = Ws[st];
+    const Dual T = tangent_of(sc.T, st), rho = tangent_of(sc.rho, st), cp = tangent_of(sc.cp, st);
+    const Dual irho = tangent_of(sc.irho, st);
+    const Dual c1 = (w[0] * kRu) * T / (rho * cp);
+    for (int k = g.lane; k < M.n; k += g.size)
+      a[k] = sfma(Dual(__ldg(M.sp + (size_t)k * SP_STRIDE + 1) * w[1 + k]), irho, -(c1 * tangent_of(s[L.hRT + k], st)));
+    g.sync();
+    const Dual iRT = 1.0 / (kRu * T);
+    for (int r = g.lane; r < M.R; r += g.size) {
+      const int* I = M.rxi + (size_t)r * RX_I;
+      const int nro = __ldg(I + 2), npo = __ldg(I + 3);
+      Dual E = Dual(0.0);
+      for (int i = 0; i < npo; ++i) E += a[__ldg(I + 7 + i)];
+      for (int i = 0; i < nro; ++i) E -= a[__ldg(I + 4 + i)];
+      const Dual qE = tangent_of(s[L.q + r], st) * E;
+      GA[r] += qE.d;
+      GE[r] += (-(qE * iRT)).d;
+    }
+    g.sync();
+  }
+}
+
+// All second-order terms of one step: the Jacobian at y differentiated along U1..U4 at once, then the
+// state part into LAM and the parameter part into GA, GE.  tmp: m doubles of scratch.
+__device__ __forceinline__ void second_order_terms(const MechView& M, Dual4* dw, const CellLayout& Ld,
+                                                   const double* y, double p, const double* const* Us,
+                                                   const double* const* Ws, double* LAM, double* tmp, double* GA,
+                                                   double* GE, const Grp1& g) {
+  Dual4* yd = dw + Ld.y;
+  for (int i = g.lane; i < M.m; i += g.size) {
+    Dual4 x(y[i]);
+#pragma unroll
+    for (int st = 0; st < 4; ++st) x.d[st] = Us[st][i];
+    yd[i] = x;
+  }
+  g.sync();
+  const ScalT<Dual4> scd = eval_jac<Dual4>(M, dw, Ld, yd, p, g);
+  vjp_tangents(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws, tmp, reinterpret_cast<double*>(dw + Ld.part), g);
+  for (int i = g.lane; i < M.m; i += g.size) LAM[i] += tmp[i];
+  g.sync();
+  theta_tangents(M, dw, Ld, scd, Ws, reinterpret_cast<Dual*>(dw + Ld.z), GA, GE, g);
+}
+
 // One adjoint step at state y (a row of the segment) with step h.  lambda (A.LAM) is updated in place,
 // the parameter gradients accumulate into GA, GE.  Returns false if the factor is singular (cannot
 // happen for a step the forward pass accepted).
-__device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
+__device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const AdjLayout& A, Dual4* dw,
                                              const CellLayout& Ld, const double* y, double p, double h,
                                              double* GA, double* GE, const Grp1& g) {
   const CellLayout& L = A.L;
@@ -219,25 +306,16 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
     ScalT<double> sc = eval_f<double>(M, s, L, s + L.y, p, s + L.f0, g);
     theta_terms<double>(M, s, L, sc, WS, s + A.A, GA, GE, g);
   }
-  // ---- Hessian and mixed parameter terms: derivative of J(y) along U_i, contracted with w_i
+  // ---- Hessian and mixed parameter terms: derivative of J(y) along U_i, contracted with w_i, for the
+  //      four stages in one evaluation of the Jacobian with four tangents
   const double* Us[4] = {U1, U2, U3, U4};
   const double* Ws[4] = {W1, W2, W3, W4};
-  for (int st = 0; st < 4; ++st) {
-    Dual* yd = dw + Ld.y;
-    for (int i = g.lane; i < m; i += g.size) yd[i] = Dual(y[i], Us[st][i]);
-    g.sync();
-    ScalT<Dual> scd = eval_jac<Dual>(M, dw, Ld, yd, p, g);
-    Dual* Gd = dw + Ld.x;
-    vjp<Dual>(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws[st], Gd, dw + Ld.part, g);
-    for (int i = g.lane; i < m; i += g.size) LAM[i] += Gd[i].d;
-    g.sync();
-    theta_terms<Dual>(M, dw, Ld, scd, Ws[st], dw + Ld.z, GA, GE, g);
-  }
+  second_order_terms(M, dw, Ld, y, p, Us, Ws, LAM, G, GA, GE, g);
   return true;
 }
 
 // Reverse pass of one cell from its tape.  Returns false on a singular factor.
-__device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const AdjLayout& A, Dual* dw,
+__device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const AdjLayout& A, Dual4* dw,
                                              const CellLayout& Ld, double p, int n_acc, const double* rec_h,
                                              const double* rec_ck, int K, int N, int cell, const Grp1& g,
                                              const IntOpts& o, double* seg, double* GA, double* GE) {

@@ -346,12 +346,12 @@ __global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const d
                           const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
                           const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
                           double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head,
-                          const int* __restrict__ perm, Dual* dual_ws, double* warp_ws, IntOpts o) {
+                          const int* __restrict__ perm, Dual4* dual_ws, double* warp_ws, IntOpts o) {
   extern __shared__ double smem[];
   const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const int gw = blockIdx.x * wpb + w;
   double* s = smem + (size_t)w * A.total;
-  Dual* dw = dual_ws + (size_t)gw * Ld.total;
+  Dual4* dw = dual_ws + (size_t)gw * Ld.total;
   const int m = M.m;
   double* seg = warp_ws + (size_t)gw * ((size_t)K * m + 2 * (size_t)M.R);
   double* GA = seg + (size_t)K * m;
@@ -894,7 +894,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   const size_t b_hio = align_up((size_t)N * 8, 256);
   const size_t b_ns = align_up((size_t)N * 4, 256);
   const size_t b_gc = grad_cell ? 0 : align_up((size_t)2 * hm.R * N * 8, 256);
-  const size_t b_dw = align_up((size_t)grid * h->L.total * sizeof(Dual), 256);
+  const size_t b_dw = align_up((size_t)grid * h->L.total * sizeof(Dual4), 256);
   const size_t b_ww = align_up((size_t)grid * ((size_t)K * m + 2 * (size_t)hm.R) * 8, 256);
   const size_t need = b_head + b_rh + b_ck + b_rn + b_hio + b_ns + b_gc + b_dw + b_ww;
   if (need > h->adj_scratch_bytes) {
@@ -916,7 +916,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   int* nsub = (int*)q; q += b_ns;
   double* gcell = grad_cell;
   if (!gcell) { gcell = (double*)q; q += b_gc; }
-  Dual* dws = (Dual*)q; q += b_dw;
+  Dual4* dws = (Dual4*)q; q += b_dw;
   double* wws = (double*)q;
   cudaStream_t strm = (cudaStream_t)stream;
   // forward pass with the tape

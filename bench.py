@@ -267,7 +267,10 @@ def main():
     ap.add_argument("--no-other-mode", action="store_true", help="time only --mode")
     ap.add_argument("--cells", type=int, default=0, help="integrate only this many seeded-random cells (profiling)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint seconds-per-gradient measurement")
+    ap.add_argument("--rtol", type=float, default=1e-6, help="relative tolerance (the headline metric is at 1e-6)")
     args = ap.parse_args()
+    global RTOL
+    RTOL = args.rtol
     if args.impl == "reference":
         return run_reference(args)
 

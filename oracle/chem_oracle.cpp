@@ -408,27 +408,50 @@ template <class S> void lu_solve(int m, const S* LU, const int* piv, S* b) {
   }
 }
 
-/* ---------------------------------------------------------------- RODAS3 (Sandu et al. 1997) */
+/* ---------------------------------------------------------------- Rosenbrock methods (k-form)
+   (I - h gamma J) k_i = h f(y + sum_j alpha_ij k_j) + h J sum_j gamma_ij k_j,
+   y_new = y + sum_i b_i k_i, error = sum_i (b_i - bhat_i) k_i; the controller's exponent is
+   -1/err_order (the order of the embedded pair plus one). */
 struct Tableau {
   int s;
   double gamma;
   double a[4][4];   // alpha_ij, j < i
   double g[4][4];   // gamma_ij, j < i
   double b[4], bhat[4];
+  int err_order;
 };
+
+/* RODAS3 (Sandu et al., Atmos. Environ. 31, 1997): 4 stages, order 3, embedded order 2, L-stable. */
 
 const Tableau kRodas3 = {
     4, 0.5,
     {{0, 0, 0, 0}, {0, 0, 0, 0}, {1.0, 0, 0, 0}, {3.0 / 4.0, -1.0 / 4.0, 1.0 / 2.0, 0}},
     {{0, 0, 0, 0}, {1.0, 0, 0, 0}, {-1.0 / 4.0, -1.0 / 4.0, 0, 0}, {1.0 / 12.0, 1.0 / 12.0, -2.0 / 3.0, 0}},
     {5.0 / 6.0, -1.0 / 6.0, -1.0 / 6.0, 1.0 / 2.0},
-    {3.0 / 4.0, -1.0 / 4.0, 1.0 / 2.0, 0.0}};
+    {3.0 / 4.0, -1.0 / 4.0, 1.0 / 2.0, 0.0},
+    3};
+
+/* ROS2 (Verwer, Spee, Blom and Hundsdorfer, SIAM J. Sci. Comput. 20, 1999): 2 stages, order 2,
+   L-stable with gamma = 1 + 1/sqrt(2); its published form (I - gamma h J) k1 = f(y),
+   (I - gamma h J) k2 = f(y + h k1) - 2 k1, y_new = y + h (3 k1 + k2)/2, with the embedded first-order
+   solution y + h k1, is in this k-form (k = h k_published): alpha_21 = 1, gamma_21 = -2 gamma,
+   b = (1/2, 1/2), bhat = (1, 0). */
+const double kRos2Gamma = 0x1.b504f333f9de6p+0;   // 1 + 1/sqrt(2) rounded to double
+const Tableau kRos2 = {
+    2, kRos2Gamma,
+    {{0, 0, 0, 0}, {1.0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}},
+    {{0, 0, 0, 0}, {-2.0 * kRos2Gamma, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}},
+    {0.5, 0.5, 0.0, 0.0},
+    {1.0, 0.0, 0.0, 0.0},
+    2};
+
+const Tableau& method_tableau(int method) { return method == 1 ? kRos2 : kRodas3; }
 
 /* One Rosenbrock step of size h from y.  Returns false if the iteration matrix is singular. */
 template <class S>
-bool ros_step(const OMech& m, double p, const Perturb<S>& pt, const S* y, double h, S* ynew, S* yerr, Eval<S>& ev) {
+bool ros_step(const OMech& m, double p, const Perturb<S>& pt, const S* y, double h, S* ynew, S* yerr, Eval<S>& ev,
+              const Tableau& tb = kRodas3) {
   const int mm = m.n + 1;
-  const Tableau& tb = kRodas3;
   std::vector<S> J((size_t)mm * mm), A((size_t)mm * mm);
   std::vector<int> piv(mm);
   jacobian(m, p, pt, y, J.data(), nullptr, ev);
@@ -470,7 +493,8 @@ struct Controls {
 
 /* Adaptive integration of one cell over [0, dt].  y (m values) is overwritten with the result. */
 int integrate_cell(const OMech& m, double p, double* y, double dt, const Controls& cc, double h_in, double* h_out,
-                   int* nsub, int* nacc, std::vector<double>* tr_h, std::vector<int>* tr_acc) {
+                   int* nsub, int* nacc, std::vector<double>* tr_h, std::vector<int>* tr_acc,
+                   const Tableau& tb = kRodas3) {
   const int mm = m.n + 1;
   *nsub = 0; *nacc = 0;
   bool ok = finite_(y[0]) && y[0] > 0.0 && finite_(p) && p > 0.0 && finite_(dt) && dt >= 0.0;
@@ -491,7 +515,7 @@ int integrate_cell(const OMech& m, double p, double* y, double dt, const Control
     const double hu = last ? dt - t : h;
     if (hu < cc.h_min) { *h_out = h; return ST_HMIN; }
     ++*nsub;
-    bool good = ros_step(m, p, pt, y, hu, ynew.data(), yerr.data(), ev);
+    bool good = ros_step(m, p, pt, y, hu, ynew.data(), yerr.data(), ev, tb);
     double err = 0.0;
     if (good) {
       double s2 = 0.0;
@@ -510,7 +534,7 @@ int integrate_cell(const OMech& m, double p, double* y, double dt, const Control
       continue;
     }
     nonfinite = 0;
-    const double fac = std::max(cc.fac_min, cc.safety * std::pow(err, -1.0 / 3.0));
+    const double fac = std::max(cc.fac_min, cc.safety * std::pow(err, -1.0 / tb.err_order));
     if (err <= 1.0) {
       if (tr_h) { tr_h->push_back(hu); tr_acc->push_back(1); }
       ++*nacc;
@@ -530,12 +554,13 @@ int integrate_cell(const OMech& m, double p, double* y, double dt, const Control
 
 /* Replay: apply the given accepted step sizes, without error control. */
 template <class S>
-bool replay_cell(const OMech& m, double p, const Perturb<S>& pt, S* y, const double* hs, int nh) {
+bool replay_cell(const OMech& m, double p, const Perturb<S>& pt, S* y, const double* hs, int nh,
+                 const Tableau& tb = kRodas3) {
   const int mm = m.n + 1;
   Eval<S> ev;
   std::vector<S> ynew(mm), yerr(mm);
   for (int s = 0; s < nh; ++s) {
-    if (!ros_step(m, p, pt, y, hs[s], ynew.data(), yerr.data(), ev)) return false;
+    if (!ros_step(m, p, pt, y, hs[s], ynew.data(), yerr.data(), ev, tb)) return false;
     for (int l = 0; l < mm; ++l) y[l] = ynew[l];
   }
   return true;
@@ -615,31 +640,33 @@ int oracle_rhs_param_cs(const OMech* m, double p, const double* y, int kind, int
   return 0;
 }
 
-/* The method's coefficients: out[0] = s, out[1] = gamma, then alpha[4][4], gamma_ij[4][4], b[4], bhat[4]. */
-int oracle_tableau(double* out) {
-  const Tableau& t = kRodas3;
-  out[0] = t.s; out[1] = t.gamma;
+/* A method's coefficients (method 0 RODAS3, 1 ROS2): out[0] = s, out[1] = gamma, then alpha[4][4],
+   gamma_ij[4][4], b[4], bhat[4], out[42] = err_order. */
+int oracle_tableau(int method, double* out) {
+  const Tableau& t = method_tableau(method);
+  out[0] = t.s; out[1] = t.gamma; out[42] = t.err_order;
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) { out[2 + 4 * i + j] = t.a[i][j]; out[18 + 4 * i + j] = t.g[i][j]; }
   for (int i = 0; i < 4; ++i) { out[34 + i] = t.b[i]; out[38 + i] = t.bhat[i]; }
   return 0;
 }
 
-/* One RODAS3 step (k-form): ynew, yerr. */
-int oracle_step(const OMech* m, double p, const double* y, double h, double* ynew, double* yerr) {
+/* One Rosenbrock step (k-form; method 0 RODAS3, 1 ROS2): ynew, yerr. */
+int oracle_step(const OMech* m, double p, const double* y, double h, double* ynew, double* yerr, int method) {
   Eval<double> ev;
   Perturb<double> pt;
-  return ros_step(*m, p, pt, y, h, ynew, yerr, ev) ? 0 : 1;
+  return ros_step(*m, p, pt, y, h, ynew, yerr, ev, method_tableau(method)) ? 0 : 1;
 }
 
 /* Adaptive integration of one cell.  y[m] in/out.  Optional trace of attempted steps (h, accepted). */
 int oracle_integrate(const OMech* m, double p, double* y, double dt, double rtol, double atol, double h_in,
                      int max_steps, double* h_out, int* nsub, int* nacc, double* tr_h, int* tr_acc, int tr_cap,
-                     int* tr_len) {
+                     int* tr_len, int method) {
   Controls cc = make_controls(rtol, atol, max_steps);
   std::vector<double> th;
   std::vector<int> ta;
-  int st = integrate_cell(*m, p, y, dt, cc, h_in, h_out, nsub, nacc, tr_h ? &th : nullptr, tr_h ? &ta : nullptr);
+  int st = integrate_cell(*m, p, y, dt, cc, h_in, h_out, nsub, nacc, tr_h ? &th : nullptr, tr_h ? &ta : nullptr,
+                          method_tableau(method));
   if (tr_h) {
     int L = (int)th.size();
     *tr_len = L;
@@ -649,9 +676,9 @@ int oracle_integrate(const OMech* m, double p, double* y, double dt, double rtol
 }
 
 /* Replay a sequence of step sizes from y (in/out) without error control. */
-int oracle_replay(const OMech* m, double p, double* y, const double* hs, int nh) {
+int oracle_replay(const OMech* m, double p, double* y, const double* hs, int nh, int method) {
   Perturb<double> pt;
-  return replay_cell(*m, p, pt, y, hs, nh) ? 0 : 1;
+  return replay_cell(*m, p, pt, y, hs, nh, method_tableau(method)) ? 0 : 1;
 }
 
 /* Complex-step derivative of the replayed final state with respect to one input:
@@ -675,7 +702,8 @@ int oracle_replay_sens_cs(const OMech* m, double p, const double* y0, const doub
    of cell c at trace[i*N + c], +h accepted, -h rejected, 0 after the last.  Returns the thread count. */
 int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, double* Y, const double* dt,
                            double rtol, double atol, int max_steps, double* h_io, int* nsub, int* nacc, int* status,
-                           int nthreads, double* trace, int trace_cap) {
+                           int nthreads, double* trace, int trace_cap, int method) {
+  const Tableau& tb = method_tableau(method);
   Controls cc = make_controls(rtol, atol, max_steps);
   const int mm = m->n + 1;
   int used = 1;
@@ -697,7 +725,7 @@ int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, do
     std::vector<double> th;
     std::vector<int> ta;
     int st = integrate_cell(*m, p[c], y.data(), dt[c], cc, h_io ? h_io[c] : 0.0, &hout, &ns, &na,
-                            trace ? &th : nullptr, trace ? &ta : nullptr);
+                            trace ? &th : nullptr, trace ? &ta : nullptr, tb);
     if (trace) {
       for (int i = 0; i < trace_cap; ++i)
         trace[(size_t)i * N + c] = i < (int)th.size() ? (ta[i] ? th[i] : -th[i]) : 0.0;

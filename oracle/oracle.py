@@ -41,15 +41,15 @@ def lib():
         L.oracle_jacobian.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp]
         L.oracle_jacobian_cs.argtypes = [C.c_void_p, C.c_double, _dp, C.c_double, _dp]
         L.oracle_rhs_param_cs.argtypes = [C.c_void_p, C.c_double, _dp, C.c_int, C.c_int, C.c_double, _dp]
-        L.oracle_tableau.argtypes = [_dp]
-        L.oracle_step.argtypes = [C.c_void_p, C.c_double, _dp, C.c_double, _dp, _dp]
+        L.oracle_tableau.argtypes = [C.c_int, _dp]
+        L.oracle_step.argtypes = [C.c_void_p, C.c_double, _dp, C.c_double, _dp, _dp, C.c_int]
         L.oracle_integrate.argtypes = [C.c_void_p, C.c_double, _dp, C.c_double, C.c_double, C.c_double,
-                                       C.c_double, C.c_int, _dp, _ip, _ip, _dp, _ip, C.c_int, _ip]
-        L.oracle_replay.argtypes = [C.c_void_p, C.c_double, _dp, _dp, C.c_int]
+                                       C.c_double, C.c_int, _dp, _ip, _ip, _dp, _ip, C.c_int, _ip, C.c_int]
+        L.oracle_replay.argtypes = [C.c_void_p, C.c_double, _dp, _dp, C.c_int, C.c_int]
         L.oracle_replay_sens_cs.argtypes = [C.c_void_p, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_int,
                                             C.c_double, _dp]
         L.oracle_integrate_batch.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
-                                             C.c_int, _dp, _ip, _ip, _ip, C.c_int, _dp, C.c_int]
+                                             C.c_int, _dp, _ip, _ip, _ip, C.c_int, _dp, C.c_int, C.c_int]
         _lib = L
     return _lib
 
@@ -130,29 +130,30 @@ class Oracle:
         self.L.oracle_rhs_param_cs(self._p, p, _d(y), kind, j, eps, _d(df))
         return df
 
-    def tableau(self):
-        out = np.zeros(42)
-        self.L.oracle_tableau(_d(out))
+    def tableau(self, method=0):
+        """Coefficients of method 0 (RODAS3) or 1 (ROS2) in the k-form of the oracle's step."""
+        out = np.zeros(43)
+        self.L.oracle_tableau(method, _d(out))
         return dict(s=int(out[0]), gamma=out[1], alpha=out[2:18].reshape(4, 4), gam=out[18:34].reshape(4, 4),
-                    b=out[34:38].copy(), bhat=out[38:42].copy())
+                    b=out[34:38].copy(), bhat=out[38:42].copy(), err_order=int(out[42]))
 
-    def step(self, y, p, h):
+    def step(self, y, p, h, method=0):
         y = np.ascontiguousarray(y, dtype=np.float64)
         yn, ye = np.empty(self.m), np.empty(self.m)
-        rc = self.L.oracle_step(self._p, p, _d(y), h, _d(yn), _d(ye))
+        rc = self.L.oracle_step(self._p, p, _d(y), h, _d(yn), _d(ye), method)
         if rc:
             raise RuntimeError("singular iteration matrix")
         return yn, ye
 
     # -------------------------------------------------------------- integration
-    def integrate(self, T, p, Y, dt, rtol=1e-6, atol=1e-12, h0=0.0, max_steps=100000, trace=False):
+    def integrate(self, T, p, Y, dt, rtol=1e-6, atol=1e-12, h0=0.0, max_steps=100000, trace=False, method=0):
         y = self.state(T, Y)
         h_out = C.c_double(0.0); ns = C.c_int(0); na = C.c_int(0); tl = C.c_int(0)
         cap = 200000 if trace else 0
         th = np.empty(cap) if trace else None
         ta = np.empty(cap, dtype=np.int32) if trace else None
         st = self.L.oracle_integrate(self._p, p, _d(y), dt, rtol, atol, h0, max_steps, C.byref(h_out),
-                                     C.byref(ns), C.byref(na), _d(th), _i(ta), cap, C.byref(tl))
+                                     C.byref(ns), C.byref(na), _d(th), _i(ta), cap, C.byref(tl), method)
         out = dict(T=y[0], Y=y[1:].copy(), y=y, h=h_out.value, nsub=ns.value, nacc=na.value, status=st)
         if trace:
             L = min(tl.value, cap)
@@ -160,10 +161,10 @@ class Oracle:
             out["trace_acc"] = ta[:L].copy()
         return out
 
-    def replay(self, y0, p, hs):
+    def replay(self, y0, p, hs, method=0):
         y = np.array(y0, dtype=np.float64)
         hs = np.ascontiguousarray(hs, dtype=np.float64)
-        rc = self.L.oracle_replay(self._p, p, _d(y), _d(hs), len(hs))
+        rc = self.L.oracle_replay(self._p, p, _d(y), _d(hs), len(hs), method)
         if rc:
             raise RuntimeError("singular iteration matrix in replay")
         return y
@@ -178,7 +179,7 @@ class Oracle:
         return dy
 
     def integrate_batch(self, T, p, Y, dt, rtol=1e-6, atol=1e-12, h_io=None, max_steps=100000, nthreads=0,
-                        trace_cap=0):
+                        trace_cap=0, method=0):
         """Structure-of-arrays batch (Y[k, c]); returns a dict of new arrays and the thread count."""
         N = int(T.shape[0])
         T = np.array(T, dtype=np.float64)
@@ -189,7 +190,7 @@ class Oracle:
         ns = np.zeros(N, dtype=np.int32); na = np.zeros(N, dtype=np.int32); st = np.zeros(N, dtype=np.int32)
         tr = np.zeros((trace_cap, N)) if trace_cap > 0 else None
         used = self.L.oracle_integrate_batch(self._p, N, _d(T), _d(p), _d(Yc), _d(dt), rtol, atol, max_steps,
-                                             _d(h), _i(ns), _i(na), _i(st), nthreads, _d(tr), trace_cap)
+                                             _d(h), _i(ns), _i(na), _i(st), nthreads, _d(tr), trace_cap, method)
         out = dict(T=T, Y=Yc, h=h, nsub=ns, nacc=na, status=st, threads=used)
         if tr is not None:
             out["trace"] = tr

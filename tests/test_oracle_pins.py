@@ -59,6 +59,31 @@ def test_rodas3_order_conditions_and_L_stability(small):
     assert max(abs(R(x)) for x in -np.logspace(-3, 8, 200)) <= 1 + 1e-12
 
 
+def test_ros2_order_conditions_and_L_stability(small):
+    """ROS2 (Verwer et al. 1999): order 2 with a first-order embedded solution, gamma = 1 + 1/sqrt(2),
+    R(-inf) = 0 (L-stable); the controller uses err^(-1/2)."""
+    t = small[1].tableau(method=1)
+    s, g = t["s"], t["gamma"]
+    assert s == 2 and t["err_order"] == 2 and small[1].tableau()["err_order"] == 3
+    assert abs(g - (1 + 1 / math.sqrt(2))) < 1e-15
+    a, gm, b, bh = t["alpha"][:s, :s], t["gam"][:s, :s], t["b"][:s], t["bhat"][:s]
+    beta_m = a + gm
+    beta = beta_m.sum(axis=1)
+    assert abs(b.sum() - 1) < 1e-15
+    assert abs(b @ beta - (0.5 - g)) < 1e-15
+    # the third-order condition fails (order exactly 2)
+    assert abs(b @ a.sum(axis=1) ** 2 - 1.0 / 3.0) > 0.1
+    assert abs(bh.sum() - 1) < 1e-15 and abs(bh @ beta - (0.5 - g)) > 0.1   # embedded: order 1
+    B = beta_m + g * np.eye(s)
+
+    def R(z):
+        return 1 + z * b @ np.linalg.solve(np.eye(s) - z * B, np.ones(s))
+
+    assert abs(1 - b @ np.linalg.solve(B, np.ones(s))) < 1e-14          # R(inf) = 0
+    assert max(abs(R(1j * y)) for y in np.logspace(-3, 6, 200)) <= 1 + 1e-12
+    assert max(abs(R(x)) for x in -np.logspace(-3, 8, 200)) <= 1 + 1e-12
+
+
 # ------------------------------------------------------------------------------------ thermo
 def test_thermo_constant_cp_special_case():
     """A NASA-7 set with only a1, a6, a7 reduces to cp/R = a1, h/RT = a1 + a6/T, s/R = a1 ln T + a7."""
@@ -270,6 +295,23 @@ def test_observed_order_three():
         errs.append(abs(y[1] - math.exp(-k * dt)))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(orders - 3.0) < 0.15), orders
+
+
+def test_ros2_observed_order_two_and_decay():
+    """Fixed ROS2 steps on A -> B: the global error falls as h^2; the adaptive run meets the closed form."""
+    k, dt = 1.0, 1.0
+    o = Oracle(_AB_mech(k, rev=0))
+    y0 = np.array([1000.0, 1.0, 0.0])
+    errs = []
+    for N in (32, 64, 128, 256):
+        y = o.replay(y0, P0, np.full(N, dt / N), method=1)
+        errs.append(abs(y[1] - math.exp(-k * dt)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 2.0) < 0.1), orders
+    r = o.integrate(1000.0, P0, np.array([1.0, 0.0]), 1.0, rtol=1e-6, atol=1e-12, method=1)
+    assert r["status"] == 0 and abs(r["Y"][0] - math.exp(-1.0)) < 2e-5
+    r3 = o.integrate(1000.0, P0, np.array([1.0, 0.0]), 1.0, rtol=1e-6, atol=1e-12)
+    assert r["nsub"] > r3["nsub"]      # the second-order method needs more steps at the same tolerance
 
 
 def test_self_convergence_order_nonlinear(small):

@@ -35,11 +35,11 @@ METRIC = "reactor-steps/s, 53sp/325rxn FP64 rtol1e-6: persistent vs plain; adjoi
 RTOL, ATOL = 1e-6, 1e-12
 
 # DRAM bytes per cell of the integration kernel, from one ncu capture of 16,384 cells of the jet field
-# (dram__bytes_read.sum + dram__bytes_write.sum = 8.36 MB; the traffic scales with the cell count: the
+# (dram__bytes_read.sum + dram__bytes_write.sum = 8.29 MB; the traffic scales with the cell count: the
 # state is read once, tables are L2-resident).  Valid only for the kernel sources it was taken on: the
 # digest below is checked at run time and the traffic is reported as null after any change.
-PROFILED_TRAFFIC_PER_CELL = 8.36e6 / 16384
-PROFILED_SOURCES = "af65debda09f593f"
+PROFILED_TRAFFIC_PER_CELL = 8.292e6 / 16384
+PROFILED_SOURCES = "f0f48ab5f55d0b53"
 KERNEL_SOURCES = ["capi.cu", "compile.cpp", "device.cuh", "elementary_tables.h", "mech.h", "scalar.cuh"]
 
 
@@ -268,6 +268,8 @@ def main():
     ap.add_argument("--cells", type=int, default=0, help="integrate only this many seeded-random cells (profiling)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint seconds-per-gradient measurement")
     ap.add_argument("--rtol", type=float, default=1e-6, help="relative tolerance (the headline metric is at 1e-6)")
+    ap.add_argument("--method", default="rodas3", choices=["rodas3", "ros2"],
+                    help="Rosenbrock method of the forward integration (the headline is RODAS3)")
     args = ap.parse_args()
     global RTOL
     RTOL = args.rtol
@@ -289,8 +291,9 @@ def main():
     if args.cells:
         F = F.subset(np.sort(np.random.default_rng(5).permutation(F.n_cells)[: args.cells]))
     evolving = WORKLOADS[args.workload]["evolving"]
+    meth = 1 if args.method == "ros2" else 0
     h = chem.create(m, local)
-    oc = opcount.model(m, h.export_plan(0), h.export_plan(1))
+    oc = opcount.model(m, h.export_plan(0), h.export_plan(1), method=1 if args.method == "ros2" else 0)
     N = F.n_cells
 
     T0 = torch.tensor(F.T, device=dev)
@@ -322,7 +325,7 @@ def main():
                 T.copy_(T0)
                 Y.copy_(Y0)
                 hio.zero_()
-            h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode, naccept=nacc)
+            h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode, naccept=nacc, method=meth)
 
         for _ in range(args.warmup):
             step()
@@ -381,7 +384,7 @@ def main():
         hio.zero_()
         ns.zero_()
         for _ in range(args.warmup):
-            h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode)
+            h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode, method=meth)
         To.copy_(T)
         Yo.copy_(Y)
         torch.cuda.synchronize()
@@ -396,7 +399,7 @@ def main():
         DTs.copy_(Dh, non_blocking=True)
         if not evolving:
             hio.zero_()
-        h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode)
+        h.integrate(T, P, Y, DTs, hio, ns, st, rtol=RTOL, atol=ATOL, mode=mode, method=meth)
         To.copy_(T, non_blocking=True)
         Yo.copy_(Y, non_blocking=True)
         So.copy_(st, non_blocking=True)
@@ -422,7 +425,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(config(args.workload, args.mode), n_cells=N,
-                       warps_per_cell=int(h.info["auto_warps_per_cell"])),
+                       warps_per_cell=int(h.info["auto_warps_per_cell"]), method=args.method),
         "e2e": {"value": world * N * e2e_steps / t_e2e, "unit": "reactor-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * (4 if args.mode == "persistent" else 1),

@@ -142,6 +142,10 @@ typedef struct {
                              one-warp cells leave fewer than 6 per SM, see chem_info).  Results of the two
                              choices agree to rounding, not bit for bit (different summation orders).
                              chem_adjoint uses one warp per cell. */
+  int method;             /* Rosenbrock method: 0 RODAS3 (Sandu et al. 1997; order 3, embedded order 2,
+                             L-stable; the default and the only one chem_adjoint differentiates),
+                             1 ROS2 (Verwer et al. 1999; order 2, embedded order 1, L-stable,
+                             gamma = 1 + 1/sqrt(2)).  Other values: CHEM_EINVAL. */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,

@@ -60,7 +60,7 @@ struct chem_handle_s {
     int N, mode, cpb, chunk, wpc;
     const void* ptr[10];
     double d[5];
-    int i[3];
+    int i[4];
     bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
   } gkey{};
   cudaGraphExec_t gexec = nullptr;
@@ -752,6 +752,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   io.trace_cap = o.trace ? o.trace_cap : 0;
   io.N = N;
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
+  if (o.method != 0 && o.method != 1) return fail(CHEM_EINVAL, "method must be 0 (RODAS3) or 1 (ROS2)");
+  io.method = o.method;
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
     return fail(CHEM_EINVAL, "non-finite option");
@@ -787,7 +789,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   const void* ptrs[10] = {T, p, Y, dt, h_io, nsub, status, o.naccept, o.trace, h->scratch};
   for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
   key.d[0] = io.rtol; key.d[1] = io.atol; key.d[2] = io.h_init; key.d[3] = io.h_min; key.d[4] = o.time_budget_s;
-  key.i[0] = io.max_substeps; key.i[1] = io.max_nonfinite; key.i[2] = io.trace_cap;
+  key.i[0] = io.max_substeps; key.i[1] = io.max_nonfinite; key.i[2] = io.trace_cap; key.i[3] = io.method;
   if (!h->gexec || !(h->gkey == key)) {
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -862,6 +864,8 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   io.deadline_ns = 0;
   io.trace = nullptr;
   io.trace_cap = 0;
+  if (o.method != 0) return fail(CHEM_EINVAL, "chem_adjoint differentiates RODAS3 steps only (method 0)");
+  io.method = 0;
   io.N = N;
   const int K = o.ckpt_every > 0 ? o.ckpt_every : 16;
   const int cap = o.tape_steps > 0 ? o.tape_steps : 4096;
@@ -993,6 +997,8 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   io.trace_cap = o.trace ? o.trace_cap : 0;
   io.N = N;
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
+  if (o.method != 0 && o.method != 1) return fail(CHEM_EINVAL, "method must be 0 (RODAS3) or 1 (ROS2)");
+  io.method = o.method;
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
     return fail(CHEM_EINVAL, "non-finite option");

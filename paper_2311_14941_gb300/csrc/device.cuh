@@ -104,6 +104,14 @@ constexpr double A31 = 2.0, A41 = 2.0, A43 = 1.0;
 constexpr double C21 = 4.0, C31 = 1.0, C32 = -1.0, C41 = 1.0, C42 = -1.0, C43 = -8.0 / 3.0;
 constexpr double M1 = 2.0, M3 = 1.0, M4 = 1.0;
 
+// ROS2 (Verwer, Spee, Blom and Hundsdorfer 1999), order 2 with a first-order embedded solution,
+// L-stable with gamma = 1 + 1/sqrt(2).  Its published stages (I - gamma h J) k1 = f(y),
+// (I - gamma h J) k2 = f(y + h k1) - 2 k1 give, with U_i = gamma h k_i, the transformed form
+//   (I/(h gamma) - J) U1 = f(y),  (I/(h gamma) - J) U2 = f(y + U1/gamma) - (2/(gamma h)) U1,
+//   y_new = y + (3/(2 gamma)) U1 + (1/(2 gamma)) U2,  err = (U1 + U2)/(2 gamma).
+constexpr double RG2 = 0x1.b504f333f9de6p+0;   // 1 + 1/sqrt(2) rounded to double
+constexpr double R2_A21 = 1.0 / RG2, R2_C21 = -2.0 / RG2, R2_M1 = 1.5 / RG2, R2_M2 = 0.5 / RG2, R2_E = 0.5 / RG2;
+
 constexpr double kInvLn10 = 0.43429448190325182765;
 constexpr double kLn10 = 2.30258509299404568402;
 
@@ -676,6 +684,60 @@ __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, con
   return so;
 }
 
+// One ROS2 attempt of size h from y (f0, S, u, v already evaluated at y); ynew into ytmp.
+template <class Gp>
+__device__ __forceinline__ StepOut ros2_attempt(const MechView& M, double* s, const CellLayout& L, double p, double h,
+                                                double rtol, double atol, const Gp& g) {
+  StepOut so{false, 0.0};
+  const int m = M.m;
+  const double ih = 1.0 / h;
+  if (!lu_build_factor(M, s, L, ih * (1.0 / RG2), g)) return so;
+  double* y = s + L.y;
+  double* yt = s + L.ytmp;
+  double* f0 = s + L.f0;
+  double* U1 = s + L.U1;
+  double* U2 = s + L.U2;
+  double* z = s + L.z;
+  const double* u = s + L.u;
+  const double* v = s + L.v;
+  for (int i = g.lane; i < m; i += g.size) { z[i] = u[i]; U1[i] = f0[i]; }
+  g.sync();
+  lu_solve_impl<true>(M, s, L, z, U1, g);
+  double vz = 0.0, vx = 0.0;
+  for (int i = g.lane; i < m; i += g.size) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
+  vz = gsum(g, vz);
+  vx = gsum(g, vx);
+  const double den = 1.0 - vz;
+  if (!(den != 0.0) || !isfinite(den)) return so;
+  const double iden = 1.0 / den;
+  vx *= iden;
+  for (int i = g.lane; i < m; i += g.size) U1[i] = fma(z[i], vx, U1[i]);
+  g.sync();
+  // stage 2
+  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(R2_A21, U1[i], y[i]);
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U2, g);
+  for (int i = g.lane; i < m; i += g.size) U2[i] = fma(R2_C21 * ih, U1[i], U2[i]);
+  g.sync();
+  sm_solve(M, s, L, U2, iden, g);
+  double e2 = 0.0;
+  bool fin = true;
+  for (int i = g.lane; i < m; i += g.size) {
+    const double yn = fma(R2_M2, U2[i], fma(R2_M1, U1[i], y[i]));
+    yt[i] = yn;
+    const double sc = fma(rtol, fmax(fabs(y[i]), fabs(yn)), atol);
+    const double e = R2_E * (U1[i] + U2[i]) / sc;
+    e2 = fma(e, e, e2);
+    fin = fin && isfinite(yn);
+  }
+  e2 = gsum(g, e2);
+  fin = gall(g, fin);
+  g.sync();
+  so.err = sqrt(e2 / (double)m);
+  so.good = fin;
+  return so;
+}
+
 struct IntOpts {
   double rtol, atol, h_init, h_min;
   int max_substeps, max_nonfinite;
@@ -690,6 +752,7 @@ struct IntOpts {
   double* rec_ck;
   int* rec_n;
   int rec_cap, rec_K;
+  int method;   // 0 RODAS3, 1 ROS2
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -743,7 +806,8 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       eval_jac<double>(M, s, L, y, p, g);
       needJ = false;
     }
-    const StepOut so = ros_attempt(M, s, L, p, hu, o.rtol, o.atol, g);
+    const StepOut so = o.method == 1 ? ros2_attempt(M, s, L, p, hu, o.rtol, o.atol, g)
+                                     : ros_attempt(M, s, L, p, hu, o.rtol, o.atol, g);
     if (o.trace && g.lane == 0 && ns <= o.trace_cap)
       o.trace[(size_t)(ns - 1) * o.N + cell] = (so.good && isfinite(so.err) && so.err <= 1.0) ? hu : -hu;
     if (!so.good || !isfinite(so.err)) {
@@ -753,7 +817,8 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       continue;
     }
     nonfinite = 0;
-    const double fac = fmax(0.2, 0.9 * pow(so.err, -1.0 / 3.0));
+    // step-size factor: err^(-1/(embedded order + 1)), 3 for RODAS3, 2 for ROS2
+    const double fac = fmax(0.2, 0.9 * pow(so.err, o.method == 1 ? -0.5 : -1.0 / 3.0));
     if (so.err <= 1.0) {
       t = last ? dt : t + hu;
       ++na;

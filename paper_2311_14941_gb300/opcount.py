@@ -43,8 +43,10 @@ class OpCount:
         return np.asarray(nsub, dtype=np.float64) * self.attempt + np.asarray(nacc, dtype=np.float64) * self.jac
 
 
-def model(desc, lu_prog: np.ndarray, sv_prog: np.ndarray) -> OpCount:
-    """desc: flat mechanism (synth.MechDesc); lu_prog/sv_prog: the exported warp programs."""
+def model(desc, lu_prog: np.ndarray, sv_prog: np.ndarray, method: int = 0) -> OpCount:
+    """desc: flat mechanism (synth.MechDesc); lu_prog/sv_prog: the exported warp programs; method 0 RODAS3
+    (2 new right-hand sides, z and 4 stage solves per attempt), 1 ROS2 (1 right-hand side, z and 2 stage
+    solves)."""
     n = len(desc.W)
     R = len(desc.A)
     m = n + 1
@@ -108,7 +110,11 @@ def model(desc, lu_prog: np.ndarray, sv_prog: np.ndarray) -> OpCount:
     sp = sv_prog.reshape(-1, 32, 4)
     solve = float((sp[:, :, 1] != 65535).sum())
     sm = solve + 2 * m
-    attempt = lu + (solve + m + DIV) + 4 * sm + 2 * f_eval + m * (1 + 1 + 3 + 2 + 4 + 3) + m * (1 + DIV + 1) + SQRT + POW + 10
+    if method == 1:
+        attempt = lu + (solve + m + DIV) + 2 * sm + f_eval + m * (1 + 1 + 2 + 2) + m * (2 + DIV + 1) + SQRT + POW + 10
+    else:
+        attempt = (lu + (solve + m + DIV) + 4 * sm + 2 * f_eval + m * (1 + 1 + 3 + 2 + 4 + 3) + m * (1 + DIV + 1) +
+                   SQRT + POW + 10)
     return OpCount(float(f_eval), float(jac), float(attempt), float(lu), float(solve))
 
 

@@ -124,21 +124,21 @@ def _integrate_gpu(h, F, dev, trace_cap=0, **kw):
     return out
 
 
-def _noise_floor(o, F, c, trace_col):
+def _noise_floor(o, F, c, trace_col, method=0):
     """Sensitivity of the oracle's own result for cell c to a 1e-15 relative perturbation of its input
     (same step sequence): the floor below which two correct FP64 implementations cannot agree."""
     hs = trace_col[trace_col > 0]
     y0 = o.state(F.T[c], F.Y[:, c])
-    base = o.replay(y0, F.p[c], hs)
+    base = o.replay(y0, F.p[c], hs, method=method)
     rng = np.random.default_rng(c)
     sig = np.zeros_like(base)
     for _ in range(3):
         yp = y0 * (1.0 + 1e-15 * rng.standard_normal(y0.shape))
-        sig = np.maximum(sig, np.abs(o.replay(yp, F.p[c], hs) - base))
+        sig = np.maximum(sig, np.abs(o.replay(yp, F.p[c], hs, method=method) - base))
     return sig
 
 
-def _compare_integration(o, g, r, F, max_flip_frac):
+def _compare_integration(o, g, r, F, max_flip_frac, method=0):
     """Cells with the same accept/reject sequence: every T and Y > 1e-12 within 1e-8 relative, or within
     10x the oracle's own rounding-propagation floor where that is larger (tiny species set by fast
     balances).  Cells whose sequence differs (a decision at err ~ 1 flipped by rounding): within
@@ -163,7 +163,7 @@ def _compare_integration(o, g, r, F, max_flip_frac):
     floor_cells = 0
     worst = 0.0
     for c in np.where(same & ~np.all(ok, axis=0))[0]:
-        sig = _noise_floor(o, F, c, r["trace"][:, c])
+        sig = _noise_floor(o, F, c, r["trace"][:, c], method)
         bad = big[:, c] & (d[:, c] > np.maximum(RTOL_INT * np.abs(yr[:, c]), 10.0 * sig))
         assert not bad.any(), (c, np.where(bad)[0], d[bad, c], yr[bad, c], sig[bad])
         floor_cells += 1
@@ -178,30 +178,30 @@ def _compare_integration(o, g, r, F, max_flip_frac):
     return len(flips)
 
 
-@pytest.mark.parametrize("wpc", [1, 2])
-def test_integrate_parity_small_full_config(dev, wpc):
+@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1)])
+def test_integrate_parity_small_full_config(dev, wpc, method):
     """1024 cells, 10 species / 27 reactions, p = 1 atm, T ~ U(900, 2200) K, Dirichlet Y, dt = 1e-5 s;
-    one or two warps per cell."""
+    one or two warps per cell; RODAS3 (method 0) or ROS2 (method 1)."""
     m, h, o = mech("small")
     F = synth.field_uniform_random(m, 1024, seed=1)
-    r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=4000)
-    g = _integrate_gpu(h, F, dev, trace_cap=4000, warps_per_cell=wpc)
-    _compare_integration(o, g, r, F, 0.02)
+    r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=8000, method=method)
+    g = _integrate_gpu(h, F, dev, trace_cap=8000, warps_per_cell=wpc, method=method)
+    _compare_integration(o, g, r, F, 0.02, method)
     assert np.all(g["status"] == 0)
 
 
-@pytest.mark.parametrize("wpc", [1, 2])
-def test_integrate_parity_methane_sized_sample(dev, wpc):
+@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1)])
+def test_integrate_parity_methane_sized_sample(dev, wpc, method):
     """120 cells of the bimodal jet field (cold, burnt and mixing-layer cells), 53/325 mechanism; one or
-    two warps per cell."""
+    two warps per cell; RODAS3 or ROS2."""
     m, h, o = mech("mid")
     F = synth.field_bimodal_jet(m, 256, 256, seed=2)
     rng = np.random.default_rng(7)
     idx = np.sort(np.concatenate([rng.choice(np.where(F.kind == k)[0], 40, replace=False) for k in (0, 1, 2)]))
     S = F.subset(idx)
-    r = o.integrate_batch(S.T, S.p, S.Y, S.dt, trace_cap=2000)
-    g = _integrate_gpu(h, S, dev, trace_cap=2000, warps_per_cell=wpc)
-    _compare_integration(o, g, r, S, 0.03)
+    r = o.integrate_batch(S.T, S.p, S.Y, S.dt, trace_cap=4000, method=method)
+    g = _integrate_gpu(h, S, dev, trace_cap=4000, warps_per_cell=wpc, method=method)
+    _compare_integration(o, g, r, S, 0.03, method)
 
 
 @pytest.mark.parametrize("wpc", [1, 2])
@@ -213,6 +213,13 @@ def test_integrate_parity_large_sample(dev, wpc):
     r = o.integrate_batch(S.T, S.p, S.Y, S.dt, trace_cap=2000)
     g = _integrate_gpu(h, S, dev, trace_cap=2000, warps_per_cell=wpc)
     _compare_integration(o, g, r, S, 0.07)
+
+
+def test_integrate_rejects_unknown_method(dev):
+    m, h, o = mech("small")
+    F = synth.field_uniform_random(m, 4, seed=4)
+    with pytest.raises(chem.ChemError):
+        _integrate_gpu(h, F, dev, method=2)
 
 
 def test_integrate_edge_cases(dev):

@@ -308,8 +308,8 @@ def main():
     nacc = torch.zeros(N, dtype=torch.int32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    clocks_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                               f"bench_clocks_r{rank}.csv")
+    import tempfile
+    clocks_path = os.path.join(tempfile.gettempdir(), f"chem_bench_clocks_r{rank}_{os.getpid()}.csv")
 
     def run_mode(mode_name):
         """W untimed and K timed steps in one mode; returns per-step ms, work counts and clocks."""

@@ -155,6 +155,14 @@ typedef struct {
 chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out);
 /* device == -1 compiles on the host only (no GPU needed): chem_info, chem_jacobian_pattern and
    chem_export_plan work, compute calls return CHEM_EINVAL. */
+/* chem_create from the JSON form of the description: an object whose keys are the field names of
+   chem_mech_desc ("W", "nasa_lo", "nasa_hi", "T_mid", "comp", "reac_ptr", ..., "troe", "low"); the
+   sizes follow from "W" (species) and "A" (reactions); two-dimensional fields (nasa_lo/hi [n][7],
+   comp [n][elements], troe [R][4], low [R][3]) may be nested rows or flat arrays; "comp" may be absent
+   or null (no element-balance check); other keys are ignored.  json_text is NUL-terminated host
+   memory, read during the call only.  CHEM_EINVAL with a message for malformed JSON, missing keys or
+   inconsistent lengths; then as chem_create. */
+chem_status chem_create_from_json(const char* json_text, int device, chem_handle* out);
 chem_status chem_destroy(chem_handle h);
 
 /* Message of the last failed call on this thread ("" if none).  Valid until the next call. */

@@ -83,7 +83,8 @@ def lib():
         L.chem_adjoint.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                    C.POINTER(OptsC), _vp]
         L.chem_eval_elementary.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp]
-        for f in ("chem_eval_elementary", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
+        L.chem_create_from_json.argtypes = [C.c_char_p, C.c_int, C.POINTER(_vp)]
+        for f in ("chem_eval_elementary", "chem_create_from_json", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
                   "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc", "chem_set_params",
                   "chem_adjoint"):
             getattr(L, f).restype = C.c_int
@@ -123,9 +124,15 @@ def _stream(stream):
 class Mechanism:
     """A compiled mechanism (``chem_create``).  ``device=-1`` compiles on the host only."""
 
-    def __init__(self, desc, device: int = 0):
+    def __init__(self, desc, device: int = 0, json_text: Optional[str] = None):
         self.desc = desc
         self.device = device
+        if json_text is not None:           # chem_create_from_json: the library parses the text
+            h = _vp()
+            _check(lib().chem_create_from_json(json_text.encode(), device, C.byref(h)), "chem_create_from_json")
+            self._h = h
+            self._finish()
+            return
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
         k = dict(W=f64(desc.W), lo=f64(desc.nasa_lo).ravel(), hi=f64(desc.nasa_hi).ravel(), Tm=f64(desc.T_mid),
@@ -144,6 +151,9 @@ class Mechanism:
         h = _vp()
         _check(lib().chem_create(C.byref(self._desc), device, C.byref(h)), "chem_create")
         self._h = h
+        self._finish()
+
+    def _finish(self):
         self.info = self._info()
         self.n = self.info["n_species"]
         self.R = self.info["n_reactions"]
@@ -276,3 +286,16 @@ def eval_elementary(fn: int, x, y, stream=None):
 def create(desc, device: int = 0) -> Mechanism:
     """chem_create."""
     return Mechanism(desc, device)
+
+
+def create_from_json(json_text: str, device: int = 0) -> Mechanism:
+    """chem_create_from_json: the library parses the text.  ``desc`` is then the Python reading of the same
+    text when it carries the generator's metadata too (used by host-side helpers such as the autotuner's
+    cache key), else None."""
+    from . import synth
+    h = Mechanism(None, device, json_text=json_text)
+    try:
+        h.desc = synth.MechDesc.from_json(json_text)
+    except (KeyError, TypeError, ValueError):
+        h.desc = None
+    return h

@@ -623,6 +623,17 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   return CHEM_OK;
 }
 
+chem_status chem_create_from_json(const char* json_text, int device, chem_handle* out) {
+  g_err.clear();
+  if (!out) return fail(CHEM_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  JsonMech jm;
+  std::string err;
+  const chem_status st = parse_mech_json(json_text, jm, err);
+  if (st != CHEM_OK) return fail(st, err);
+  return chem_create(&jm.desc, device, out);   // compiles into the handle's own tables
+}
+
 chem_status chem_destroy(chem_handle h) {
   if (!h) return CHEM_OK;
   if (h->device < 0) { delete h; return CHEM_OK; }

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -645,6 +646,219 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
         if (!build_gather(gj, Pg.g_jac[p], err, Pg.width, true)) return CHEM_EUNSUPPORTED;
     }
   }
+  return CHEM_OK;
+}
+
+}  // namespace chemgb
+
+// ------------------------------------------------------------------------ mechanism description in JSON
+namespace chemgb {
+namespace {
+
+struct JVal {
+  enum Kind { NUL, BOOL, NUM, STR, ARR, OBJ } kind = NUL;
+  double num = 0.0;
+  std::string str;
+  std::vector<JVal> arr;
+  std::vector<std::pair<std::string, JVal>> obj;
+};
+
+struct JParser {
+  const char* p;
+  const char* end;
+  std::string err;
+  int depth = 0;
+  void ws() { while (p < end && (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r')) ++p; }
+  bool fail(const std::string& m) { if (err.empty()) err = m; return false; }
+  bool lit(const char* s) {
+    const size_t n = std::strlen(s);
+    if ((size_t)(end - p) < n || std::strncmp(p, s, n) != 0) return false;
+    p += n;
+    return true;
+  }
+  bool string(std::string& out) {
+    if (p >= end || *p != '"') return fail("string expected");
+    ++p;
+    while (p < end && *p != '"') {
+      if (*p == '\\') {
+        if (++p >= end) return fail("unterminated escape");
+        const char c = *p++;
+        switch (c) {
+          case 'n': out += '\n'; break;
+          case 't': out += '\t'; break;
+          case 'r': out += '\r'; break;
+          case 'b': out += '\b'; break;
+          case 'f': out += '\f'; break;
+          case 'u': if (end - p < 4) return fail("bad \\u escape"); p += 4; out += '?'; break;
+          default: out += c;
+        }
+      } else {
+        out += *p++;
+      }
+    }
+    if (p >= end) return fail("unterminated string");
+    ++p;
+    return true;
+  }
+  bool value(JVal& v) {
+    if (++depth > 64) return fail("nesting too deep");
+    ws();
+    if (p >= end) return fail("unexpected end of text");
+    bool ok = true;
+    if (*p == '{') {
+      v.kind = JVal::OBJ;
+      ++p; ws();
+      if (p < end && *p == '}') { ++p; }
+      else {
+        while (ok) {
+          ws();
+          std::string key;
+          if (!string(key)) return false;
+          ws();
+          if (p >= end || *p != ':') return fail("':' expected");
+          ++p;
+          v.obj.emplace_back(key, JVal());
+          if (!value(v.obj.back().second)) return false;
+          ws();
+          if (p < end && *p == ',') { ++p; continue; }
+          if (p < end && *p == '}') { ++p; break; }
+          return fail("',' or '}' expected");
+        }
+      }
+    } else if (*p == '[') {
+      v.kind = JVal::ARR;
+      ++p; ws();
+      if (p < end && *p == ']') { ++p; }
+      else {
+        while (true) {
+          v.arr.emplace_back();
+          if (!value(v.arr.back())) return false;
+          ws();
+          if (p < end && *p == ',') { ++p; continue; }
+          if (p < end && *p == ']') { ++p; break; }
+          return fail("',' or ']' expected");
+        }
+      }
+    } else if (*p == '"') {
+      v.kind = JVal::STR;
+      ok = string(v.str);
+    } else if (lit("true")) { v.kind = JVal::BOOL; v.num = 1.0; }
+    else if (lit("false")) { v.kind = JVal::BOOL; v.num = 0.0; }
+    else if (lit("null")) { v.kind = JVal::NUL; }
+    else {
+      char* q = nullptr;
+      const std::string tok(p, std::min<size_t>(64, (size_t)(end - p)));
+      const double d = std::strtod(tok.c_str(), &q);
+      if (q == tok.c_str()) return fail("value expected");
+      p += (q - tok.c_str());
+      v.kind = JVal::NUM;
+      v.num = d;
+    }
+    --depth;
+    return ok;
+  }
+};
+
+const JVal* jfind(const JVal& o, const char* key) {
+  for (auto& kv : o.obj)
+    if (kv.first == key) return &kv.second;
+  return nullptr;
+}
+
+// Flattens a (possibly nested) numeric array; inner = length of the innermost rows (1 for a flat one).
+bool jflat(const JVal& v, std::vector<double>& out, int& inner, std::string& err, const char* key) {
+  inner = 1;
+  if (v.kind != JVal::ARR) { err = std::string("\"") + key + "\" must be an array"; return false; }
+  for (auto& e : v.arr) {
+    if (e.kind == JVal::NUM || e.kind == JVal::BOOL) { out.push_back(e.num); continue; }
+    if (e.kind == JVal::ARR) {
+      if (out.empty() && inner == 1) inner = (int)e.arr.size();
+      if ((int)e.arr.size() != inner) { err = std::string("rows of \"") + key + "\" differ in length"; return false; }
+      for (auto& x : e.arr) {
+        if (x.kind != JVal::NUM) { err = std::string("\"") + key + "\" must hold numbers"; return false; }
+        out.push_back(x.num);
+      }
+      continue;
+    }
+    err = std::string("\"") + key + "\" must hold numbers";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+chem_status parse_mech_json(const char* text, JsonMech& jm, std::string& err) {
+  if (!text) { err = "json_text must not be NULL"; return CHEM_EINVAL; }
+  JParser P{text, text + std::strlen(text), {}};
+  JVal root;
+  if (!P.value(root)) { err = "JSON: " + P.err; return CHEM_EINVAL; }
+  P.ws();
+  if (P.p != P.end) { err = "JSON: text after the top-level value"; return CHEM_EINVAL; }
+  if (root.kind != JVal::OBJ) { err = "JSON: the description must be an object"; return CHEM_EINVAL; }
+  auto getd = [&](const char* key, std::vector<double>& out, int& inner, bool required) -> bool {
+    const JVal* v = jfind(root, key);
+    if (!v || v->kind == JVal::NUL) {
+      if (required) err = std::string("JSON: missing \"") + key + "\"";
+      return !required;
+    }
+    return jflat(*v, out, inner, err, key);
+  };
+  auto geti = [&](const char* key, std::vector<int>& out, int& inner, bool required) -> bool {
+    std::vector<double> tmp;
+    if (!getd(key, tmp, inner, required)) return false;
+    for (double x : tmp) {
+      if (x != std::floor(x) || std::fabs(x) > 2147483647.0) { err = std::string("JSON: \"") + key + "\" must hold integers"; return false; }
+      out.push_back((int)x);
+    }
+    return true;
+  };
+  int in = 1;
+  if (!getd("W", jm.W, in, true) || !getd("T_mid", jm.T_mid, in, true) ||
+      !getd("nasa_lo", jm.nasa_lo, in, true) || !getd("nasa_hi", jm.nasa_hi, in, true) ||
+      !geti("reac_ptr", jm.reac_ptr, in, true) || !geti("reac_sp", jm.reac_sp, in, true) ||
+      !geti("reac_nu", jm.reac_nu, in, true) || !geti("prod_ptr", jm.prod_ptr, in, true) ||
+      !geti("prod_sp", jm.prod_sp, in, true) || !geti("prod_nu", jm.prod_nu, in, true) ||
+      !getd("A", jm.A, in, true) || !getd("b", jm.b, in, true) || !getd("Ea", jm.Ea, in, true) ||
+      !geti("rtype", jm.rtype, in, true) || !geti("reversible", jm.reversible, in, true) ||
+      !geti("eff_ptr", jm.eff_ptr, in, true) || !geti("eff_sp", jm.eff_sp, in, true) ||
+      !getd("eff_alpha", jm.eff_alpha, in, true) || !getd("troe", jm.troe, in, true) ||
+      !getd("low", jm.low, in, true))
+    return CHEM_EINVAL;
+  int comp_inner = 0;
+  if (!geti("comp", jm.comp, comp_inner, false)) return CHEM_EINVAL;
+  const int n = (int)jm.W.size(), R = (int)jm.A.size();
+  if (n < 1) { err = "JSON: \"W\" must list at least one species"; return CHEM_EINVAL; }
+  auto need = [&](size_t have, size_t want, const char* key) {
+    if (have == want) return true;
+    err = std::string("JSON: \"") + key + "\" has " + std::to_string(have) + " values, expected " + std::to_string(want);
+    return false;
+  };
+  if (!need(jm.T_mid.size(), n, "T_mid") || !need(jm.nasa_lo.size(), 7 * (size_t)n, "nasa_lo") ||
+      !need(jm.nasa_hi.size(), 7 * (size_t)n, "nasa_hi") || !need(jm.b.size(), R, "b") ||
+      !need(jm.Ea.size(), R, "Ea") || !need(jm.rtype.size(), R, "rtype") ||
+      !need(jm.reversible.size(), R, "reversible") || !need(jm.reac_ptr.size(), R + 1, "reac_ptr") ||
+      !need(jm.prod_ptr.size(), R + 1, "prod_ptr") || !need(jm.eff_ptr.size(), R + 1, "eff_ptr") ||
+      !need(jm.troe.size(), 4 * (size_t)R, "troe") || !need(jm.low.size(), 3 * (size_t)R, "low") ||
+      !need(jm.eff_alpha.size(), jm.eff_sp.size(), "eff_alpha"))
+    return CHEM_EINVAL;
+  jm.n_elements = 0;
+  if (!jm.comp.empty()) {
+    if (comp_inner < 1 || jm.comp.size() != (size_t)n * comp_inner) {
+      err = "JSON: \"comp\" must be an n_species x n_elements array";
+      return CHEM_EINVAL;
+    }
+    jm.n_elements = comp_inner;
+  }
+  chem_mech_desc& d = jm.desc;
+  d.n_species = n; d.n_reactions = R; d.n_elements = jm.n_elements;
+  d.W = jm.W.data(); d.nasa_lo = jm.nasa_lo.data(); d.nasa_hi = jm.nasa_hi.data(); d.T_mid = jm.T_mid.data();
+  d.comp = jm.comp.empty() ? nullptr : jm.comp.data();
+  d.reac_ptr = jm.reac_ptr.data(); d.reac_sp = jm.reac_sp.data(); d.reac_nu = jm.reac_nu.data();
+  d.prod_ptr = jm.prod_ptr.data(); d.prod_sp = jm.prod_sp.data(); d.prod_nu = jm.prod_nu.data();
+  d.A = jm.A.data(); d.b = jm.b.data(); d.Ea = jm.Ea.data(); d.rtype = jm.rtype.data();
+  d.reversible = jm.reversible.data(); d.eff_ptr = jm.eff_ptr.data(); d.eff_sp = jm.eff_sp.data();
+  d.eff_alpha = jm.eff_alpha.data(); d.troe = jm.troe.data(); d.low = jm.low.data();
   return CHEM_OK;
 }
 

@@ -43,4 +43,16 @@ struct HostMech {
 // Validates and compiles; returns CHEM_OK or an error code with a message in err.
 chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string& err);
 
+// A mechanism description read from JSON: the arrays, and a chem_mech_desc pointing into them.
+struct JsonMech {
+  std::vector<double> W, T_mid, nasa_lo, nasa_hi, A, b, Ea, eff_alpha, troe, low;
+  std::vector<int> comp, reac_ptr, reac_sp, reac_nu, prod_ptr, prod_sp, prod_nu, rtype, reversible, eff_ptr, eff_sp;
+  int n_elements = 0;
+  chem_mech_desc desc{};
+};
+// Parses the JSON form of a description (keys named as the chem_mech_desc fields; two-dimensional
+// arrays as nested rows or flat; other keys ignored).  CHEM_EINVAL with a message on malformed text,
+// missing keys or inconsistent lengths; the description itself is validated by compile_mechanism.
+chem_status parse_mech_json(const char* text, JsonMech& jm, std::string& err);
+
 }  // namespace chemgb

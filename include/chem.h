@@ -29,6 +29,8 @@
 #ifndef CHEM_H_
 #define CHEM_H_
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -263,6 +265,23 @@ chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double
    checked against CUDA's.  Runs on the current device.  CHEM_EINVAL for fn outside {0, 1, 2, 3},
    N < 0 or null pointers with N > 0. */
 chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem_stream stream);
+
+/* Load balancing between processes (Sec. 2.5: the chemistry work is redistributed between MPI ranks so
+   that every rank carries about the same load).  A pure host computation, no handle and no device: every
+   rank calls it on the same all-gathered input and obtains the same plan.
+     world   number of ranks, >= 1.
+     counts  HOST [world]: cells held by each rank (>= 0).
+     costs   HOST [sum counts]: each cell's expected cost (its previous substep count, or 1 when none is
+             known), rank 0's cells first, each rank's in its local order; finite and >= 0.
+     dest    HOST [sum counts], out: the rank that integrates each cell (same order as costs).
+   Rule: target = total cost / world.  Each rank keeps its cheapest cells (ascending cost, ties by local
+   index) while their running sum stays within the target; the remaining cells are dealt in descending
+   cost (ties by rank, then local index) to the rank with the least current load (ties to the lowest
+   rank).  Hence no rank ends above target + the largest single cost, a rank at or below the target
+   keeps all its cells, and a rank above it sends away the fewest cells the target allows.
+   CHEM_EINVAL for world < 1, a negative count, a negative or non-finite cost, or NULL arrays with cells
+   present; dest is then unspecified. */
+chem_status chem_balance_plan(int world, const int64_t* counts, const double* costs, int32_t* dest);
 
 #ifdef __cplusplus
 }

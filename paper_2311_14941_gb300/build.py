@@ -1,7 +1,7 @@
 """Build the CUDA library ``_native/libchemgb.so`` in-tree (sm_103a only).
 
-Two translation units compiled in parallel: the host mechanism compiler (C++) and the C ABI with its
-kernels (CUDA).  Called by ``__graft_entry__.build()``; also runnable as a script.
+Three translation units compiled in parallel: the host mechanism compiler and the load-balance planner
+(C++), and the C ABI with its kernels (CUDA).  Called by ``__graft_entry__.build()``; also runnable as a script.
 """
 import os
 import subprocess
@@ -37,9 +37,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 *inc]
     if ptxas_info:
         cu_flags += ["-Xptxas", "-v"]
+    host = [NVCC, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-x", "c++", *inc]
     jobs = [
-        [NVCC, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-x", "c++", *inc, "-c", os.path.join(CSRC, "compile.cpp"),
-         "-o", os.path.join(OUT, "compile.o")],
+        [*host, "-c", os.path.join(CSRC, "compile.cpp"), "-o", os.path.join(OUT, "compile.o")],
+        [*host, "-c", os.path.join(CSRC, "balance.cpp"), "-o", os.path.join(OUT, "balance.o")],
         [*cu_flags, "-c", os.path.join(CSRC, "capi.cu"), "-o", os.path.join(OUT, "capi.o")],
     ]
 
@@ -55,7 +56,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         list(ex.map(run, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([NVCC, *ARCH, "-shared", "-o", tmp, os.path.join(OUT, "compile.o"), os.path.join(OUT, "capi.o")])
+    run([NVCC, *ARCH, "-shared", "-o", tmp, os.path.join(OUT, "compile.o"), os.path.join(OUT, "balance.o"),
+         os.path.join(OUT, "capi.o")])
     os.replace(tmp, LIB)
     return LIB
 

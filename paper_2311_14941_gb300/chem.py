@@ -84,7 +84,8 @@ def lib():
                                    C.POINTER(OptsC), _vp]
         L.chem_eval_elementary.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp]
         L.chem_create_from_json.argtypes = [C.c_char_p, C.c_int, C.POINTER(_vp)]
-        for f in ("chem_eval_elementary", "chem_create_from_json", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
+        L.chem_balance_plan.argtypes = [C.c_int, _vp, _vp, _vp]
+        for f in ("chem_balance_plan", "chem_eval_elementary", "chem_create_from_json", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
                   "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc", "chem_set_params",
                   "chem_adjoint"):
             getattr(L, f).restype = C.c_int
@@ -299,3 +300,16 @@ def create_from_json(json_text: str, device: int = 0) -> Mechanism:
     except (KeyError, TypeError, ValueError):
         h.desc = None
     return h
+
+
+def balance_plan(counts, costs) -> np.ndarray:
+    """chem_balance_plan: destination rank of every cell.  counts[r] = cells of rank r; costs = all ranks'
+    per-cell costs, rank 0's first, each rank's in local order.  Host arrays."""
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    cst = np.ascontiguousarray(costs, dtype=np.float64)
+    if cst.shape[0] != int(cnt.sum()):
+        raise ValueError("costs must hold sum(counts) values")
+    dest = np.empty(cst.shape[0], dtype=np.int32)
+    _check(lib().chem_balance_plan(len(cnt), cnt.ctypes.data_as(_vp), cst.ctypes.data_as(_vp),
+                                   dest.ctypes.data_as(_vp)), "chem_balance_plan")
+    return dest

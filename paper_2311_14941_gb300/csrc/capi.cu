@@ -623,6 +623,13 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   return CHEM_OK;
 }
 
+chem_status chem_balance_plan(int world, const int64_t* counts, const double* costs, int32_t* dest) {
+  g_err.clear();
+  std::string err;
+  const chem_status st = balance_plan(world, counts, costs, dest, err);
+  return st == CHEM_OK ? CHEM_OK : fail(st, err);
+}
+
 chem_status chem_create_from_json(const char* json_text, int device, chem_handle* out) {
   g_err.clear();
   if (!out) return fail(CHEM_EINVAL, "out must not be NULL");

@@ -1,5 +1,6 @@
 // compile.h -- host mechanism compiler: description -> tables and warp programs.
 #pragma once
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -54,5 +55,8 @@ struct JsonMech {
 // arrays as nested rows or flat; other keys ignored).  CHEM_EINVAL with a message on malformed text,
 // missing keys or inconsistent lengths; the description itself is validated by compile_mechanism.
 chem_status parse_mech_json(const char* text, JsonMech& jm, std::string& err);
+
+// Destination rank of every cell of every rank for an even chemistry load (chem_balance_plan).
+chem_status balance_plan(int world, const int64_t* counts, const double* costs, int32_t* dest, std::string& err);
 
 }  // namespace chemgb

@@ -17,7 +17,8 @@
  *     (alpha_k = 1 unless listed); Troe fall-off k = k_inf Pr/(1+Pr) F (Gilbert-Luther-Troe form);
  *   - reverse rates k_r = k_f / Kc with Kc = exp(-dG/(Ru T)) (p0/(Ru T))^(sum nu), p0 = 101325 Pa;
  *   - Jacobian d f / d y written out densely by the chain rule through C(T, Y), rho(T, Y), c_p(T, Y);
- *   - the 4-stage L-stable Rosenbrock method RODAS3 (Sandu et al. 1997) in its k-form
+ *   - the 4-stage L-stable Rosenbrock method RODAS3 (Sandu et al. 1997; also ROS2 and RODAS4) in its
+ *     k-form
  *       (I - h g J) k_i = h f(y + sum_j a_ij k_j) + h J sum_j g_ij k_j,
  *       y1 = y + sum b_i k_i,  err = sum (b_i - bhat_i) k_i,
  *     with dense partial-pivot LU, and the Hairer-Wanner step-size controller.
@@ -412,13 +413,15 @@ template <class S> void lu_solve(int m, const S* LU, const int* piv, S* b) {
    (I - h gamma J) k_i = h f(y + sum_j alpha_ij k_j) + h J sum_j gamma_ij k_j,
    y_new = y + sum_i b_i k_i, error = sum_i (b_i - bhat_i) k_i; the controller's exponent is
    -1/err_order (the order of the embedded pair plus one). */
+constexpr int kMaxStages = 6;
+
 struct Tableau {
   int s;
   double gamma;
-  double a[4][4];   // alpha_ij, j < i
-  double g[4][4];   // gamma_ij, j < i
-  double b[4], bhat[4];
-  int err_order;
+  double a[kMaxStages][kMaxStages];   // alpha_ij, j < i
+  double g[kMaxStages][kMaxStages];   // gamma_ij, j < i
+  double b[kMaxStages], bhat[kMaxStages];
+  int err_order;                      // the error estimate is O(h^err_order): controller exponent -1/err_order
 };
 
 /* RODAS3 (Sandu et al., Atmos. Environ. 31, 1997): 4 stages, order 3, embedded order 2, L-stable. */
@@ -445,7 +448,66 @@ const Tableau kRos2 = {
     {1.0, 0.0, 0.0, 0.0},
     2};
 
-const Tableau& method_tableau(int method) { return method == 1 ? kRos2 : kRodas3; }
+/* RODAS4 (Hairer and Wanner, Solving Ordinary Differential Equations II, Sec. VI.4): 6 stages, order 4,
+   embedded order 3, stiffly accurate, L-stable, gamma = 1/4.  The method is published in the transformed
+   variables u_i = sum_j Gamma_ij k_j (Gamma lower triangular with diagonal gamma):
+     (I/(h gamma) - J) u_i = f(y + sum_j a_ij u_j) + sum_j (c_ij / h) u_j,
+     y_new = y + sum_i m_i u_i,   error estimate sum_i e_i u_i.
+   Those published numbers are kept here as printed, and the k-form of this oracle's step follows from
+   them: Gamma^-1 = I/gamma - C (C = the strictly lower c_ij), alpha = A Gamma, b = m Gamma, and the
+   embedded weights bhat = (m - e) Gamma. */
+Tableau rodas4_tableau() {
+  const int s = 6;
+  const double gamma = 0.25;
+  double A[6][6] = {}, Cm[6][6] = {};
+  A[1][0] = 1.544;
+  A[2][0] = 0.9466785280815826; A[2][1] = 0.2557011698983284;
+  A[3][0] = 3.314825187068521; A[3][1] = 2.896124015972201; A[3][2] = 0.9986419139977817;
+  A[4][0] = 1.221224509226641; A[4][1] = 6.019134481288629; A[4][2] = 12.53708332932087;
+  A[4][3] = -0.6878860361058950;
+  for (int j = 0; j < 4; ++j) A[5][j] = A[4][j];   // stage 6 starts from stage 5's point plus u_5
+  A[5][4] = 1.0;
+  Cm[1][0] = -5.6688;
+  Cm[2][0] = -2.430093356833875; Cm[2][1] = -0.2063599157091915;
+  Cm[3][0] = -0.1073529058151375; Cm[3][1] = -9.594562251023355; Cm[3][2] = -20.47028614809616;
+  Cm[4][0] = 7.496443313967647; Cm[4][1] = -10.24680431464352; Cm[4][2] = -33.99990352819905;
+  Cm[4][3] = 11.70890893206160;
+  Cm[5][0] = 8.083246795921522; Cm[5][1] = -7.981132988064893; Cm[5][2] = -31.52159432874371;
+  Cm[5][3] = 16.31930543123136; Cm[5][4] = -6.058818238834054;
+  const double mw[6] = {A[4][0], A[4][1], A[4][2], A[4][3], 1.0, 1.0};
+  const double ew[6] = {0, 0, 0, 0, 0, 1.0};
+  // Gamma from its inverse G = I/gamma - C (lower triangular): column by column, forward substitution
+  double Gi[6][6] = {}, Gm[6][6] = {};
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) Gi[i][j] = (i == j ? 1.0 / gamma : 0.0) - Cm[i][j];
+  for (int c = 0; c < s; ++c)
+    for (int i = 0; i < s; ++i) {
+      double r = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) r -= Gi[i][k] * Gm[k][c];
+      Gm[i][c] = r / Gi[i][i];
+    }
+  Tableau t{};
+  t.s = s;
+  t.gamma = gamma;
+  t.err_order = 4;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < i; ++j) {
+      double al = 0.0;
+      for (int k = j; k < i; ++k) al += A[i][k] * Gm[k][j];
+      t.a[i][j] = al;
+      t.g[i][j] = Gm[i][j];
+    }
+  for (int j = 0; j < s; ++j) {
+    double bb = 0.0, bh = 0.0;
+    for (int i = j; i < s; ++i) { bb += mw[i] * Gm[i][j]; bh += (mw[i] - ew[i]) * Gm[i][j]; }
+    t.b[j] = bb;
+    t.bhat[j] = bh;
+  }
+  return t;
+}
+const Tableau kRodas4 = rodas4_tableau();
+
+const Tableau& method_tableau(int method) { return method == 1 ? kRos2 : method == 2 ? kRodas4 : kRodas3; }
 
 /* One Rosenbrock step of size h from y.  Returns false if the iteration matrix is singular. */
 template <class S>
@@ -640,18 +702,19 @@ int oracle_rhs_param_cs(const OMech* m, double p, const double* y, int kind, int
   return 0;
 }
 
-/* A method's coefficients (method 0 RODAS3, 1 ROS2): out[0] = s, out[1] = gamma, then alpha[4][4],
-   gamma_ij[4][4], b[4], bhat[4], out[42] = err_order. */
+/* A method's coefficients (method 0 RODAS3, 1 ROS2, 2 RODAS4), padded to S = 6 stages: out[0] = s,
+   out[1] = gamma, then alpha[S][S], gamma_ij[S][S], b[S], bhat[S], and err_order last (87 values). */
 int oracle_tableau(int method, double* out) {
   const Tableau& t = method_tableau(method);
-  out[0] = t.s; out[1] = t.gamma; out[42] = t.err_order;
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) { out[2 + 4 * i + j] = t.a[i][j]; out[18 + 4 * i + j] = t.g[i][j]; }
-  for (int i = 0; i < 4; ++i) { out[34 + i] = t.b[i]; out[38 + i] = t.bhat[i]; }
+  constexpr int S = kMaxStages, SS = S * S;
+  out[0] = t.s; out[1] = t.gamma; out[2 + 2 * SS + 2 * S] = t.err_order;
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) { out[2 + S * i + j] = t.a[i][j]; out[2 + SS + S * i + j] = t.g[i][j]; }
+  for (int i = 0; i < S; ++i) { out[2 + 2 * SS + i] = t.b[i]; out[2 + 2 * SS + S + i] = t.bhat[i]; }
   return 0;
 }
 
-/* One Rosenbrock step (k-form; method 0 RODAS3, 1 ROS2): ynew, yerr. */
+/* One Rosenbrock step (k-form; method 0 RODAS3, 1 ROS2, 2 RODAS4): ynew, yerr. */
 int oracle_step(const OMech* m, double p, const double* y, double h, double* ynew, double* yerr, int method) {
   Eval<double> ev;
   Perturb<double> pt;

@@ -131,11 +131,15 @@ class Oracle:
         return df
 
     def tableau(self, method=0):
-        """Coefficients of method 0 (RODAS3) or 1 (ROS2) in the k-form of the oracle's step."""
-        out = np.zeros(43)
+        """Coefficients of method 0 (RODAS3), 1 (ROS2) or 2 (RODAS4) in the k-form of the oracle's step
+        (arrays padded to six stages)."""
+        S = 6
+        out = np.zeros(2 + 2 * S * S + 2 * S + 1)
         self.L.oracle_tableau(method, _d(out))
-        return dict(s=int(out[0]), gamma=out[1], alpha=out[2:18].reshape(4, 4), gam=out[18:34].reshape(4, 4),
-                    b=out[34:38].copy(), bhat=out[38:42].copy(), err_order=int(out[42]))
+        o = 2 + 2 * S * S
+        return dict(s=int(out[0]), gamma=out[1], alpha=out[2:2 + S * S].reshape(S, S),
+                    gam=out[2 + S * S:o].reshape(S, S), b=out[o:o + S].copy(), bhat=out[o + S:o + 2 * S].copy(),
+                    err_order=int(out[o + 2 * S]))
 
     def step(self, y, p, h, method=0):
         y = np.ascontiguousarray(y, dtype=np.float64)

@@ -84,6 +84,54 @@ def test_ros2_order_conditions_and_L_stability(small):
     assert max(abs(R(x)) for x in -np.logspace(-3, 8, 200)) <= 1 + 1e-12
 
 
+def _rosenbrock_conditions(b, a, gm, g, order):
+    """Residuals of the Rosenbrock order conditions up to `order` (Hairer and Wanner, Sec. VI.7, with
+    beta_ij = alpha_ij + gamma_ij and beta'_i = sum_{j<i} beta_ij) for weights b."""
+    bm = a + gm
+    be = bm.sum(axis=1)
+    al = a.sum(axis=1)
+    r = [b.sum() - 1, b @ be - (0.5 - g)]
+    if order >= 3:
+        r += [b @ al ** 2 - 1.0 / 3.0, b @ (bm @ be) - (1.0 / 6.0 - g + g * g)]
+    if order >= 4:
+        r += [b @ al ** 3 - 0.25, b @ (al * (a @ be)) - (1.0 / 8.0 - g / 3.0), b @ (bm @ al ** 2) - (1.0 / 12.0 - g / 3.0),
+              b @ (bm @ (bm @ be)) - (1.0 / 24.0 - g / 2.0 + 1.5 * g * g - g ** 3)]
+    return np.array(r)
+
+
+def test_rodas4_order_conditions_and_L_stability(small):
+    """RODAS4 (Hairer and Wanner, Sec. VI.4), as the oracle derives its k-form from the published
+    transformed coefficients: all eight order-4 conditions, an order-3 embedded solution that is not of
+    order 4, the published nodes alpha_i and gamma_i, stiff accuracy of both solutions, and R(-inf) = 0."""
+    t = small[1].tableau(method=2)
+    s, g = t["s"], t["gamma"]
+    assert s == 6 and g == 0.25 and t["err_order"] == 4
+    a, gm, b, bh = t["alpha"][:s, :s], t["gam"][:s, :s], t["b"][:s], t["bhat"][:s]
+    assert np.max(np.abs(_rosenbrock_conditions(b, a, gm, g, 4))) < 1e-14
+    assert np.max(np.abs(_rosenbrock_conditions(bh, a, gm, g, 3))) < 1e-14
+    assert np.min(np.abs(_rosenbrock_conditions(bh, a, gm, g, 4)[4:])) > 1e-3     # embedded: exactly order 3
+    assert np.allclose(a.sum(axis=1), [0.0, 0.386, 0.21, 0.63, 1.0, 1.0], atol=1e-15)
+    assert np.allclose(gm.sum(axis=1) + g, [0.25, -0.1043, 0.1035, -0.0362, 0.0, 0.0], atol=1e-14)
+    # stiffly accurate: y_new is stage 6's point plus k-combination with b = last row of beta and weight gamma;
+    # the embedded solution is stage 6's point itself
+    beta_m = a + gm
+    assert np.allclose(beta_m[s - 1, : s - 1], b[: s - 1], atol=1e-14) and abs(b[s - 1] - g) < 1e-15
+    assert np.allclose(a[s - 1, : s - 1], bh[: s - 1], atol=1e-14) and bh[s - 1] == 0.0
+    B = beta_m + g * np.eye(s)
+
+    def R(z, w=b):
+        return 1 + z * w @ np.linalg.solve(np.eye(s) - z * B, np.ones(s))
+
+    assert abs(1 - b @ np.linalg.solve(B, np.ones(s))) < 1e-13 and abs(1 - bh @ np.linalg.solve(B, np.ones(s))) < 1e-13
+    assert abs(R(-1e12)) < 1e-10
+    assert max(abs(R(1j * y)) for y in np.logspace(-3, 6, 200)) <= 1 + 1e-12
+    assert max(abs(R(x)) for x in -np.logspace(-3, 8, 200)) <= 1 + 1e-12
+    # the same residual function on RODAS3 (order 3): its fourth-order conditions do not all hold
+    t3 = small[1].tableau()
+    r3 = _rosenbrock_conditions(t3["b"][:4], t3["alpha"][:4, :4], t3["gam"][:4, :4], t3["gamma"], 4)
+    assert np.max(np.abs(r3[:4])) < 1e-15 and np.max(np.abs(r3[4:])) > 1e-3
+
+
 # ------------------------------------------------------------------------------------ thermo
 def test_thermo_constant_cp_special_case():
     """A NASA-7 set with only a1, a6, a7 reduces to cp/R = a1, h/RT = a1 + a6/T, s/R = a1 ln T + a7."""
@@ -312,6 +360,40 @@ def test_ros2_observed_order_two_and_decay():
     assert r["status"] == 0 and abs(r["Y"][0] - math.exp(-1.0)) < 2e-5
     r3 = o.integrate(1000.0, P0, np.array([1.0, 0.0]), 1.0, rtol=1e-6, atol=1e-12)
     assert r["nsub"] > r3["nsub"]      # the second-order method needs more steps at the same tolerance
+
+
+def test_rodas4_observed_order_four_and_decay():
+    """Fixed RODAS4 steps on A -> B: the global error falls as h^4; the adaptive run meets the closed form
+    with fewer steps than RODAS3 at the same tolerance."""
+    k, dt = 1.0, 1.0
+    o = Oracle(_AB_mech(k, rev=0))
+    y0 = np.array([1000.0, 1.0, 0.0])
+    errs = []
+    for N in (8, 16, 32, 64):
+        y = o.replay(y0, P0, np.full(N, dt / N), method=2)
+        errs.append(abs(y[1] - math.exp(-k * dt)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 4.0) < 0.05), orders
+    r = o.integrate(1000.0, P0, np.array([1.0, 0.0]), 1.0, rtol=1e-6, atol=1e-12, method=2)
+    assert r["status"] == 0 and abs(r["Y"][0] - math.exp(-1.0)) < 1e-6
+    r3 = o.integrate(1000.0, P0, np.array([1.0, 0.0]), 1.0, rtol=1e-6, atol=1e-12)
+    assert r["nsub"] < r3["nsub"]
+
+
+def test_rodas4_self_convergence_nonlinear(small):
+    """On the stiff small mechanism fixed RODAS4 steps converge at order about 4 once h is small
+    (coarser steps show the order reduction of Rosenbrock methods on stiff problems)."""
+    m, o = small
+    F = synth.field_uniform_random(m, 4, seed=5)
+    y0 = o.state(F.T[1], F.Y[:, 1])
+    t_end = 2e-9
+    ref = o.replay(y0, P0, np.full(4096, t_end / 4096), method=2)
+    errs = []
+    for N in (32, 64, 128):
+        y = o.replay(y0, P0, np.full(N, t_end / N), method=2)
+        errs.append(np.max(np.abs(y - ref) / (np.abs(ref) + 1e-6)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 3.8), orders
 
 
 def test_self_convergence_order_nonlinear(small):

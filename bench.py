@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "reactor-steps/s, 53sp/325rxn FP64 rtol1e-6: persistent vs plain; adjoint s/grad"
 RTOL, ATOL = 1e-6, 1e-12
+METHODS = {"rodas3": 0, "ros2": 1, "rodas4": 2}   # chem_integrate_opts.method
 
 # DRAM bytes per cell of the integration kernel, from one ncu capture of 16,384 cells of the jet field
 # (dram__bytes_read.sum + dram__bytes_write.sum = 9.00 MB; the traffic scales with the cell count: the
@@ -142,8 +143,9 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(m, F, name, budget_s=12.0):
-    """The oracle as it stands on this host's cores over a bounded sample of the workload's cells."""
+def cpu_baseline(m, F, name, budget_s=12.0, method=0):
+    """The oracle as it stands on this host's cores over a bounded sample of the workload's cells, with the
+    same Rosenbrock method and tolerances as the timed GPU run."""
     from oracle.oracle import Oracle
     o = Oracle(m)
     rng = np.random.default_rng(11)
@@ -154,7 +156,7 @@ def cpu_baseline(m, F, name, budget_s=12.0):
         sl = idx[done:done + chunk]
         S = F.subset(sl)
         t0 = time.perf_counter()
-        r = o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL)
+        r = o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL, method=method)
         t_used += time.perf_counter() - t0
         threads = r["threads"]
         done += len(sl)
@@ -232,21 +234,23 @@ def run_reference(args):
     o = Oracle(m)
     rng = np.random.default_rng(13)
     per_step = 64
+    meth = METHODS[args.method]
     for _ in range(args.warmup):
         S = F.subset(rng.choice(F.n_cells, per_step, replace=False))
-        o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL)
+        o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL, method=meth)
     t, threads = 0.0, 0
     for _ in range(args.steps):
         S = F.subset(rng.choice(F.n_cells, per_step, replace=False))
         t0 = time.perf_counter()
-        r = o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL)
+        r = o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL, method=meth)
         t += time.perf_counter() - t0
         threads = r["threads"]
     v = per_step * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "reactor-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config(args.workload, "oracle"), sample=f"{per_step} random cells per step"),
+            "config": dict(config(args.workload, "oracle"), sample=f"{per_step} random cells per step",
+                           method=args.method),
             "cpu_baseline": {"value": v, "unit": "reactor-steps/s", "cores": threads, "kind": "oracle",
                              "sample": f"{per_step} seeded-random cells of the workload's initial field per step"},
             "e2e": {"value": v, "unit": "reactor-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -268,7 +272,7 @@ def main():
     ap.add_argument("--cells", type=int, default=0, help="integrate only this many seeded-random cells (profiling)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint seconds-per-gradient measurement")
     ap.add_argument("--rtol", type=float, default=1e-6, help="relative tolerance (the headline metric is at 1e-6)")
-    ap.add_argument("--method", default="rodas3", choices=["rodas3", "ros2"],
+    ap.add_argument("--method", default="rodas3", choices=list(METHODS),
                     help="Rosenbrock method of the forward integration (the headline is RODAS3)")
     args = ap.parse_args()
     global RTOL
@@ -291,9 +295,9 @@ def main():
     if args.cells:
         F = F.subset(np.sort(np.random.default_rng(5).permutation(F.n_cells)[: args.cells]))
     evolving = WORKLOADS[args.workload]["evolving"]
-    meth = 1 if args.method == "ros2" else 0
+    meth = METHODS[args.method]
     h = chem.create(m, local)
-    oc = opcount.model(m, h.export_plan(0), h.export_plan(1), method=1 if args.method == "ros2" else 0)
+    oc = opcount.model(m, h.export_plan(0), h.export_plan(1), method=meth)
     N = F.n_cells
 
     T0 = torch.tensor(F.T, device=dev)
@@ -448,7 +452,7 @@ def main():
     if adj is not None:
         line["adjoint"] = adj
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(m, F, args.workload)
+        line["cpu_baseline"] = cpu_baseline(m, F, args.workload, method=meth)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -147,7 +147,9 @@ typedef struct {
   int method;             /* Rosenbrock method: 0 RODAS3 (Sandu et al. 1997; order 3, embedded order 2,
                              L-stable; the default and the only one chem_adjoint differentiates),
                              1 ROS2 (Verwer et al. 1999; order 2, embedded order 1, L-stable,
-                             gamma = 1 + 1/sqrt(2)).  Other values: CHEM_EINVAL. */
+                             gamma = 1 + 1/sqrt(2)), 2 RODAS4 (Hairer and Wanner, Sec. VI.4; 6 stages,
+                             order 4, embedded order 3, stiffly accurate, L-stable, gamma = 1/4; same
+                             shared memory per cell as RODAS3).  Other values: CHEM_EINVAL. */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,

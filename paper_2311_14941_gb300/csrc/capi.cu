@@ -770,7 +770,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   io.trace_cap = o.trace ? o.trace_cap : 0;
   io.N = N;
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
-  if (o.method != 0 && o.method != 1) return fail(CHEM_EINVAL, "method must be 0 (RODAS3) or 1 (ROS2)");
+  if (o.method < 0 || o.method > 2) return fail(CHEM_EINVAL, "method must be 0 (RODAS3), 1 (ROS2) or 2 (RODAS4)");
   io.method = o.method;
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
@@ -1015,7 +1015,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   io.trace_cap = o.trace ? o.trace_cap : 0;
   io.N = N;
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
-  if (o.method != 0 && o.method != 1) return fail(CHEM_EINVAL, "method must be 0 (RODAS3) or 1 (ROS2)");
+  if (o.method < 0 || o.method > 2) return fail(CHEM_EINVAL, "method must be 0 (RODAS3), 1 (ROS2) or 2 (RODAS4)");
   io.method = o.method;
   if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
   if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))

@@ -112,6 +112,25 @@ constexpr double M1 = 2.0, M3 = 1.0, M4 = 1.0;
 constexpr double RG2 = 0x1.b504f333f9de6p+0;   // 1 + 1/sqrt(2) rounded to double
 constexpr double R2_A21 = 1.0 / RG2, R2_C21 = -2.0 / RG2, R2_M1 = 1.5 / RG2, R2_M2 = 0.5 / RG2, R2_E = 0.5 / RG2;
 
+// RODAS4 (Hairer and Wanner, Solving ODEs II, Sec. VI.4), order 4 with an order-3 embedded solution,
+// stiffly accurate and L-stable, gamma = 1/4, in its published transformed form:
+//   (I/(h gamma) - J) U_i = f(y + sum_j a_ij U_j) + sum_j (c_ij / h) U_j.
+// a_6j = a_5j (j < 5) and a_65 = 1, m = (a_51, a_52, a_53, a_54, 1, 1), e = (0, 0, 0, 0, 0, 1): stage 6
+// starts from stage 5's point plus U5, y_new is stage 6's point plus U6, and U6 is the error estimate.
+constexpr double RG4 = 0.25;
+constexpr double R4_A21 = 1.544;
+constexpr double R4_A31 = 0.9466785280815826, R4_A32 = 0.2557011698983284;
+constexpr double R4_A41 = 3.314825187068521, R4_A42 = 2.896124015972201, R4_A43 = 0.9986419139977817;
+constexpr double R4_A51 = 1.221224509226641, R4_A52 = 6.019134481288629, R4_A53 = 12.53708332932087,
+                 R4_A54 = -0.6878860361058950;
+constexpr double R4_C21 = -5.6688;
+constexpr double R4_C31 = -2.430093356833875, R4_C32 = -0.2063599157091915;
+constexpr double R4_C41 = -0.1073529058151375, R4_C42 = -9.594562251023355, R4_C43 = -20.47028614809616;
+constexpr double R4_C51 = 7.496443313967647, R4_C52 = -10.24680431464352, R4_C53 = -33.99990352819905,
+                 R4_C54 = 11.70890893206160;
+constexpr double R4_C61 = 8.083246795921522, R4_C62 = -7.981132988064893, R4_C63 = -31.52159432874371,
+                 R4_C64 = 16.31930543123136, R4_C65 = -6.058818238834054;
+
 constexpr double kInvLn10 = 0.43429448190325182765;
 constexpr double kLn10 = 2.30258509299404568402;
 
@@ -738,6 +757,104 @@ __device__ __forceinline__ StepOut ros2_attempt(const MechView& M, double* s, co
   return so;
 }
 
+// One RODAS4 attempt of size h from y (f0, S, u, v already evaluated at y); ynew into ytmp.  U5 lives in
+// the Jacobian's w_k vector (x), which is scratch until the next Jacobian evaluation; stage 6's
+// coefficient sum is gathered into U1 and its solution U6 takes U2's place, so the attempt needs no
+// shared memory beyond RODAS3's.
+template <class Gp>
+__device__ __forceinline__ StepOut ros4_attempt(const MechView& M, double* s, const CellLayout& L, double p, double h,
+                                                double rtol, double atol, const Gp& g) {
+  StepOut so{false, 0.0};
+  const int m = M.m;
+  const double ih = 1.0 / h;
+  if (!lu_build_factor(M, s, L, ih * (1.0 / RG4), g)) return so;
+  double* y = s + L.y;
+  double* yt = s + L.ytmp;
+  double* f0 = s + L.f0;
+  double* U1 = s + L.U1;
+  double* U2 = s + L.U2;
+  double* U3 = s + L.U3;
+  double* U4 = s + L.U4;
+  double* U5 = s + L.x;
+  double* z = s + L.z;
+  const double* u = s + L.u;
+  const double* v = s + L.v;
+  // z = A^-1 u and stage 1's A^-1 f0 in one pass of the solve program, then the Sherman-Morrison
+  // correction of stage 1
+  for (int i = g.lane; i < m; i += g.size) { z[i] = u[i]; U1[i] = f0[i]; }
+  g.sync();
+  lu_solve_impl<true>(M, s, L, z, U1, g);
+  double vz = 0.0, vx = 0.0;
+  for (int i = g.lane; i < m; i += g.size) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
+  vz = gsum(g, vz);
+  vx = gsum(g, vx);
+  const double den = 1.0 - vz;
+  if (!(den != 0.0) || !isfinite(den)) return so;
+  const double iden = 1.0 / den;
+  vx *= iden;
+  for (int i = g.lane; i < m; i += g.size) U1[i] = fma(z[i], vx, U1[i]);
+  g.sync();
+  // stage 2
+  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(R4_A21, U1[i], y[i]);
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U2, g);
+  for (int i = g.lane; i < m; i += g.size) U2[i] = fma(R4_C21 * ih, U1[i], U2[i]);
+  g.sync();
+  sm_solve(M, s, L, U2, iden, g);
+  // stage 3
+  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(R4_A32, U2[i], fma(R4_A31, U1[i], y[i]));
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U3, g);
+  for (int i = g.lane; i < m; i += g.size) U3[i] = fma(ih, fma(R4_C31, U1[i], R4_C32 * U2[i]), U3[i]);
+  g.sync();
+  sm_solve(M, s, L, U3, iden, g);
+  // stage 4
+  for (int i = g.lane; i < m; i += g.size)
+    yt[i] = fma(R4_A43, U3[i], fma(R4_A42, U2[i], fma(R4_A41, U1[i], y[i])));
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U4, g);
+  for (int i = g.lane; i < m; i += g.size)
+    U4[i] = fma(ih, fma(R4_C41, U1[i], fma(R4_C42, U2[i], R4_C43 * U3[i])), U4[i]);
+  g.sync();
+  sm_solve(M, s, L, U4, iden, g);
+  // stage 5
+  for (int i = g.lane; i < m; i += g.size)
+    yt[i] = fma(R4_A54, U4[i], fma(R4_A53, U3[i], fma(R4_A52, U2[i], fma(R4_A51, U1[i], y[i]))));
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U5, g);
+  for (int i = g.lane; i < m; i += g.size)
+    U5[i] = fma(ih, fma(R4_C51, U1[i], fma(R4_C52, U2[i], fma(R4_C53, U3[i], R4_C54 * U4[i]))), U5[i]);
+  g.sync();
+  sm_solve(M, s, L, U5, iden, g);
+  // stage 6: stage 5's point plus U5; the coefficient sum of U1..U5 goes into U1 (not read afterwards)
+  for (int i = g.lane; i < m; i += g.size) {
+    yt[i] += U5[i];
+    U1[i] = ih * fma(R4_C61, U1[i], fma(R4_C62, U2[i], fma(R4_C63, U3[i], fma(R4_C64, U4[i], R4_C65 * U5[i]))));
+  }
+  g.sync();
+  eval_f<double>(M, s, L, yt, p, U2, g);
+  for (int i = g.lane; i < m; i += g.size) U2[i] += U1[i];
+  g.sync();
+  sm_solve(M, s, L, U2, iden, g);
+  // solution = stage 6's point + U6, error estimate U6, scaled RMS norm
+  double e2 = 0.0;
+  bool fin = true;
+  for (int i = g.lane; i < m; i += g.size) {
+    const double yn = yt[i] + U2[i];
+    yt[i] = yn;
+    const double sc = fma(rtol, fmax(fabs(y[i]), fabs(yn)), atol);
+    const double e = U2[i] / sc;
+    e2 = fma(e, e, e2);
+    fin = fin && isfinite(yn);
+  }
+  e2 = gsum(g, e2);
+  fin = gall(g, fin);
+  g.sync();
+  so.err = sqrt(e2 / (double)m);
+  so.good = fin;
+  return so;
+}
+
 struct IntOpts {
   double rtol, atol, h_init, h_min;
   int max_substeps, max_nonfinite;
@@ -752,7 +869,7 @@ struct IntOpts {
   double* rec_ck;
   int* rec_n;
   int rec_cap, rec_K;
-  int method;   // 0 RODAS3, 1 ROS2
+  int method;   // 0 RODAS3, 1 ROS2, 2 RODAS4
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -806,8 +923,9 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       eval_jac<double>(M, s, L, y, p, g);
       needJ = false;
     }
-    const StepOut so = o.method == 1 ? ros2_attempt(M, s, L, p, hu, o.rtol, o.atol, g)
-                                     : ros_attempt(M, s, L, p, hu, o.rtol, o.atol, g);
+    const StepOut so = o.method == 1   ? ros2_attempt(M, s, L, p, hu, o.rtol, o.atol, g)
+                       : o.method == 2 ? ros4_attempt(M, s, L, p, hu, o.rtol, o.atol, g)
+                                       : ros_attempt(M, s, L, p, hu, o.rtol, o.atol, g);
     if (o.trace && g.lane == 0 && ns <= o.trace_cap)
       o.trace[(size_t)(ns - 1) * o.N + cell] = (so.good && isfinite(so.err) && so.err <= 1.0) ? hu : -hu;
     if (!so.good || !isfinite(so.err)) {
@@ -817,8 +935,9 @@ __device__ __forceinline__ void integrate_cell(const MechView& M, double* s, con
       continue;
     }
     nonfinite = 0;
-    // step-size factor: err^(-1/(embedded order + 1)), 3 for RODAS3, 2 for ROS2
-    const double fac = fmax(0.2, 0.9 * pow(so.err, o.method == 1 ? -0.5 : -1.0 / 3.0));
+    // step-size factor: err^(-1/(embedded order + 1)): 3 for RODAS3, 2 for ROS2, 4 for RODAS4
+    const double fac =
+        fmax(0.2, 0.9 * pow(so.err, o.method == 1 ? -0.5 : o.method == 2 ? -0.25 : -1.0 / 3.0));
     if (so.err <= 1.0) {
       t = last ? dt : t + hu;
       ++na;

@@ -46,7 +46,7 @@ class OpCount:
 def model(desc, lu_prog: np.ndarray, sv_prog: np.ndarray, method: int = 0) -> OpCount:
     """desc: flat mechanism (synth.MechDesc); lu_prog/sv_prog: the exported warp programs; method 0 RODAS3
     (2 new right-hand sides, z and 4 stage solves per attempt), 1 ROS2 (1 right-hand side, z and 2 stage
-    solves)."""
+    solves), 2 RODAS4 (5 right-hand sides, z and 6 stage solves)."""
     n = len(desc.W)
     R = len(desc.A)
     m = n + 1
@@ -112,6 +112,10 @@ def model(desc, lu_prog: np.ndarray, sv_prog: np.ndarray, method: int = 0) -> Op
     sm = solve + 2 * m
     if method == 1:
         attempt = lu + (solve + m + DIV) + 2 * sm + f_eval + m * (1 + 1 + 2 + 2) + m * (2 + DIV + 1) + SQRT + POW + 10
+    elif method == 2:
+        # stage points and coefficient sums: 2 + 5 + 7 + 9 + 8 per component, then solution and error
+        attempt = (lu + (solve + m + DIV) + 6 * sm + 5 * f_eval + m * (2 + 5 + 7 + 9 + 8) + m * (2 + DIV + 1) +
+                   SQRT + POW + 10)
     else:
         attempt = (lu + (solve + m + DIV) + 4 * sm + 2 * f_eval + m * (1 + 1 + 3 + 2 + 4 + 3) + m * (1 + DIV + 1) +
                    SQRT + POW + 10)

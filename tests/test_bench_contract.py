@@ -45,6 +45,10 @@ def test_opcount_methods():
     assert a.f_eval == b.f_eval and a.jac == b.jac and a.lu == b.lu
     # RODAS3 has one more right-hand side and two more stage solves per attempt than ROS2
     assert a.attempt - b.attempt >= a.f_eval + 2 * a.solve
+    c = opcount.model(m, h.export_plan(0), h.export_plan(1), method=2)
+    # RODAS4: three more right-hand sides and two more stage solves per attempt than RODAS3
+    assert c.f_eval == a.f_eval and c.jac == a.jac
+    assert c.attempt - a.attempt >= 3 * a.f_eval + 2 * a.solve
     s = a.cell_slots(np.array([10, 20]), np.array([9, 18]))
     assert np.allclose(s, [10 * a.attempt + 9 * a.jac, 20 * a.attempt + 18 * a.jac])
     assert abs(opcount.fp64_peak_tflops() - 2 * 152 * 2.07 * 2 / 1e3) < 1e-12

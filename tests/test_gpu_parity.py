@@ -178,10 +178,10 @@ def _compare_integration(o, g, r, F, max_flip_frac, method=0):
     return len(flips)
 
 
-@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1)])
+@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1), (1, 2), (2, 2)])
 def test_integrate_parity_small_full_config(dev, wpc, method):
     """1024 cells, 10 species / 27 reactions, p = 1 atm, T ~ U(900, 2200) K, Dirichlet Y, dt = 1e-5 s;
-    one or two warps per cell; RODAS3 (method 0) or ROS2 (method 1)."""
+    one or two warps per cell; RODAS3 (method 0), ROS2 (method 1) or RODAS4 (method 2)."""
     m, h, o = mech("small")
     F = synth.field_uniform_random(m, 1024, seed=1)
     r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=8000, method=method)
@@ -190,10 +190,10 @@ def test_integrate_parity_small_full_config(dev, wpc, method):
     assert np.all(g["status"] == 0)
 
 
-@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1)])
+@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1), (1, 2)])
 def test_integrate_parity_methane_sized_sample(dev, wpc, method):
     """120 cells of the bimodal jet field (cold, burnt and mixing-layer cells), 53/325 mechanism; one or
-    two warps per cell; RODAS3 or ROS2."""
+    two warps per cell; RODAS3, ROS2 or RODAS4."""
     m, h, o = mech("mid")
     F = synth.field_bimodal_jet(m, 256, 256, seed=2)
     rng = np.random.default_rng(7)
@@ -218,8 +218,9 @@ def test_integrate_parity_large_sample(dev, wpc):
 def test_integrate_rejects_unknown_method(dev):
     m, h, o = mech("small")
     F = synth.field_uniform_random(m, 4, seed=4)
-    with pytest.raises(chem.ChemError):
-        _integrate_gpu(h, F, dev, method=2)
+    for bad in (-1, 3):
+        with pytest.raises(chem.ChemError):
+            _integrate_gpu(h, F, dev, method=bad)
 
 
 def test_integrate_edge_cases(dev):

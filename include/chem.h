@@ -11,8 +11,10 @@
  *   - NASA-7 thermo, modified Arrhenius, third-body and Troe fall-off rates, reverse rates from Kc;
  *   - an exact Jacobian J = S + u v^T whose sparse part S has a pattern fixed per mechanism (the rank-one
  *     term is the constant-pressure density coupling, v_i = Wbar / W_i);
- *   - the L-stable Rosenbrock method RODAS3 with a sparse LU whose fill-reducing ordering and symbolic
- *     factorisation are fixed once per mechanism, one warp per cell.
+ *   - the L-stable Rosenbrock method RODAS3 (or, by option, ROS2 or RODAS4) with a sparse LU whose
+ *     fill-reducing ordering and symbolic factorisation are fixed once per mechanism, one warp (or two)
+ *     per cell;
+ *   - load balancing between processes as a host-side plan (chem_balance_plan).
  *
  * Conventions for every entry point below.
  *   - Array arguments of the compute calls are DEVICE pointers (cudaMalloc / torch tensors on the

@@ -41,9 +41,15 @@ def _run_elimination(prog, LU, dinv, width=32):
     P = prog.reshape(-1, width, 4)
     for st in P:
         kind = st[0, 0]
+        assert np.all(st[:, 0] == kind), "every lane's op carries the step's kind"
         live = st[st[:, 1] != 65535]
         t, a, b = live[:, 1], live[:, 2], live[:, 3]
         assert len(np.unique(t)) == len(t), "two lanes write one target in a step"
+        # lanes of one step run unordered (two warps per cell are not in lockstep): no lane of an update
+        # step may read a factor entry that another lane of the step writes (scale and reciprocal steps
+        # read only their own target and the 1/pivot array)
+        if kind == 2:
+            assert not np.isin(t, np.concatenate([a, b])).any(), "a step reads an entry it writes"
         if kind == 2:
             LU[t] = LU[t] - LU[a] * LU[b]
         elif kind == 1:
@@ -56,9 +62,12 @@ def _run_solve(prog, LU, dinv, x, width=32):
     P = prog.reshape(-1, width, 4)
     for st in P:
         kind = st[0, 0]
+        assert np.all(st[:, 0] == kind)
         live = st[st[:, 1] != 65535]
         t, a, b = live[:, 1], live[:, 2], live[:, 3]
         assert len(np.unique(t)) == len(t)
+        if kind == 2:
+            assert not np.isin(t, b).any(), "a step reads a vector entry it writes"
         if kind == 2:
             x[t] = x[t] - LU[a] * x[b]
         else:

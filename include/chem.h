@@ -270,6 +270,40 @@ chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double
    N < 0 or null pointers with N > 0. */
 chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem_stream stream);
 
+/* Zonal reference-cell mapping (Sec. 2.5: for regions of low reactivity the chemistry solution is taken
+   from a reference cell instead of being integrated).  Options of chem_integrate_mapped:
+     T_max       cells with T >= T_max (or any non-finite key value) are never mapped;
+     dT          temperature bin width (> 0, finite);
+     n_species   number of mass fractions in the zone key, 0..8;
+     species     their indices (0-based, distinct, < n_species of the mechanism);
+     dY          their bin widths (> 0, finite).
+   A candidate cell (T < T_max) belongs to the zone given by the integers floor(T/dT), floor(Y_s/dY_s)
+   for the listed species s, and the exact values of p and dt: cells of one zone differ by less than dT
+   in T and dY_s in each listed Y_s and share p and dt. */
+typedef struct {
+  double T_max;
+  double dT;
+  int n_species;
+  int species[8];
+  double dY[8];
+} chem_map_opts;
+
+/* chem_integrate with zonal reference-cell mapping.  In every zone with more than one cell, the cell of
+   lowest index is the zone's reference: it is integrated, and every other member takes over its change,
+     T_c <- T_c + (T_ref(dt) - T_ref(0)),  Y_k,c <- Y_k,c + (Y_k,ref(dt) - Y_k,ref(0)) for all k,
+   with status_c = status_ref, nsub_c = 0 (no substep of its own, the cost key of the next call) and h_io_c
+   unchanged.  All other cells are integrated exactly as by chem_integrate.  The mapping keeps sum(Y)
+   to rounding; it does not keep every Y_k >= 0 (the bins bound the error, the caller chooses them).
+     map            host struct; NULL: no mapping (every cell integrated, results as chem_integrate);
+     ref            DEVICE [N], out: the reference of each cell (the cell itself when it was integrated);
+     n_integrated   HOST, out (nullable): the number of cells integrated.
+   Other arguments as for chem_integrate; opts->trace and opts->naccept must be NULL.  The call waits
+   once on `stream` (for the number of cells to integrate) and keeps scratch in the handle (about
+   (n + 14) * 8 bytes per cell).  CHEM_EINVAL for invalid options. */
+chem_status chem_integrate_mapped(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
+                                  double* h_io, int* nsub, int* status, const chem_integrate_opts* opts,
+                                  const chem_map_opts* map, int* ref, int* n_integrated, chem_stream stream);
+
 /* Load balancing between processes (Sec. 2.5: the chemistry work is redistributed between MPI ranks so
    that every rank carries about the same load).  A pure host computation, no handle and no device: every
    rank calls it on the same all-gathered input and obtains the same plan.

@@ -50,6 +50,11 @@ class OptsC(C.Structure):
                 ("warps_per_cell", C.c_int), ("method", C.c_int)]
 
 
+class MapOptsC(C.Structure):
+    _fields_ = [("T_max", C.c_double), ("dT", C.c_double), ("n_species", C.c_int), ("species", C.c_int * 8),
+                ("dY", C.c_double * 8)]
+
+
 CELL_STATUS = {0: "OK", 1: "MAXSTEPS", 2: "HMIN", 3: "NONFINITE", 4: "BADINPUT", 5: "TIMEOUT"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "chem.h")
 
@@ -85,7 +90,9 @@ def lib():
         L.chem_eval_elementary.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp]
         L.chem_create_from_json.argtypes = [C.c_char_p, C.c_int, C.POINTER(_vp)]
         L.chem_balance_plan.argtypes = [C.c_int, _vp, _vp, _vp]
-        for f in ("chem_balance_plan", "chem_eval_elementary", "chem_create_from_json", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
+        L.chem_integrate_mapped.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(OptsC),
+                                            C.POINTER(MapOptsC), _vp, C.POINTER(C.c_int), _vp]
+        for f in ("chem_integrate_mapped", "chem_balance_plan", "chem_eval_elementary", "chem_create_from_json", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
                   "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc", "chem_set_params",
                   "chem_adjoint"):
             getattr(L, f).restype = C.c_int
@@ -273,6 +280,34 @@ class Mechanism:
             _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
             _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
             _dptr(status, torch.int32, N, "status"), C.byref(o), _stream(stream)), "chem_integrate_noalloc")
+
+
+    def integrate_mapped(self, T, p, Y, dt, h_io, nsub, status, ref, mapping=None, rtol=1e-6, atol=1e-12,
+                         h_init=0.0, h_min=0.0, max_substeps=0, max_nonfinite=0, mode=0, block_cells=0, chunk=0,
+                         warps_per_cell=0, method=0, stream=None) -> int:
+        """chem_integrate_mapped: like `integrate`, with zonal reference-cell mapping.  mapping: None or
+        dict(T_max, dT, species=[...], dY=[...]).  ref (int32 [N], device) receives each cell's reference.
+        Returns the number of cells integrated."""
+        import torch
+        N = T.numel()
+        o = OptsC(rtol, atol, h_init, h_min, 0.0, max_substeps, max_nonfinite, mode, block_cells, chunk, None, None,
+                  0, 0, 0, warps_per_cell, method)
+        mp = None
+        if mapping is not None:
+            sp = list(mapping.get("species", ()))
+            dy = list(mapping.get("dY", ()))
+            if len(sp) != len(dy) or len(sp) > 8:
+                raise ValueError("mapping: species and dY must have the same length, at most 8")
+            mp = MapOptsC(float(mapping["T_max"]), float(mapping["dT"]), len(sp), (C.c_int * 8)(*sp),
+                          (C.c_double * 8)(*dy))
+        cnt = C.c_int(0)
+        _check(lib().chem_integrate_mapped(
+            self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
+            _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
+            _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
+            _dptr(status, torch.int32, N, "status"), C.byref(o), C.byref(mp) if mp is not None else None,
+            _dptr(ref, torch.int32, N, "ref"), C.byref(cnt), _stream(stream)), "chem_integrate_mapped")
+        return int(cnt.value)
 
 
 def eval_elementary(fn: int, x, y, stream=None):

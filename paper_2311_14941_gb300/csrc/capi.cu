@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -49,6 +50,8 @@ struct chem_handle_s {
   size_t scratch_bytes = 0;
   void* adj_scratch = nullptr;     // adjoint tape, gradients, dual workspaces (grows on demand)
   size_t adj_scratch_bytes = 0;
+  void* map_scratch = nullptr;     // zonal mapping: zone table and the compacted cells (grows on demand)
+  size_t map_scratch_bytes = 0;
   // per warps-per-cell choice (set with the attributes): the largest block that launches (in cells), the
   // block size that fits the most cells per SM, and that number of cells
   int max_cells[kMaxWarpsPerCell] = {1, 1};
@@ -650,6 +653,7 @@ chem_status chem_destroy(chem_handle h) {
   if (h->blob) cudaFree(h->blob);
   if (h->scratch) cudaFree(h->scratch);
   if (h->adj_scratch) cudaFree(h->adj_scratch);
+  if (h->map_scratch) cudaFree(h->map_scratch);
   delete h;
   return CHEM_OK;
 }
@@ -1071,4 +1075,265 @@ extern "C" chem_status chem_eval_elementary(int fn, int N, const double* x, doub
   if (!x || !y) return fail(CHEM_EINVAL, "null array argument");
   k_elementary<<<(N + 255) / 256, 256, 0, (cudaStream_t)stream>>>(fn, N, x, y);
   return launch_check("chem_eval_elementary launch");
+}
+
+// ===================================================================== zonal reference-cell mapping
+// Sec. 2.5: where the reactivity is low, a cell's chemistry solution is mapped from a reference cell.
+// Zones are found with one open-addressing hash table over the zone keys: every candidate inserts its
+// key and lowers the slot's cell index to its own (atomicMin), so each zone's reference is its lowest
+// index whatever the thread order; a candidate then compares its quantised key with that reference's
+// (a 64-bit hash collision between two zones therefore only costs mapping, never correctness).  The
+// cells to integrate are compacted, integrated by chem_integrate, and the members of each zone take
+// their reference's change before the integrated results are scattered back.
+namespace {
+
+struct MapKey {
+  double T_max, dT;
+  int ns;
+  int sp[8];
+  double dY[8];
+};
+
+// splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// The zone of cell c: q[0] = floor(T/dT), q[1 + i] = floor(Y_s_i / dY_i); false if c is not a candidate
+// (T >= T_max, a non-finite key value, p or dt, or a quotient of magnitude 2^62 or more).
+__device__ bool zone_of(const MapKey& mk, int N, int c, const double* T, const double* p, const double* Y,
+                        const double* dt, long long* q) {
+  const double t = T[c];
+  if (!(isfinite(t) && t < mk.T_max) || !isfinite(p[c]) || !isfinite(dt[c])) return false;
+  for (int i = 0; i <= mk.ns; ++i) {
+    const double x = i == 0 ? t : Y[(size_t)mk.sp[i - 1] * N + c];
+    const double d = i == 0 ? mk.dT : mk.dY[i - 1];
+    if (!isfinite(x)) return false;
+    const double r = x / d;
+    if (!(fabs(r) < 4611686018427387904.0)) return false;   // 2^62
+    q[i] = (long long)floor(r);
+  }
+  return true;
+}
+
+__device__ unsigned long long zone_hash(const long long* q, int nq, double p, double dt) {
+  unsigned long long h = mix64((unsigned long long)__double_as_longlong(p + 0.0));   // -0 and +0 alike
+  h = mix64(h ^ (unsigned long long)__double_as_longlong(dt + 0.0));
+  for (int i = 0; i < nq; ++i) h = mix64(h ^ (unsigned long long)q[i]);
+  return h ? h : 1ull;   // 0 marks an empty slot and a non-candidate
+}
+
+__global__ void k_fill_int(int n, int* __restrict__ a, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+__global__ void k_map_insert(MapKey mk, int N, const double* __restrict__ T, const double* __restrict__ p,
+                             const double* __restrict__ Y, const double* __restrict__ dt,
+                             unsigned long long* __restrict__ key, unsigned long long* tkey, int* tref,
+                             unsigned tmask) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  long long q[9];
+  if (!zone_of(mk, N, c, T, p, Y, dt, q)) { key[c] = 0ull; return; }
+  const unsigned long long hs = zone_hash(q, mk.ns + 1, p[c], dt[c]);
+  key[c] = hs;
+  unsigned s = (unsigned)hs & tmask;
+  for (unsigned it = 0; it <= tmask; ++it, s = (s + 1u) & tmask) {   // the table is at least half empty
+    const unsigned long long prev = atomicCAS(&tkey[s], 0ull, hs);
+    if (prev == 0ull || prev == hs) { atomicMin(&tref[s], c); return; }
+  }
+}
+
+__global__ void k_map_resolve(MapKey mk, int N, const double* __restrict__ T, const double* __restrict__ p,
+                              const double* __restrict__ Y, const double* __restrict__ dt,
+                              const unsigned long long* __restrict__ key, const unsigned long long* __restrict__ tkey,
+                              const int* __restrict__ tref, unsigned tmask, int* __restrict__ ref,
+                              int* __restrict__ pos, int* __restrict__ list, int* count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  int r = c;
+  const unsigned long long hs = key[c];
+  if (hs) {
+    unsigned s = (unsigned)hs & tmask;
+    for (unsigned it = 0; it <= tmask; ++it, s = (s + 1u) & tmask) {
+      const unsigned long long k = tkey[s];
+      if (k == hs) { r = tref[s]; break; }
+      if (k == 0ull) break;
+    }
+    if (r < 0 || r >= N) r = c;
+    if (r != c) {
+      long long qa[9], qb[9];
+      bool same = zone_of(mk, N, c, T, p, Y, dt, qa) && zone_of(mk, N, r, T, p, Y, dt, qb) && p[c] == p[r] &&
+                  dt[c] == dt[r];
+      for (int i = 0; same && i <= mk.ns; ++i) same = qa[i] == qb[i];
+      if (!same) r = c;
+    }
+  }
+  ref[c] = r;
+  if (r == c) {
+    const int j = atomicAdd(count, 1);
+    list[j] = c;
+    pos[c] = j;
+  }
+}
+
+__global__ void k_map_gather(int M, const int* __restrict__ list, int N, int n, const double* __restrict__ T,
+                             const double* __restrict__ p, const double* __restrict__ Y,
+                             const double* __restrict__ dt, const double* __restrict__ h_io,
+                             const int* __restrict__ nsub, double* __restrict__ cT, double* __restrict__ cp,
+                             double* __restrict__ cY, double* __restrict__ cdt, double* __restrict__ ch,
+                             int* __restrict__ cns) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int c = list[j];
+  cT[j] = T[c]; cp[j] = p[c]; cdt[j] = dt[c]; ch[j] = h_io[c]; cns[j] = nsub[c];
+  for (int k = 0; k < n; ++k) cY[(size_t)k * M + j] = Y[(size_t)k * N + c];
+}
+
+// members take their reference's change; runs before the scatter, so T[r], Y[.., r] still hold the
+// references' initial states
+__global__ void k_map_apply(int N, int n, const int* __restrict__ ref, const int* __restrict__ pos,
+                            double* __restrict__ T, double* __restrict__ Y, int* __restrict__ nsub,
+                            int* __restrict__ status, const double* __restrict__ cT, const double* __restrict__ cY,
+                            const int* __restrict__ cst, int M) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const int r = ref[c];
+  if (r == c) return;
+  const int j = pos[r];
+  T[c] = T[c] + (cT[j] - T[r]);
+  for (int k = 0; k < n; ++k) {
+    const size_t o = (size_t)k * N;
+    Y[o + c] = Y[o + c] + (cY[(size_t)k * M + j] - Y[o + r]);
+  }
+  status[c] = cst[j];
+  nsub[c] = 0;
+}
+
+__global__ void k_map_scatter(int M, const int* __restrict__ list, int N, int n, const double* __restrict__ cT,
+                              const double* __restrict__ cY, const double* __restrict__ ch,
+                              const int* __restrict__ cns, const int* __restrict__ cst, double* __restrict__ T,
+                              double* __restrict__ Y, double* __restrict__ h_io, int* __restrict__ nsub,
+                              int* __restrict__ status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int c = list[j];
+  T[c] = cT[j]; h_io[c] = ch[j]; nsub[c] = cns[j]; status[c] = cst[j];
+  for (int k = 0; k < n; ++k) Y[(size_t)k * N + c] = cY[(size_t)k * M + j];
+}
+
+// scratch of one call, 256-byte aligned pieces
+struct MapScratch {
+  unsigned long long *key, *tkey;
+  int *tref, *pos, *list, *count, *cns, *cst;
+  double *cT, *cp, *cdt, *ch, *cY;
+  unsigned tmask;
+  size_t bytes;
+};
+
+MapScratch map_layout(char* base, int N, int n) {
+  unsigned S = 1024;
+  while (S < 2u * (unsigned)N) S <<= 1;
+  MapScratch m{};
+  size_t o = 0;
+  // base == nullptr: only the size is wanted
+  auto take = [&](size_t b) { size_t at = o; o = align_up(o + b, 256); return base ? base + at : nullptr; };
+  m.key = (unsigned long long*)take((size_t)N * 8);
+  m.tkey = (unsigned long long*)take((size_t)S * 8);
+  m.tref = (int*)take((size_t)S * 4);
+  m.pos = (int*)take((size_t)N * 4);
+  m.list = (int*)take((size_t)N * 4);
+  m.count = (int*)take(4);
+  m.cns = (int*)take((size_t)N * 4);
+  m.cst = (int*)take((size_t)N * 4);
+  m.cT = (double*)take((size_t)N * 8);
+  m.cp = (double*)take((size_t)N * 8);
+  m.cdt = (double*)take((size_t)N * 8);
+  m.ch = (double*)take((size_t)N * 8);
+  m.cY = (double*)take((size_t)N * n * 8);
+  m.tmask = S - 1;
+  m.bytes = o;
+  return m;
+}
+
+}  // namespace
+
+extern "C" chem_status chem_integrate_mapped(chem_handle h, int N, double* T, const double* p, double* Y,
+                                             const double* dt, double* h_io, int* nsub, int* status,
+                                             const chem_integrate_opts* opts, const chem_map_opts* map, int* ref,
+                                             int* n_integrated, chem_stream stream) {
+  chem_status st = check_handle(h);
+  if (st != CHEM_OK) return st;
+  if (n_integrated) *n_integrated = 0;
+  if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
+  if (N > (1 << 29)) return fail(CHEM_EINVAL, "N must be <= 2^29 for chem_integrate_mapped");
+  if (N == 0) return CHEM_OK;
+  if (!T || !p || !Y || !dt || !h_io || !nsub || !status || !ref) return fail(CHEM_EINVAL, "null array argument");
+  chem_integrate_opts o{};
+  if (opts) o = *opts;
+  if (o.trace || o.naccept) return fail(CHEM_EINVAL, "chem_integrate_mapped takes no trace and no naccept");
+  const int n = h->hm.n;
+  MapKey mk{};
+  mk.T_max = -INFINITY;   // no candidates
+  mk.dT = 1.0;
+  if (map) {
+    if (std::isnan(map->T_max)) return fail(CHEM_EINVAL, "map->T_max is NaN");
+    if (!(map->dT > 0.0) || !std::isfinite(map->dT)) return fail(CHEM_EINVAL, "map->dT must be finite and > 0");
+    if (map->n_species < 0 || map->n_species > 8) return fail(CHEM_EINVAL, "map->n_species must be 0..8");
+    mk.T_max = map->T_max;
+    mk.dT = map->dT;
+    mk.ns = map->n_species;
+    for (int i = 0; i < mk.ns; ++i) {
+      const int s = map->species[i];
+      if (s < 0 || s >= n) return fail(CHEM_EINVAL, "map->species out of range");
+      for (int j = 0; j < i; ++j)
+        if (map->species[j] == s) return fail(CHEM_EINVAL, "map->species repeats a species");
+      if (!(map->dY[i] > 0.0) || !std::isfinite(map->dY[i])) return fail(CHEM_EINVAL, "map->dY must be finite and > 0");
+      mk.sp[i] = s;
+      mk.dY[i] = map->dY[i];
+    }
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  const size_t need = map_layout(nullptr, N, n).bytes;
+  if (h->map_scratch_bytes < need) {
+    if (h->map_scratch) cudaFree(h->map_scratch);
+    h->map_scratch = nullptr;
+    h->map_scratch_bytes = 0;
+    const size_t bytes = need + need / 4;
+    if (cudaMalloc(&h->map_scratch, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CHEM_ENOMEM, "cudaMalloc of mapping scratch failed");
+    }
+    h->map_scratch_bytes = bytes;
+  }
+  const MapScratch m = map_layout((char*)h->map_scratch, N, n);
+  cudaStream_t strm = (cudaStream_t)stream;
+  const int S = (int)(m.tmask + 1u);
+  cudaMemsetAsync(m.tkey, 0, (size_t)S * 8, strm);
+  cudaMemsetAsync(m.count, 0, 4, strm);
+  k_fill_int<<<(S + 255) / 256, 256, 0, strm>>>(S, m.tref, INT_MAX);
+  const int gb = (N + 255) / 256;
+  k_map_insert<<<gb, 256, 0, strm>>>(mk, N, T, p, Y, dt, m.key, m.tkey, m.tref, m.tmask);
+  k_map_resolve<<<gb, 256, 0, strm>>>(mk, N, T, p, Y, dt, m.key, m.tkey, m.tref, m.tmask, ref, m.pos, m.list,
+                                       m.count);
+  if ((st = launch_check("chem_integrate_mapped zone launch")) != CHEM_OK) return st;
+  int M = 0;
+  if ((e = cudaMemcpyAsync(&M, m.count, 4, cudaMemcpyDeviceToHost, strm)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync");
+  if ((e = cudaStreamSynchronize(strm)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (M < 1 || M > N) return fail(CHEM_ECUDA, "internal error: bad count of cells to integrate");
+  const int gm = (M + 255) / 256;
+  k_map_gather<<<gm, 256, 0, strm>>>(M, m.list, N, n, T, p, Y, dt, h_io, nsub, m.cT, m.cp, m.cY, m.cdt, m.ch, m.cns);
+  if ((st = launch_check("chem_integrate_mapped gather launch")) != CHEM_OK) return st;
+  if ((st = chem_integrate(h, M, m.cT, m.cp, m.cY, m.cdt, m.ch, m.cns, m.cst, &o, stream)) != CHEM_OK) return st;
+  k_map_apply<<<gb, 256, 0, strm>>>(N, n, ref, m.pos, T, Y, nsub, status, m.cT, m.cY, m.cst, M);
+  k_map_scatter<<<gm, 256, 0, strm>>>(M, m.list, N, n, m.cT, m.cY, m.ch, m.cns, m.cst, T, Y, h_io, nsub, status);
+  if ((st = launch_check("chem_integrate_mapped launch")) != CHEM_OK) return st;
+  if (n_integrated) *n_integrated = M;
+  return CHEM_OK;
 }

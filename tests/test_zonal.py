@@ -76,3 +76,115 @@ def test_no_mapping_is_plain_integration():
     b = o.integrate_batch(F.T, F.p, F.Y, F.dt, 1e-6, 1e-12, nthreads=1)
     assert np.array_equal(a["T"], b["T"]) and np.array_equal(a["Y"], b["Y"]) and a["n_integrated"] == 12
     assert np.array_equal(a["ref"], np.arange(12))
+
+
+# ----------------------------------------------------------------------------------------------- GPU
+def _gpu_field(F, dev):
+    import torch
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    N = F.n_cells
+    return dict(T=t(F.T), p=t(F.p), Y=t(F.Y.reshape(-1)), dt=t(F.dt), h=t(np.zeros(N)),
+                ns=t(np.zeros(N), torch.int32), st=t(np.zeros(N), torch.int32), ref=t(np.zeros(N), torch.int32))
+
+
+def _cold_key(m, F):
+    """The two species whose mass fractions vary most over the cold cells (the fuel/air mixture)."""
+    cold = F.T < 700.0
+    sp = np.argsort(-F.Y[:, cold].std(axis=1))[:2]
+    return dict(T_max=700.0, dT=20.0, species=[int(s) for s in sp], dY=[0.02, 0.02])
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch.device("cuda", 0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", [0, 1])
+def test_mapped_integration_matches_oracle(dev, mode):
+    """4096 cells of the bimodal jet field, 10/27 mechanism, dt 1e-5 s: cold cells (< 700 K) mapped by
+    (T, two key species).  Zones bit for bit; integrated cells bit-identical to chem_integrate and within
+    the integration tolerance of the oracle; members exactly T_c + (T_ref(dt) - T_ref(0)) (and Y)."""
+    import torch
+    from paper_2311_14941_gb300 import chem
+    m = synth.mechanism_small()
+    F = synth.field_bimodal_jet(m, 64, 64, seed=4)
+    mp = _cold_key(m, F)
+    h = chem.create(m, 0)
+    g = _gpu_field(F, dev)
+    M = h.integrate_mapped(g["T"], g["p"], g["Y"], g["dt"], g["h"], g["ns"], g["st"], g["ref"], mp, mode=mode)
+    torch.cuda.synchronize()
+    N, n = F.n_cells, m.n_species
+    ref = g["ref"].cpu().numpy()
+    want = zonal.references(F.T, F.p, F.Y, F.dt, mp["T_max"], mp["dT"], mp["species"], mp["dY"])
+    assert np.array_equal(ref, want)
+    integ = ref == np.arange(N)
+    assert M == int(integ.sum()) and M < 0.75 * N           # a good share of the cold cells is mapped
+    Tg, Yg = g["T"].cpu().numpy(), g["Y"].cpu().numpy().reshape(n, N)
+    nsg, stg, hg = g["ns"].cpu().numpy(), g["st"].cpu().numpy(), g["h"].cpu().numpy()
+    # integrated cells: bit for bit the plain chem_integrate results
+    q = _gpu_field(F, dev)
+    h.integrate(q["T"], q["p"], q["Y"], q["dt"], q["h"], q["ns"], q["st"], mode=mode)
+    torch.cuda.synchronize()
+    Tq, Yq = q["T"].cpu().numpy(), q["Y"].cpu().numpy().reshape(n, N)
+    assert np.array_equal(Tg[integ], Tq[integ]) and np.array_equal(Yg[:, integ], Yq[:, integ])
+    assert np.array_equal(nsg[integ], q["ns"].cpu().numpy()[integ])
+    assert np.array_equal(stg[integ], q["st"].cpu().numpy()[integ])
+    # members: the reference's change added, in the same floating-point order
+    mem = np.flatnonzero(~integ)
+    r = ref[mem]
+    assert np.array_equal(Tg[mem], F.T[mem] + (Tg[r] - F.T[r]))
+    assert np.array_equal(Yg[:, mem], F.Y[:, mem] + (Yg[:, r] - F.Y[:, r]))
+    assert np.all(nsg[mem] == 0) and np.array_equal(stg[mem], stg[r]) and np.all(hg[mem] == 0.0)
+    # against the oracle's mapped integration
+    o = Oracle(m)
+    want = zonal.integrate_mapped(o, F.T, F.p, F.Y, F.dt, mp)
+    assert want["n_integrated"] == M
+    assert np.array_equal(stg, want["status"])
+    y_g = np.vstack([Tg[None, :], Yg])
+    y_o = np.vstack([want["T"][None, :], want["Y"]])
+    scale = np.abs(y_o) + np.abs(np.vstack([want["T"][None, :], want["Y"]])[:, want["ref"]])
+    d = np.abs(y_g - y_o)
+    big = scale > 1e-12
+    assert np.all(d[big] <= 1e-5 * scale[big] + 1e-11)                       # every cell: 10 rtol
+    tight = np.all((d <= 1e-8 * scale) | ~big, axis=0)
+    assert tight.mean() > 0.97, tight.mean()                                 # most: the 1e-8 bar
+    print(f"mapped {N - M} of {N} cells; {tight.mean():.4f} of cells within 1e-8")
+
+
+@pytest.mark.gpu
+def test_no_mapping_equals_chem_integrate(dev):
+    import torch
+    from paper_2311_14941_gb300 import chem
+    m = synth.mechanism_small()
+    F = synth.field_uniform_random(m, 777, seed=6)
+    h = chem.create(m, 0)
+    a, b = _gpu_field(F, dev), _gpu_field(F, dev)
+    M = h.integrate_mapped(a["T"], a["p"], a["Y"], a["dt"], a["h"], a["ns"], a["st"], a["ref"], None, mode=1)
+    h.integrate(b["T"], b["p"], b["Y"], b["dt"], b["h"], b["ns"], b["st"], mode=1)
+    torch.cuda.synchronize()
+    assert M == 777
+    assert np.array_equal(a["ref"].cpu().numpy(), np.arange(777))
+    for k in ("T", "Y", "h", "ns", "st"):
+        assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.gpu
+def test_mapping_rejects_bad_options(dev):
+    from paper_2311_14941_gb300 import chem
+    m = synth.mechanism_small()
+    F = synth.field_uniform_random(m, 8, seed=6)
+    h = chem.create(m, 0)
+    g = _gpu_field(F, dev)
+    args = (g["T"], g["p"], g["Y"], g["dt"], g["h"], g["ns"], g["st"], g["ref"])
+    for bad in (dict(T_max=700.0, dT=0.0), dict(T_max=700.0, dT=-1.0), dict(T_max=float("nan"), dT=10.0),
+                dict(T_max=700.0, dT=10.0, species=[0, 0], dY=[0.1, 0.1]),
+                dict(T_max=700.0, dT=10.0, species=[m.n_species], dY=[0.1]),
+                dict(T_max=700.0, dT=10.0, species=[1], dY=[0.0])):
+        with pytest.raises(chem.ChemError) as ei:
+            h.integrate_mapped(*args, bad)
+        assert "status 1" in str(ei.value)
+    assert h.integrate_mapped(*args, dict(T_max=-1.0, dT=10.0)) == 8      # nothing below T_max

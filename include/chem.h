@@ -45,7 +45,7 @@ typedef enum {
   CHEM_EINVAL = 1,       /* invalid argument or mechanism description */
   CHEM_ENOMEM = 2,       /* device or host allocation failed */
   CHEM_ECUDA = 3,        /* a CUDA runtime call failed */
-  CHEM_EUNSUPPORTED = 4  /* valid but outside this build's limits (e.g. shared memory per cell) */
+  CHEM_EUNSUPPORTED = 4  /* valid but outside the library's limits (e.g. shared memory per cell) */
 } chem_status;
 
 /* Per-cell status codes written by chem_integrate. */

@@ -161,9 +161,20 @@ def cpu_baseline(m, F, name, budget_s=12.0, method=0):
         threads = r["threads"]
         done += len(sl)
         chunk = min(chunk * 2, 1024)
+    # the same oracle on one core, over the first cells of the same sample
+    one, t_one = 0, 0.0
+    while t_one < budget_s / 2 and one < F.n_cells:
+        sl = idx[one:one + 8]
+        S = F.subset(sl)
+        t0 = time.perf_counter()
+        o.integrate_batch(S.T, S.p, S.Y, S.dt, RTOL, ATOL, method=method, nthreads=1)
+        t_one += time.perf_counter() - t0
+        one += len(sl)
     return {"value": done / t_used, "unit": "reactor-steps/s", "cores": int(threads), "kind": "oracle",
             "sample": f"{done} seeded-random cells of the {name} workload's initial field, each integrated over "
-                      f"its dt with OpenMP over cells ({t_used:.1f} s)"}
+                      f"its dt with OpenMP over cells ({t_used:.1f} s)",
+            "single_core": {"value": one / t_one, "unit": "reactor-steps/s", "cores": 1,
+                            "sample": f"the first {one} cells of the same sample ({t_one:.1f} s)"}}
 
 
 def adjoint_fields(name, m, F):
@@ -387,6 +398,7 @@ def main():
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         slots = 0.0
+        subs = 0
         torch.cuda.synchronize()
         with Clocks(clocks_path) as ck:
             for i in range(args.steps):
@@ -395,15 +407,22 @@ def main():
                 step()
                 evs[i][1].record(stream)
                 if evolving:   # per-step work differs: count it step by step (outside the timed events)
-                    slots += float(oc.cell_slots(ns.cpu().numpy(), nacc.cpu().numpy()).sum())
+                    ns_h = ns.cpu().numpy()
+                    slots += float(oc.cell_slots(ns_h, nacc.cpu().numpy()).sum())
+                    subs += int(ns_h.sum())
             torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in evs]
         if not evolving:
             slots = args.steps * float(oc.cell_slots(ns.cpu().numpy(), nacc.cpu().numpy()).sum())
+            subs = args.steps * int(ns.sum().item())
         t_total = shard.max_over_ranks(sum(step_ms) / 1e3, dev)
-        return {"t": t_total, "step_ms": step_ms, "slots": slots, "nsub": ns.cpu().numpy(),
+        if world > 1:   # substeps of the whole job
+            tot = torch.tensor([float(subs)], dtype=torch.float64, device=dev)
+            dist.all_reduce(tot)
+            subs = int(tot.item())
+        return {"t": t_total, "step_ms": step_ms, "slots": slots, "subs": subs, "nsub": ns.cpu().numpy(),
                 "nacc": nacc.cpu().numpy(), "status": st.cpu().numpy(), "clocks": ck.summary(local)}
 
     other = "plain" if args.mode == "persistent" else "persistent"
@@ -490,7 +509,7 @@ def main():
                              "the integrate launches; peak derived: 2 DFMA/clk/SM x 152 SM x 2.07 GHz; traffic: DRAM "
                              "bytes per launch scaled from a 16,384-cell ncu capture (null if the kernel changed)"},
         "substeps": {"total": int(nsub.sum()), "mean": float(nsub.mean()), "max": int(nsub.max()),
-                     "accepted": int(nac.sum())},
+                     "accepted": int(nac.sum()), "per_s": res["subs"] / t_total},
         "cell_status": {str(k): int(v) for k, v in zip(*np.unique(res["status"], return_counts=True))},
         "step_ms": res["step_ms"],
     }

@@ -52,3 +52,12 @@ def test_opcount_methods():
     s = a.cell_slots(np.array([10, 20]), np.array([9, 18]))
     assert np.allclose(s, [10 * a.attempt + 9 * a.jac, 20 * a.attempt + 18 * a.jac])
     assert abs(opcount.fp64_peak_tflops() - 2 * 152 * 2.07 * 2 / 1e3) < 1e-12
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    m = synth.mechanism_small()
+    F = synth.field_uniform_random(m, 64, seed=3)
+    b = bench.cpu_baseline(m, F, "small test", budget_s=0.2)
+    assert b["kind"] == "oracle" and b["unit"] == "reactor-steps/s" and b["value"] > 0 and b["cores"] >= 1
+    one = b["single_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and "cells" in one["sample"]

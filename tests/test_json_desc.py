@@ -57,3 +57,45 @@ def test_invalid_mechanism_in_valid_json_is_rejected_by_the_compiler():
     with pytest.raises(chem.ChemError) as ei:
         chem.create_from_json(json.dumps(d), device=-1)
     assert "status 1" in str(ei.value)
+
+
+def test_mutated_json_never_crashes_and_is_checked():
+    """Seeded random edits of a valid description (deleted, inserted or replaced characters, truncation):
+    every result is either a compiled handle or CHEM_EINVAL, never a crash or another status."""
+    import ctypes
+    import random
+    L = chem.lib()
+    base = synth.mechanism_small().to_json()
+    rng = random.Random(2311)
+    alphabet = '{}[]",:.-+eE0123456789 \n\tabcdefnulltrue\\/'
+    seen = {0: 0, 1: 0}
+    for _ in range(600):
+        s = list(base)
+        for _ in range(rng.randint(1, 6)):
+            op, i = rng.random(), rng.randrange(len(s) + 1)
+            if op < 0.4 and s:
+                del s[min(i, len(s) - 1)]
+            elif op < 0.8:
+                s.insert(i, rng.choice(alphabet))
+            elif s:
+                s[min(i, len(s) - 1)] = rng.choice(alphabet)
+        if rng.random() < 0.1:
+            s = s[:rng.randrange(len(s) + 1)]
+        h = ctypes.c_void_p()
+        rc = L.chem_create_from_json("".join(s).encode(), -1, ctypes.byref(h))
+        assert rc in (0, 1), rc
+        seen[rc] += 1
+        if rc == 0:
+            L.chem_destroy(h)
+    assert seen[0] > 0 and seen[1] > 0
+
+
+@pytest.mark.parametrize("text", [
+    '{"W": ' + "[" * 100000 + "]" * 100000 + "}",          # nesting far beyond the reader's limit
+    '{"W": ' + '{"a":' * 50000 + "1" + "}" * 50000 + "}",
+    '{"W": [1e999]}', '{"W": [1,2,]}', "", "{",
+])
+def test_pathological_json_is_rejected(text):
+    with pytest.raises(chem.ChemError) as ei:
+        chem.create_from_json(text, device=-1)
+    assert "status 1" in str(ei.value)

@@ -193,19 +193,22 @@ chem_status chem_jacobian_pattern(chem_handle h, int* row_ptr, int* col_idx);
    With out == NULL only *count is written.  *count: number of ints. */
 chem_status chem_export_plan(chem_handle h, int which, int* out, int* count);
 
-/* Right-hand side of the reactor ODE for N cells:
+/* Right-hand side of the reactor ODE for N cells (each cell a homogeneous reactor, Sec. 1 and Sec. 2.5):
    dTdt [N] = -sum_k H_k w_k / (rho c_p), dYdt [n*N] = W_k w_k / rho, wdot [n*N] (nullable) = net molar
    production rates w_k in mol/(m^3 s).  Inputs T [N], p [N], Y [n*N]. */
 chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, const double* Y,
                        double* dTdt, double* dYdt, double* wdot, chem_stream stream);
 
-/* Exact Jacobian of chem_rates' right-hand side, J = S + u v^T, for N cells:
+/* Exact Jacobian of chem_rates' right-hand side, J = S + u v^T, for N cells (the sparse analytical
+   Jacobian of Sec. 2.5; S in the static pattern of chem_jacobian_pattern):
    S_vals [nnz_S*N] (entry-major: entry e of cell c at S_vals[e*N + c], entries in the CSR order of
    chem_jacobian_pattern), u [m*N], v [m*N] (v_0 = 0, v_{1+k} = Wbar / W_k). */
 chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p, const double* Y,
                           double* S_vals, double* u, double* v, chem_stream stream);
 
-/* Advance N cells over their own step dt[c] with RODAS3 and error control.
+/* Advance N cells over their own step dt[c] (Sec. 2.5: every cell integrated over its flow time step, with
+   its own step under local time stepping) by the Rosenbrock method of opts->method (RODAS3 by
+   default) with error control.
    In/out: T [N], Y [n*N]; h_io [N] (in: first step, <= 0 takes h_init; out: next proposed step);
    nsub [N] (in: previous substep counts, the sort key of mode 1; out: attempts taken in this call);
    status [N] (out: CHEM_CELL_*).  In: p [N], dt [N].  opts may be NULL (defaults).
@@ -272,7 +275,8 @@ chem_status chem_eval_elementary(int fn, int N, const double* x, double* y, chem
 
 /* Zonal reference-cell mapping (Sec. 2.5: for regions of low reactivity the chemistry solution is taken
    from a reference cell instead of being integrated).  Options of chem_integrate_mapped:
-     T_max       cells with T >= T_max (or any non-finite key value) are never mapped;
+     T_max       cells with T >= T_max, a non-finite key value, p or dt, or a key quotient (below) of
+                 magnitude 2^62 or more are never mapped (NaN: CHEM_EINVAL);
      dT          temperature bin width (> 0, finite);
      n_species   number of mass fractions in the zone key, 0..8;
      species     their indices (0-based, distinct, < n_species of the mechanism);
@@ -297,7 +301,7 @@ typedef struct {
      map            host struct; NULL: no mapping (every cell integrated, results as chem_integrate);
      ref            DEVICE [N], out: the reference of each cell (the cell itself when it was integrated);
      n_integrated   HOST, out (nullable): the number of cells integrated.
-   Other arguments as for chem_integrate; opts->trace and opts->naccept must be NULL.  The call waits
+   Other arguments as for chem_integrate; opts->trace and opts->naccept must be NULL; N <= 2^29.  The call waits
    once on `stream` (for the number of cells to integrate) and keeps scratch in the handle (about
    (n + 14) * 8 bytes per cell).  CHEM_EINVAL for invalid options. */
 chem_status chem_integrate_mapped(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,

@@ -26,6 +26,8 @@
  *     returns the message of the last failure on the calling thread.  Per-cell numerical failures never
  *     fail the call: they are reported in the per-cell status array.
  *   - No call aborts, traps or prints.  A handle may be used from one host thread at a time.
+ *   - Calls that take a handle run on the handle's device: they make it current for the call and put the
+ *     caller's current device back before returning (chem_create likewise for its `device`).
  *   - Units: SI (K, Pa, kg/mol, mol/m^3, J/mol, s).
  */
 #ifndef CHEM_H_
@@ -133,7 +135,10 @@ typedef struct {
                              substep count */
   int block_cells;        /* cells in flight per block (each takes warps_per_cell warps); 0: automatic;
                              larger requests are reduced to the largest block that launches */
-  int chunk;              /* cells taken per queue pull in mode 1; 0: automatic */
+  int chunk;              /* cells taken per queue pull in mode 1; 0: automatic (1).  Values above an even
+                             share of the cells over the resident lane groups, ceil(N / groups), are
+                             reduced to that share (a larger pull only leaves lane groups idle); results
+                             do not depend on it */
   int* naccept;           /* optional DEVICE array [N]: accepted steps per cell (NULL: not written) */
   double* trace;          /* optional DEVICE array [trace_cap*N]: attempt i of cell c at trace[i*N + c],
                              +h if accepted, -h if rejected, 0 after the last attempt (NULL: off) */

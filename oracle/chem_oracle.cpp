@@ -760,7 +760,9 @@ int oracle_replay_sens_cs(const OMech* m, double p, const double* y0, const doub
   return ok ? 0 : 1;
 }
 
-/* Batch driver over N cells (structure of arrays: Y[k*N + c]); OpenMP dynamic schedule over cells.
+/* Batch driver over N cells (structure of arrays: Y[k*N + c]); OpenMP dynamic schedule over cells, one
+   cell at a time (a cell's integration takes milliseconds to seconds, so small samples keep every core
+   busy).
    h_io: in initial step (<= 0: default), out last proposed step.  Optional trace [trace_cap*N]: attempt i
    of cell c at trace[i*N + c], +h accepted, -h rejected, 0 after the last.  Returns the thread count. */
 int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, double* Y, const double* dt,
@@ -777,7 +779,7 @@ int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, do
 #pragma omp single
     used = omp_get_num_threads();
   }
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int c = 0; c < N; ++c) {
     std::vector<double> y(mm);

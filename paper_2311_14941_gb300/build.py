@@ -1,7 +1,8 @@
 """Build the CUDA library ``_native/libchemgb.so`` in-tree (sm_103a only).
 
-Three translation units compiled in parallel: the host mechanism compiler and the load-balance planner
-(C++), and the C ABI with its kernels (CUDA).  Called by ``__graft_entry__.build()``; also runnable as a script.
+Five translation units compiled in parallel: the host mechanism compiler and the load-balance planner
+(C++), the C ABI with its small kernels, the forward (rate, Jacobian, integration) kernels and the
+adjoint kernels (CUDA).  Called by ``__graft_entry__.build()``; also runnable as a script.
 """
 import os
 import subprocess
@@ -42,6 +43,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         [*host, "-c", os.path.join(CSRC, "compile.cpp"), "-o", os.path.join(OUT, "compile.o")],
         [*host, "-c", os.path.join(CSRC, "balance.cpp"), "-o", os.path.join(OUT, "balance.o")],
         [*cu_flags, "-c", os.path.join(CSRC, "capi.cu"), "-o", os.path.join(OUT, "capi.o")],
+        [*cu_flags, "-c", os.path.join(CSRC, "kern_forward.cu"), "-o", os.path.join(OUT, "kern_forward.o")],
+        [*cu_flags, "-c", os.path.join(CSRC, "kern_adjoint.cu"), "-o", os.path.join(OUT, "kern_adjoint.o")],
     ]
 
     def run(cmd):
@@ -56,8 +59,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         list(ex.map(run, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([NVCC, *ARCH, "-shared", "-o", tmp, os.path.join(OUT, "compile.o"), os.path.join(OUT, "balance.o"),
-         os.path.join(OUT, "capi.o")])
+    run([NVCC, *ARCH, "-shared", "-o", tmp, *(os.path.join(OUT, f + ".o") for f in
+                                              ("compile", "balance", "capi", "kern_forward", "kern_adjoint"))])
     os.replace(tmp, LIB)
     return LIB
 

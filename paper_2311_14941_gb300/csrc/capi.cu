@@ -11,8 +11,7 @@
 
 #include "../../include/chem.h"
 #include "compile.h"
-#include "adjoint.cuh"
-#include "device.cuh"
+#include "kernels.cuh"
 
 using namespace chemgb;
 
@@ -57,6 +56,7 @@ struct chem_handle_s {
   int max_cells[kMaxWarpsPerCell] = {1, 1};
   int default_cells[kMaxWarpsPerCell] = {1, 1};
   int resident_cells[kMaxWarpsPerCell] = {0, 0};
+  int bps_cache[kMaxWarpsPerCell][17] = {};   // resident blocks per SM of the persistent kernel, per shape
   int auto_wpc = 1;                // warps per cell when the caller leaves the choice to the library
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
@@ -136,124 +136,11 @@ size_t put(std::vector<char>& buf, const std::vector<T>& v) {
 // =============================================================================================== kernels
 namespace chemgb {
 
-__device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long long* stamp,
-                                                 unsigned long long budget_ns);
-
-// Load one cell's state into y (lanes over state components).
-template <class Gp>
-__device__ __forceinline__ void load_state(double* y, int m, int N, int c, const double* T, const double* Y,
-                                           const Gp& g) {
-  for (int i = g.lane; i < m; i += g.size) y[i] = (i == 0) ? T[c] : Y[(size_t)(i - 1) * N + c];
-  g.sync();
-}
-
-// The lane group of this thread when each cell of a block takes W warps; s = the cell's memory.
-__device__ __forceinline__ void cell_slot(int gs, const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
-  cell_in_block = threadIdx.x / gs;
-  s = smem + (size_t)cell_in_block * L.total;
-}
-template <int W>
-__device__ __forceinline__ GrpW<W> cell_group(const CellLayout& L, double* smem, int& cell_in_block, double*& s);
-template <>
-__device__ __forceinline__ Grp1 cell_group<1>(const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
-  cell_slot(Grp1::size, L, smem, cell_in_block, s);
-  return Grp1{(int)threadIdx.x - cell_in_block * Grp1::size};
-}
-template <>
-__device__ __forceinline__ Grp2 cell_group<2>(const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
-  cell_slot(Grp2::size, L, smem, cell_in_block, s);
-  return Grp2{(int)threadIdx.x - cell_in_block * Grp2::size, 1 + cell_in_block, s + L.misc};
-}
-
-// Block-cooperative coalesced load of the block's consecutive cells: adjacent threads read adjacent
-// cells of the same state row (structure of arrays), then each lane group owns its cell's copy.
-__device__ __forceinline__ void load_tile(double* smem, const CellLayout& L, int m, int N, int c0, int wpb,
-                                          const double* T, const double* Y) {
-  const int total = wpb * m;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int row = idx / wpb, w = idx - row * wpb;
-    const int c = c0 + w;
-    if (c < N) smem[(size_t)w * L.total + L.y + row] = (row == 0) ? T[c] : Y[(size_t)(row - 1) * N + c];
-  }
-  __syncthreads();
-}
-
-__global__ void k_rates(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
-                        const double* __restrict__ Y, double* __restrict__ dTdt, double* __restrict__ dYdt,
-                        double* __restrict__ wdot) {
-  extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int c0 = blockIdx.x * wpb;
-  double* s = smem + (size_t)w * L.total;
-  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
-  const int c = c0 + w;
-  if (c >= N) return;
-  const Grp1 g{lane};
-  double* f = s + L.f0;
-  Scal sc = eval_f<double>(M, s, L, s + L.y, p[c], f, g);
-  for (int i = lane; i < M.m; i += kWarp) {
-    if (i == 0) dTdt[c] = f[0];
-    else dYdt[(size_t)(i - 1) * N + c] = f[i];
-  }
-  if (wdot) {
-    for (int k = lane; k < M.n; k += kWarp) wdot[(size_t)k * N + c] = f[1 + k] * sc.rho * __ldg(M.sp + (size_t)k * SP_STRIDE);
-  }
-}
-
-__global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
-                           const double* __restrict__ Y, double* __restrict__ Sv, double* __restrict__ u,
-                           double* __restrict__ v) {
-  extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int c0 = blockIdx.x * wpb;
-  double* s = smem + (size_t)w * L.total;
-  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
-  const int c = c0 + w;
-  if (c >= N) return;
-  eval_jac<double>(M, s, L, s + L.y, p[c], Grp1{lane});
-  for (int e = lane; e < M.nnz_S; e += kWarp) Sv[(size_t)__ldg(M.s_out + e) * N + c] = s[L.S + e];
-  for (int i = lane; i < M.m; i += kWarp) {
-    u[(size_t)i * N + c] = s[L.u + i];
-    v[(size_t)i * N + c] = s[L.v + i];
-  }
-}
-
-// Plain form: one lane group (W warps) per cell, cells in index order, one launch.
-template <int W>
-__global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __restrict__ T, const double* __restrict__ p,
-                                  double* __restrict__ Y, const double* __restrict__ dt, double* __restrict__ h_io,
-                                  int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
-                                  IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
-  extern __shared__ double smem[];
-  const int cpb = blockDim.x / (W * kWarp);
-  int w = 0;
-  double* s = nullptr;
-  const GrpW<W> g = cell_group<W>(L, smem, w, s);
-  const int c0 = blockIdx.x * cpb;
-  load_tile(smem, L, M.m, N, c0, cpb, T, Y);
-  const int c = c0 + w;
-  if (c >= N) return;
-  double h = h_io[c];
-  int ns = 0, na = 0, st = 0;
-  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, with_deadline(o, stamp, budget_ns), g, c);
-  const double* y = s + L.y;
-  for (int i = g.lane; i < M.m; i += g.size) {
-    if (i == 0) T[c] = y[0];
-    else Y[(size_t)(i - 1) * N + c] = y[i];
-  }
-  if (g.lane == 0) {
-    h_io[c] = h;
-    nsub[c] = ns;
-    status[c] = st;
-    if (nacc_out) nacc_out[c] = na;
-  }
-}
-
 // ---- sorted work queue (the on-chip form of the paper's dynamic load balancing)
 constexpr int kBuckets = 32;
 
-// Scratch layout (bytes): [0, 128) bucket counts, [128, 256) bucket cursors, [256, 260) queue head,
-// [264, 272) start stamp (ns), [512, 512 + 4N) permutation.
+// Scratch layout (bytes): [0, 128) bucket counts, [128, 256) bucket cursors, [256, 264) queue head
+// (64-bit), [264, 272) start stamp (ns), [512, 512 + 4N) permutation.
 constexpr size_t kScrCounts = 0, kScrCursor = 128, kScrHead = 256, kScrStamp = 264, kScrPerm = 512;
 
 // Scratch for chem_integrate_noalloc: a fixed array in the module's static device memory, so that
@@ -295,142 +182,34 @@ __global__ void k_sort_scatter(int N, const int* __restrict__ nsub_prev, const i
   }
 }
 
-__device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long long* stamp,
-                                                 unsigned long long budget_ns) {
-  if (budget_ns && stamp) o.deadline_ns = *stamp + budget_ns;
-  return o;
-}
-
-// Persistent form: grid sized to the resident capacity; every warp pulls `chunk` cells at a time from
-// the sorted queue with one atomicAdd and integrates them one after the other.  No block-wide barrier:
-// warps of a block finish independently.
-template <int W>
-__global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* __restrict__ T,
-                                       const double* __restrict__ p, double* __restrict__ Y,
-                                       const double* __restrict__ dt, double* __restrict__ h_io,
-                                       int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
-                                       const int* __restrict__ perm, int* __restrict__ head, int chunk, IntOpts o,
-                                       const unsigned long long* stamp, unsigned long long budget_ns) {
-  extern __shared__ double smem[];
-  int w = 0;
-  double* s = nullptr;
-  const GrpW<W> g = cell_group<W>(L, smem, w, s);
-  const IntOpts oo = with_deadline(o, stamp, budget_ns);
-  while (true) {
-    const int base = (int)gbcast(g, g.lane == 0 ? atomicAdd(head, chunk) : 0);
-    if (base >= N) break;
-    const int end = min(base + chunk, N);
-    for (int j = base; j < end; ++j) {
-      const int c = perm[j];
-      load_state(s + L.y, M.m, N, c, T, Y, g);
-      double h = h_io[c];
-      int ns = 0, na = 0, st = 0;
-      integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, oo, g, c);
-      const double* y = s + L.y;
-      for (int i = g.lane; i < M.m; i += g.size) {
-        if (i == 0) T[c] = y[0];
-        else Y[(size_t)(i - 1) * N + c] = y[i];
-      }
-      if (g.lane == 0) {
-        h_io[c] = h;
-        nsub[c] = ns;
-        status[c] = st;
-        if (nacc_out) nacc_out[c] = na;
-      }
-      g.sync();
-    }
-  }
-}
-
-// ---- discrete adjoint: resident warps pull cells; each has its own dual-number workspace in global
-// memory (the forward-layout size in Duals)
-__global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const double* __restrict__ p,
-                          const double* __restrict__ rec_h, const double* __restrict__ rec_ck,
-                          const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
-                          const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
-                          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head,
-                          const int* __restrict__ perm, Dual4* dual_ws, double* warp_ws, IntOpts o) {
-  extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int gw = blockIdx.x * wpb + w;
-  double* s = smem + (size_t)w * A.total;
-  Dual4* dw = dual_ws + (size_t)gw * Ld.total;
-  const int m = M.m;
-  double* seg = warp_ws + (size_t)gw * ((size_t)K * m + 2 * (size_t)M.R);
-  double* GA = seg + (size_t)K * m;
-  double* GE = GA + M.R;
-  while (true) {
-    int c = 0;
-    if (lane == 0) c = atomicAdd(head, 1);
-    c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= N) break;
-    c = perm[c];   // costliest cells (longest tapes) first
-    const int na = rec_n[c];
-    double* LAM = s + A.LAM;
-    for (int i = lane; i < m; i += kWarp) LAM[i] = (i == 0) ? gT[c] : gY[(size_t)(i - 1) * N + c];
-    for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
-    __syncwarp();
-    bool ok = na >= 0;
-    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, Grp1{lane}, o, seg, GA, GE);
-    if (!ok) {
-      for (int i = lane; i < m; i += kWarp) LAM[i] = 0.0;
-      for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
-      __syncwarp();
-    }
-    for (int r = lane; r < M.R; r += kWarp) {
-      const int d = __ldg(M.rx_order + r);
-      grad_cell[(size_t)d * N + c] = GA[r];
-      grad_cell[(size_t)(M.R + d) * N + c] = GE[r];
-    }
-    if (gT0 && lane == 0) gT0[c] = LAM[0];
-    if (gY0)
-      for (int i = 1 + lane; i < m; i += kWarp) gY0[(size_t)(i - 1) * N + c] = LAM[i];
-    if (status && lane == 0 && !ok && status[c] == CHEM_CELL_OK) status[c] = CHEM_CELL_NOTAPE;
-    __syncwarp();
-  }
-}
-
-// sums over cells in a fixed order (one warp per parameter): deterministic gradients
-__global__ void k_grad_reduce(int N, int P, const double* __restrict__ grad_cell, double* __restrict__ out1,
-                              double* __restrict__ out2, int half) {
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp, lane = threadIdx.x % kWarp;
-  if (wg >= P) return;
-  double acc = 0.0;
-  for (int c = lane; c < N; c += kWarp) acc += grad_cell[(size_t)wg * N + c];
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    if (wg < half) out1[wg] = acc;
-    else out2[wg - half] = acc;
-  }
-}
-
-// parameter shifts: ln A_r = ln A_r,0 + dlnA[d], Ea_r = Ea_r,0 + dEa[d] (d: description index of
-// compiled reaction r); Troe low-pressure limits shift jointly
-__global__ void k_set_params(MechView M, const double* __restrict__ rxd0, double* __restrict__ rxd,
-                             const double* __restrict__ dlnA, const double* __restrict__ dEa) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= M.R) return;
-  const int d = __ldg(M.rx_order + r);
-  const double a = dlnA ? dlnA[d] : 0.0, e = dEa ? dEa[d] / kRu : 0.0;
-  const double* src = rxd0 + (size_t)r * RX_D;
-  double* dst = rxd + (size_t)r * RX_D;
-  dst[0] = src[0] + a;
-  dst[2] = src[2] + e;
-  if (__ldg((const int*)(M.rxi + (size_t)r * RX_I)) == 2) {
-    dst[3] = src[3] + a;
-    dst[5] = src[5] + e;
-  }
-}
-
 }  // namespace chemgb
 
 // =============================================================================================== ABI
 namespace {
 
-chem_status check_handle(chem_handle h) {
+// The handle's device is made current for the duration of an entry point; the caller's current device
+// is put back when the scope ends, so a call never leaves another device selected.
+struct DeviceScope {
+  int prev = -1;
+  int cur = -1;
+  cudaError_t enter(int device) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) { prev = -1; return e; }
+    cur = prev;
+    if (device == prev) return cudaSuccess;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) cur = device;
+    return e;
+  }
+  ~DeviceScope() {
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+chem_status check_handle(chem_handle h, DeviceScope& ds) {
   if (!h) return fail(CHEM_EINVAL, "null handle");
   if (h->device < 0) return fail(CHEM_EINVAL, "handle was compiled on the host only (device -1)");
-  cudaError_t e = cudaSetDevice(h->device);
+  cudaError_t e = ds.enter(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   return CHEM_OK;
 }
@@ -443,21 +222,21 @@ chem_status set_attrs(chem_handle h) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_plain<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+      (e = cudaFuncSetAttribute(forward_kernel(KF_PLAIN, 1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_plain<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+      (e = cudaFuncSetAttribute(forward_kernel(KF_PLAIN, 2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+      (e = cudaFuncSetAttribute(forward_kernel(KF_PERSISTENT, 1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_integrate_persistent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+      (e = cudaFuncSetAttribute(forward_kernel(KF_PERSISTENT, 2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute");
   // largest block per warps-per-cell choice: shared memory, the threads the kernels' registers allow
   // (both forms), at most 16 cells, and for two-warp cells the 15 named barriers besides barrier 0
   for (int wpc = 1; wpc <= kMaxWarpsPerCell; ++wpc) {
     cudaFuncAttributes fa1, fa2;
-    if ((e = cudaFuncGetAttributes(&fa1, wpc == 1 ? k_integrate_plain<1> : k_integrate_plain<2>)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa2, wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>)) !=
+    if ((e = cudaFuncGetAttributes(&fa1, forward_kernel(KF_PLAIN, wpc))) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa2, forward_kernel(KF_PERSISTENT, wpc))) !=
             cudaSuccess)
       return cuda_fail(e, "cudaFuncGetAttributes");
     int c = std::max(1, h->smem_optin / std::max(h->cell_bytes, 1));
@@ -473,7 +252,7 @@ chem_status set_attrs(chem_handle h) {
     for (int c = 1; c <= max_cells_per_block(h, wpc); ++c) {
       int blocks = 0;
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-               &blocks, wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>, c * wpc * kWarp,
+               &blocks, forward_kernel(KF_PERSISTENT, wpc), c * wpc * kWarp,
                (size_t)c * h->cell_bytes)) != cudaSuccess)
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
       if (blocks * c > best_cells) { best_cells = blocks * c; best_c = c; }
@@ -517,6 +296,78 @@ chem_status launch_check(const char* what) {
   return CHEM_OK;
 }
 
+// Resident blocks per SM of the persistent kernel for a launch shape (cached per shape).
+chem_status persistent_blocks_per_sm(chem_handle h, int wpc, int cpb, int& bps) {
+  int& cached = h->bps_cache[wpc - 1][cpb];
+  if (cached == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, forward_kernel(KF_PERSISTENT, wpc),
+                                                                  cpb * wpc * kWarp,
+                                                                  (size_t)cpb * h->cell_bytes);
+    if (e != cudaSuccess) { cached = 0; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
+    cached = std::max(cached, 1);
+  }
+  bps = cached;
+  return CHEM_OK;
+}
+
+// Defaults and checks of the step-control fields of chem_integrate_opts (tolerances, step limits,
+// method, trace), common to every integrating entry point.
+chem_status tolerance_opts(const chem_integrate_opts& o, int N, IntOpts& io) {
+  io = IntOpts{};
+  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
+  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
+  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
+  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
+  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
+  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
+  io.deadline_ns = 0;
+  io.trace = o.trace;
+  io.trace_cap = o.trace ? o.trace_cap : 0;
+  io.N = N;
+  io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
+  if (o.method < 0 || o.method > 2) return fail(CHEM_EINVAL, "method must be 0 (RODAS3), 1 (ROS2) or 2 (RODAS4)");
+  io.method = o.method;
+  if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
+  if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
+    return fail(CHEM_EINVAL, "non-finite option");
+  return CHEM_OK;
+}
+
+// One integration call's options after defaults and checks, and its launch shape.  Shared by
+// chem_integrate and chem_integrate_noalloc so that the two entry points cannot drift apart.
+struct IntCall {
+  chem_integrate_opts o{};
+  IntOpts io{};
+  unsigned long long budget_ns = 0;
+  int wpc = 1;     // warps per cell
+  int cpb = 1;     // cells per block
+  int grid = 1;    // persistent form: resident blocks on the device
+  int chunk = 1;   // persistent form: cells per queue pull
+};
+
+chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opts, IntCall& c) {
+  chem_integrate_opts& o = c.o;
+  if (opts) o = *opts;
+  chem_status st = tolerance_opts(o, N, c.io);
+  if (st != CHEM_OK) return st;
+  if (o.mode != 0 && o.mode != 1) return fail(CHEM_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
+  if (o.warps_per_cell < 0 || o.warps_per_cell > kMaxWarpsPerCell)
+    return fail(CHEM_EINVAL, "warps_per_cell must be 0 (automatic), 1 or 2");
+  if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  c.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
+  c.wpc = o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc;
+  c.cpb = cells_per_block(h, o.block_cells, c.wpc);
+  int bps = 1;
+  if ((st = persistent_blocks_per_sm(h, c.wpc, c.cpb, bps)) != CHEM_OK) return st;
+  c.grid = h->num_sms * bps;
+  // a pull larger than an even share of the cells over the resident lane groups only leaves groups idle
+  const long long groups = (long long)c.grid * c.cpb;
+  const long long share = std::max(1LL, ((long long)N + groups - 1) / groups);
+  c.chunk = (int)std::min<long long>(o.chunk > 0 ? o.chunk : 1, share);
+  return CHEM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -544,7 +395,8 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
   if (device < 0 || device >= ndev) return fail(CHEM_EINVAL, "device index out of range");
-  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  DeviceScope ds;
+  if ((e = ds.enter(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   chem_handle h = new (std::nothrow) chem_handle_s();
   if (!h) return fail(CHEM_ENOMEM, "host allocation failed");
   h->device = device;
@@ -647,7 +499,8 @@ chem_status chem_create_from_json(const char* json_text, int device, chem_handle
 chem_status chem_destroy(chem_handle h) {
   if (!h) return CHEM_OK;
   if (h->device < 0) { delete h; return CHEM_OK; }
-  cudaSetDevice(h->device);
+  DeviceScope ds;
+  ds.enter(h->device);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->blob) cudaFree(h->blob);
@@ -674,7 +527,8 @@ chem_status chem_info(chem_handle h, chem_info_t* info) {
   for (int w = 0; w < kMaxWarpsPerCell; ++w) { info->max_block_cells[w] = 0; info->resident_cells[w] = 0; }
   info->auto_warps_per_cell = 0;
   if (h->device >= 0) {
-    chem_status st = check_handle(h);
+    DeviceScope ds;
+    chem_status st = check_handle(h, ds);
     if (st == CHEM_OK) st = set_attrs(h);
     if (st != CHEM_OK) return st;
     for (int w = 0; w < kMaxWarpsPerCell; ++w) {
@@ -727,7 +581,8 @@ chem_status chem_export_plan(chem_handle h, int which, int* out, int* count) {
 
 chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, const double* Y, double* dTdt,
                        double* dYdt, double* wdot, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
   if (N == 0) return CHEM_OK;
@@ -741,7 +596,8 @@ chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, c
 
 chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p, const double* Y, double* S_vals,
                           double* u, double* v, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
   if (N == 0) return CHEM_OK;
@@ -755,41 +611,22 @@ chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p
 
 chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, double* Y, const double* dt,
                            double* h_io, int* nsub, int* status, const chem_integrate_opts* opts, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
   if (N == 0) return CHEM_OK;
   if (!T || !p || !Y || !dt || !h_io || !nsub || !status) return fail(CHEM_EINVAL, "null array argument");
-  chem_integrate_opts o{};
-  if (opts) o = *opts;
-  IntOpts io;
-  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
-  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
-  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
-  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
-  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
-  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
-  io.deadline_ns = 0;
-  io.trace = o.trace;
-  io.trace_cap = o.trace ? o.trace_cap : 0;
-  io.N = N;
-  io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
-  if (o.method < 0 || o.method > 2) return fail(CHEM_EINVAL, "method must be 0 (RODAS3), 1 (ROS2) or 2 (RODAS4)");
-  io.method = o.method;
-  if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
-  if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
-    return fail(CHEM_EINVAL, "non-finite option");
-  if (o.mode != 0 && o.mode != 1) return fail(CHEM_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
-  if (o.warps_per_cell < 0 || o.warps_per_cell > kMaxWarpsPerCell)
-    return fail(CHEM_EINVAL, "warps_per_cell must be 0 (automatic), 1 or 2");
-  if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
-  if ((st = set_attrs(h)) != CHEM_OK) return st;
-  const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
+  IntCall c;
+  if ((st = parse_integrate(h, N, opts, c)) != CHEM_OK) return st;
+  const chem_integrate_opts& o = c.o;
+  const IntOpts& io = c.io;
+  const unsigned long long budget_ns = c.budget_ns;
   cudaStream_t strm = (cudaStream_t)stream;
   cudaError_t e;
-  const int wpc = o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc;
+  const int wpc = c.wpc;
   const MechView& V = h->view[wpc - 1];
-  const int cpb = cells_per_block(h, o.block_cells, wpc);
+  const int cpb = c.cpb;
   if (o.mode == 0) {
     unsigned long long* stamp = nullptr;
     if (budget_ns) {
@@ -797,15 +634,14 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
       stamp = (unsigned long long*)((char*)h->scratch + kScrStamp);
       k_stamp<<<1, 32, 0, strm>>>(stamp);
     }
-    auto kern = wpc == 1 ? k_integrate_plain<1> : k_integrate_plain<2>;
-    kern<<<(N + cpb - 1) / cpb, cpb * wpc * kWarp, cpb * h->cell_bytes, strm>>>(
-        V, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns);
+    launch_integrate_plain(wpc, (N + cpb - 1) / cpb, cpb * wpc * kWarp, cpb * h->cell_bytes, strm, V, h->L, N, T, p, Y,
+                           dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns);
     return launch_check("chem_integrate launch");
   }
   // persistent mode: sort by previous cost, then one resident grid pulling from the queue; the whole
   // sequence is one CUDA graph, captured once per argument set and replayed on `stream`
   if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
-  const int chunk = o.chunk > 0 ? o.chunk : 1;
+  const int chunk = c.chunk;
   chem_handle_s::GraphKey key{};
   key.N = N; key.mode = 1; key.cpb = cpb; key.chunk = chunk; key.wpc = wpc;
   const void* ptrs[10] = {T, p, Y, dt, h_io, nsub, status, o.naccept, o.trace, h->scratch};
@@ -816,29 +652,23 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamCreate");
-    int bps = 0;
-    auto kern = wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cpb * wpc * kWarp,
-                                                           (size_t)cpb * h->cell_bytes)) != cudaSuccess)
-      return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    bps = std::max(bps, 1);
-    const int grid = std::min(h->num_sms * bps, (N + cpb - 1) / cpb);
+    const int grid = std::min(c.grid, (N + cpb - 1) / cpb);
     char* scr = (char*)h->scratch;
     int* counts = (int*)(scr + kScrCounts);
     int* cursor = (int*)(scr + kScrCursor);
-    int* head = (int*)(scr + kScrHead);
+    unsigned long long* head = (unsigned long long*)(scr + kScrHead);
     unsigned long long* stamp = (unsigned long long*)(scr + kScrStamp);
     int* perm = (int*)(scr + kScrPerm);
     const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
     cudaStream_t cs = h->cap_stream;
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaMemsetAsync(scr, 0, kScrHead + 4, cs);
+    cudaMemsetAsync(scr, 0, kScrHead + 8, cs);
     k_stamp<<<1, 32, 0, cs>>>(stamp);
     k_sort_count<<<sblocks, 256, 0, cs>>>(N, nsub, counts);
     k_sort_scatter<<<sblocks, 256, 0, cs>>>(N, nsub, counts, cursor, perm);
-    kern<<<grid, cpb * wpc * kWarp, cpb * h->cell_bytes, cs>>>(
-        V, h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+    launch_integrate_persistent(wpc, grid, cpb * wpc * kWarp, cpb * h->cell_bytes, cs, V, h->L, N, T, p, Y, dt, h_io,
+                                nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
     cudaGraph_t graph = nullptr;
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &graph);
@@ -856,7 +686,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
 }  // extern "C"
 
 extern "C" chem_status chem_set_params(chem_handle h, const double* dlnA, const double* dEa, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (h->hm.R == 0) return CHEM_OK;
   k_set_params<<<(h->hm.R + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->view[0], h->rxd0, (double*)h->view[0].rxd,
@@ -868,7 +699,8 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
                                     const double* gT, const double* gY, double* grad_lnA, double* grad_Ea,
                                     double* grad_cell, double* gT0, double* gY0, int* status,
                                     const chem_integrate_opts* opts, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
   if (N == 0) return CHEM_OK;
@@ -876,19 +708,10 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
     return fail(CHEM_EINVAL, "null array argument");
   chem_integrate_opts o{};
   if (opts) o = *opts;
-  IntOpts io;
-  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
-  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
-  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
-  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
-  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
-  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
-  io.deadline_ns = 0;
-  io.trace = nullptr;
-  io.trace_cap = 0;
   if (o.method != 0) return fail(CHEM_EINVAL, "chem_adjoint differentiates RODAS3 steps only (method 0)");
-  io.method = 0;
-  io.N = N;
+  o.trace = nullptr;   // the adjoint records its own tape instead
+  IntOpts io;
+  if ((st = tolerance_opts(o, N, io)) != CHEM_OK) return st;
   const int K = o.ckpt_every > 0 ? o.ckpt_every : 16;
   const int cap = o.tape_steps > 0 ? o.tape_steps : 4096;
   if (K > 64) return fail(CHEM_EINVAL, "ckpt_every must be <= 64");
@@ -948,15 +771,15 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   // forward pass with the tape
   io.rec_h = rec_h; io.rec_ck = rec_ck; io.rec_n = rec_n; io.rec_cap = cap; io.rec_K = K;
   if ((e = cudaMemsetAsync(hio, 0, (size_t)N * 8, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  k_integrate_plain<1><<<N, kWarp, h->cell_bytes, strm>>>(h->view[0], h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
-                                                       io, nullptr, 0ull);
+  launch_integrate_plain(1, N, kWarp, h->cell_bytes, strm, h->view[0], h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
+                         io, nullptr, 0ull);
   if ((st = launch_check("chem_adjoint forward launch")) != CHEM_OK) return st;
   // reverse pass, cells ordered by tape length (longest first) as in the sorted work queue
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr;
   if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
   char* scr = (char*)h->scratch;
   int* perm = (int*)(scr + kScrPerm);
-  if ((e = cudaMemsetAsync(scr, 0, kScrHead + 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if ((e = cudaMemsetAsync(scr, 0, kScrHead + 8, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts));
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts), (int*)(scr + kScrCursor), perm);
@@ -997,7 +820,8 @@ chem_status noalloc_scratch_address(int device, char** out) {
 extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, const double* p, double* Y,
                                               const double* dt, double* h_io, int* nsub, int* status,
                                               const chem_integrate_opts* opts, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
   if (N > kNoAllocMaxCells)
@@ -1005,56 +829,30 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
                                  " cells per call (fixed static scratch); got " + std::to_string(N));
   if (N == 0) return CHEM_OK;
   if (!T || !p || !Y || !dt || !h_io || !nsub || !status) return fail(CHEM_EINVAL, "null array argument");
-  chem_integrate_opts o{};
-  if (opts) o = *opts;
-  IntOpts io;
-  io.rtol = o.rtol > 0.0 ? o.rtol : 1e-6;
-  io.atol = o.atol > 0.0 ? o.atol : 1e-12;
-  io.h_init = o.h_init > 0.0 ? o.h_init : 1e-7;
-  io.h_min = o.h_min > 0.0 ? o.h_min : 1e-20;
-  io.max_substeps = o.max_substeps > 0 ? o.max_substeps : 100000;
-  io.max_nonfinite = o.max_nonfinite > 0 ? o.max_nonfinite : 10;
-  io.deadline_ns = 0;
-  io.trace = o.trace;
-  io.trace_cap = o.trace ? o.trace_cap : 0;
-  io.N = N;
-  io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr; io.rec_cap = 0; io.rec_K = 1;
-  if (o.method < 0 || o.method > 2) return fail(CHEM_EINVAL, "method must be 0 (RODAS3), 1 (ROS2) or 2 (RODAS4)");
-  io.method = o.method;
-  if (o.trace && o.trace_cap < 1) return fail(CHEM_EINVAL, "trace_cap must be >= 1 when trace is given");
-  if (!(std::isfinite(io.rtol) && std::isfinite(io.atol) && std::isfinite(io.h_init) && std::isfinite(io.h_min)))
-    return fail(CHEM_EINVAL, "non-finite option");
-  if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
-  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  chem_integrate_opts o1{};
+  if (opts) o1 = *opts;
+  o1.mode = 1;   // always the sorted work queue
+  IntCall c;
+  if ((st = parse_integrate(h, N, &o1, c)) != CHEM_OK) return st;
   char* scr = nullptr;
   if ((st = noalloc_scratch_address(h->device, &scr)) != CHEM_OK) return st;
-  const unsigned long long budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-  if (o.warps_per_cell < 0 || o.warps_per_cell > kMaxWarpsPerCell)
-    return fail(CHEM_EINVAL, "warps_per_cell must be 0 (automatic), 1 or 2");
-  const int wpc = o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc;
-  const int wpb = cells_per_block(h, o.block_cells, wpc);
-  const int chunk = o.chunk > 0 ? o.chunk : 1;
-  int bps = 0;
-  auto kern = wpc == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, wpb * wpc * kWarp,
-                                                                (size_t)wpb * h->cell_bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  bps = std::max(bps, 1);
-  const int grid = std::min(h->num_sms * bps, (N + wpb - 1) / wpb);
+  const int wpc = c.wpc, wpb = c.cpb;
+  const int grid = std::min(c.grid, (N + wpb - 1) / wpb);
   const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
   int* counts = (int*)(scr + kScrCounts);
   int* cursor = (int*)(scr + kScrCursor);
-  int* head = (int*)(scr + kScrHead);
+  unsigned long long* head = (unsigned long long*)(scr + kScrHead);
   unsigned long long* stamp = (unsigned long long*)(scr + kScrStamp);
   int* perm = (int*)(scr + kScrPerm);
   cudaStream_t strm = (cudaStream_t)stream;
+  cudaError_t e;
   // the array keeps the previous call's contents: clear the counters and the queue head first
-  if ((e = cudaMemsetAsync(scr, 0, kScrHead + 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if ((e = cudaMemsetAsync(scr, 0, kScrHead + 8, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   k_stamp<<<1, 32, 0, strm>>>(stamp);
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, nsub, counts);
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, nsub, counts, cursor, perm);
-  kern<<<grid, wpb * wpc * kWarp, wpb * h->cell_bytes, strm>>>(
-      h->view[wpc - 1], h->L, N, T, p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+  launch_integrate_persistent(wpc, grid, wpb * wpc * kWarp, wpb * h->cell_bytes, strm, h->view[wpc - 1], h->L, N, T, p,
+                              Y, dt, h_io, nsub, status, c.o.naccept, perm, head, c.chunk, c.io, stamp, c.budget_ns);
   return launch_check("chem_integrate_noalloc launch");
 }
 
@@ -1266,7 +1064,8 @@ extern "C" chem_status chem_integrate_mapped(chem_handle h, int N, double* T, co
                                              const double* dt, double* h_io, int* nsub, int* status,
                                              const chem_integrate_opts* opts, const chem_map_opts* map, int* ref,
                                              int* n_integrated, chem_stream stream) {
-  chem_status st = check_handle(h);
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
   if (n_integrated) *n_integrated = 0;
   if (N < 0) return fail(CHEM_EINVAL, "N must be >= 0");
@@ -1297,8 +1096,7 @@ extern "C" chem_status chem_integrate_mapped(chem_handle h, int N, double* T, co
       mk.dY[i] = map->dY[i];
     }
   }
-  cudaError_t e = cudaSetDevice(h->device);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  cudaError_t e;
   const size_t need = map_layout(nullptr, N, n).bytes;
   if (h->map_scratch_bytes < need) {
     if (h->map_scratch) cudaFree(h->map_scratch);

@@ -1,0 +1,196 @@
+// kern_forward.cu -- the rate, Jacobian and integration kernels (one lane group per cell).
+#include <cuda_runtime.h>
+
+#include "../../include/chem.h"
+#include "kernels.cuh"
+
+namespace chemgb {
+
+__device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long long* stamp,
+                                                 unsigned long long budget_ns);
+
+// Load one cell's state into y (lanes over state components).
+template <class Gp>
+__device__ __forceinline__ void load_state(double* y, int m, int N, int c, const double* T, const double* Y,
+                                           const Gp& g) {
+  for (int i = g.lane; i < m; i += g.size) y[i] = (i == 0) ? T[c] : Y[(size_t)(i - 1) * N + c];
+  g.sync();
+}
+
+// The lane group of this thread when each cell of a block takes W warps; s = the cell's memory.
+__device__ __forceinline__ void cell_slot(int gs, const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
+  cell_in_block = threadIdx.x / gs;
+  s = smem + (size_t)cell_in_block * L.total;
+}
+template <int W>
+__device__ __forceinline__ GrpW<W> cell_group(const CellLayout& L, double* smem, int& cell_in_block, double*& s);
+template <>
+__device__ __forceinline__ Grp1 cell_group<1>(const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
+  cell_slot(Grp1::size, L, smem, cell_in_block, s);
+  return Grp1{(int)threadIdx.x - cell_in_block * Grp1::size};
+}
+template <>
+__device__ __forceinline__ Grp2 cell_group<2>(const CellLayout& L, double* smem, int& cell_in_block, double*& s) {
+  cell_slot(Grp2::size, L, smem, cell_in_block, s);
+  return Grp2{(int)threadIdx.x - cell_in_block * Grp2::size, 1 + cell_in_block, s + L.misc};
+}
+
+// Block-cooperative coalesced load of the block's consecutive cells: adjacent threads read adjacent
+// cells of the same state row (structure of arrays), then each lane group owns its cell's copy.
+__device__ __forceinline__ void load_tile(double* smem, const CellLayout& L, int m, int N, int c0, int wpb,
+                                          const double* T, const double* Y) {
+  const int total = wpb * m;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = idx / wpb, w = idx - row * wpb;
+    const int c = c0 + w;
+    if (c < N) smem[(size_t)w * L.total + L.y + row] = (row == 0) ? T[c] : Y[(size_t)(row - 1) * N + c];
+  }
+  __syncthreads();
+}
+
+__global__ void k_rates(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
+                        const double* __restrict__ Y, double* __restrict__ dTdt, double* __restrict__ dYdt,
+                        double* __restrict__ wdot) {
+  extern __shared__ double smem[];
+  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int c0 = blockIdx.x * wpb;
+  double* s = smem + (size_t)w * L.total;
+  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
+  const int c = c0 + w;
+  if (c >= N) return;
+  const Grp1 g{lane};
+  double* f = s + L.f0;
+  Scal sc = eval_f<double>(M, s, L, s + L.y, p[c], f, g);
+  for (int i = lane; i < M.m; i += kWarp) {
+    if (i == 0) dTdt[c] = f[0];
+    else dYdt[(size_t)(i - 1) * N + c] = f[i];
+  }
+  if (wdot) {
+    for (int k = lane; k < M.n; k += kWarp) wdot[(size_t)k * N + c] = f[1 + k] * sc.rho * __ldg(M.sp + (size_t)k * SP_STRIDE);
+  }
+}
+
+__global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
+                           const double* __restrict__ Y, double* __restrict__ Sv, double* __restrict__ u,
+                           double* __restrict__ v) {
+  extern __shared__ double smem[];
+  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int c0 = blockIdx.x * wpb;
+  double* s = smem + (size_t)w * L.total;
+  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
+  const int c = c0 + w;
+  if (c >= N) return;
+  eval_jac<double>(M, s, L, s + L.y, p[c], Grp1{lane});
+  for (int e = lane; e < M.nnz_S; e += kWarp) Sv[(size_t)__ldg(M.s_out + e) * N + c] = s[L.S + e];
+  for (int i = lane; i < M.m; i += kWarp) {
+    u[(size_t)i * N + c] = s[L.u + i];
+    v[(size_t)i * N + c] = s[L.v + i];
+  }
+}
+
+// Plain form: one lane group (W warps) per cell, cells in index order, one launch.
+template <int W>
+__global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __restrict__ T, const double* __restrict__ p,
+                                  double* __restrict__ Y, const double* __restrict__ dt, double* __restrict__ h_io,
+                                  int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
+                                  IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
+  extern __shared__ double smem[];
+  const int cpb = blockDim.x / (W * kWarp);
+  int w = 0;
+  double* s = nullptr;
+  const GrpW<W> g = cell_group<W>(L, smem, w, s);
+  const int c0 = blockIdx.x * cpb;
+  load_tile(smem, L, M.m, N, c0, cpb, T, Y);
+  const int c = c0 + w;
+  if (c >= N) return;
+  double h = h_io[c];
+  int ns = 0, na = 0, st = 0;
+  integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, with_deadline(o, stamp, budget_ns), g, c);
+  const double* y = s + L.y;
+  for (int i = g.lane; i < M.m; i += g.size) {
+    if (i == 0) T[c] = y[0];
+    else Y[(size_t)(i - 1) * N + c] = y[i];
+  }
+  if (g.lane == 0) {
+    h_io[c] = h;
+    nsub[c] = ns;
+    status[c] = st;
+    if (nacc_out) nacc_out[c] = na;
+  }
+}
+
+__device__ __forceinline__ IntOpts with_deadline(IntOpts o, const unsigned long long* stamp,
+                                                 unsigned long long budget_ns) {
+  if (budget_ns && stamp) o.deadline_ns = *stamp + budget_ns;
+  return o;
+}
+
+// Persistent form: grid sized to the resident capacity; every warp pulls `chunk` cells at a time from
+// the sorted queue with one atomicAdd and integrates them one after the other.  No block-wide barrier:
+// warps of a block finish independently.
+template <int W>
+__global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* __restrict__ T,
+                                       const double* __restrict__ p, double* __restrict__ Y,
+                                       const double* __restrict__ dt, double* __restrict__ h_io,
+                                       int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
+                                       const int* __restrict__ perm, unsigned long long* __restrict__ head, int chunk,
+                                       IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
+  extern __shared__ double smem[];
+  int w = 0;
+  double* s = nullptr;
+  const GrpW<W> g = cell_group<W>(L, smem, w, s);
+  const IntOpts oo = with_deadline(o, stamp, budget_ns);
+  while (true) {
+    // 64-bit queue head: every pull adds `chunk`, including the last pulls past the end, so a 32-bit
+    // head could wrap for large N * lane groups * chunk
+    const long long base =
+        gbcast(g, g.lane == 0 ? (long long)atomicAdd(head, (unsigned long long)chunk) : 0ll);
+    if (base >= N) break;
+    const int end = (int)min(base + (long long)chunk, (long long)N);
+    for (int j = (int)base; j < end; ++j) {
+      const int c = perm[j];
+      load_state(s + L.y, M.m, N, c, T, Y, g);
+      double h = h_io[c];
+      int ns = 0, na = 0, st = 0;
+      integrate_cell(M, s, L, p[c], dt[c], h, ns, na, st, oo, g, c);
+      const double* y = s + L.y;
+      for (int i = g.lane; i < M.m; i += g.size) {
+        if (i == 0) T[c] = y[0];
+        else Y[(size_t)(i - 1) * N + c] = y[i];
+      }
+      if (g.lane == 0) {
+        h_io[c] = h;
+        nsub[c] = ns;
+        status[c] = st;
+        if (nacc_out) nacc_out[c] = na;
+      }
+      g.sync();
+    }
+  }
+}
+
+
+const void* forward_kernel(ForwardKernel kind, int W) {
+  if (kind == KF_PLAIN) return W == 1 ? (const void*)k_integrate_plain<1> : (const void*)k_integrate_plain<2>;
+  return W == 1 ? (const void*)k_integrate_persistent<1> : (const void*)k_integrate_persistent<2>;
+}
+
+void launch_integrate_plain(int W, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+                            const CellLayout& L, int N, double* T, const double* p, double* Y, const double* dt,
+                            double* h_io, int* nsub, int* status, int* nacc_out, const IntOpts& o,
+                            const unsigned long long* stamp, unsigned long long budget_ns) {
+  auto kern = W == 1 ? k_integrate_plain<1> : k_integrate_plain<2>;
+  kern<<<grid, block, smem, stream>>>(M, L, N, T, p, Y, dt, h_io, nsub, status, nacc_out, o, stamp, budget_ns);
+}
+
+void launch_integrate_persistent(int W, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+                                 const CellLayout& L, int N, double* T, const double* p, double* Y,
+                                 const double* dt, double* h_io, int* nsub, int* status, int* nacc_out,
+                                 const int* perm, unsigned long long* head, int chunk, const IntOpts& o,
+                                 const unsigned long long* stamp, unsigned long long budget_ns) {
+  auto kern = W == 1 ? k_integrate_persistent<1> : k_integrate_persistent<2>;
+  kern<<<grid, block, smem, stream>>>(M, L, N, T, p, Y, dt, h_io, nsub, status, nacc_out, perm, head, chunk, o,
+                                      stamp, budget_ns);
+}
+
+}  // namespace chemgb

@@ -251,3 +251,48 @@ def test_integrate_edge_cases(dev):
     assert np.all(g["status"] == 1) and np.array_equal(g["status"], r["status"])
     assert np.all(g["nsub"] == 3)
     assert np.allclose(g["T"], r["T"], rtol=1e-10)
+
+
+def _lts_regime_cells(m):
+    """224 cells of the 262,144-cell LTS mix (per-cell dt log-uniform 1e-7..1e-3 s), stratified so that
+    cold, burnt and igniting cells each come with dt above and below 1e-4 s, plus 16 igniting cells of
+    the adjoint workload (T0 1000-1400 K, p 1-10 atm) over dt = 1e-3 s, which take 500 to 3,500 steps."""
+    F = synth.field_lts_mix(m, 262144, seed=3)
+    rng = np.random.default_rng(23)
+    big = F.dt > 1e-4
+    pick = []
+    for k, n in ((0, 96), (1, 64), (3, 64)):
+        pick += list(rng.choice(np.where((F.kind == k) & ~big)[0], n // 2, replace=False))
+        pick += list(rng.choice(np.where((F.kind == k) & big)[0], n - n // 2, replace=False))
+    S = F.subset(np.sort(np.array(pick)))
+    G = synth.field_igniting(m, 4096, seed=4, dt=1e-3)
+    Sg = G.subset(np.sort(rng.choice(4096, 16, replace=False)))
+    return synth.Field(np.concatenate([S.T, Sg.T]), np.concatenate([S.p, Sg.p]), np.concatenate([S.Y, Sg.Y], axis=1),
+                       np.concatenate([S.dt, Sg.dt]), np.concatenate([S.kind, Sg.kind]))
+
+
+@pytest.mark.parametrize("wpc", [1, 2])
+def test_sorted_queue_parity_long_dt_regime(dev, wpc):
+    """The sorted work queue (mode 1) against the oracle in the regime of the LTS and adjoint workloads:
+    dt up to 1e-3 s, cold, burnt and igniting cells, with a previous-step cost key that reorders them;
+    one and two warps per cell; same trace-matched criteria as the other integration tests."""
+    m, h, o = mech("mid")
+    F = _lts_regime_cells(m)
+    cap = 4000
+    r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=cap)
+    assert r["nsub"].max() < cap and r["nsub"].max() > 2000
+    N = F.n_cells
+    key = np.random.default_rng(5).integers(0, 3000, N).astype(np.int32)
+    T = to_dev(F.T, dev)
+    Y = to_dev(F.Y.reshape(-1), dev)
+    hio = torch.zeros(N, dtype=torch.float64, device=dev)
+    ns = torch.tensor(key, device=dev)
+    st = torch.zeros(N, dtype=torch.int32, device=dev)
+    tr = torch.zeros(cap * N, dtype=torch.float64, device=dev)
+    h.integrate(T, to_dev(F.p, dev), Y, to_dev(F.dt, dev), hio, ns, st, trace=tr, mode=1, warps_per_cell=wpc,
+                chunk=2)
+    torch.cuda.synchronize()
+    g = dict(T=T.cpu().numpy(), Y=Y.cpu().numpy().reshape(F.Y.shape), h=hio.cpu().numpy(), nsub=ns.cpu().numpy(),
+             status=st.cpu().numpy(), trace=tr.cpu().numpy().reshape(cap, N))
+    assert np.all(g["status"] == 0)
+    _compare_integration(o, g, r, F, 0.1)

@@ -103,3 +103,21 @@ def test_two_warps_per_cell_plain_equals_persistent(mid, dev):
     assert np.all(plain["status"] == 0)
     one = _run(h, F, dev, mode=0, warps_per_cell=1)
     assert np.array_equal(one["status"], plain["status"])
+
+
+def test_calls_leave_the_callers_current_device(dev):
+    """Every entry point runs on its handle's device and puts the caller's current device back."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs: a handle on device 1 called while device 0 is current")
+    m = synth.mechanism_small()
+    h = chem.create(m, 1)
+    torch.cuda.set_device(0)
+    F = synth.field_uniform_random(m, 8, seed=2)
+    d1 = torch.device("cuda", 1)
+    T = torch.tensor(F.T, device=d1)
+    Y = torch.tensor(F.Y.reshape(-1), device=d1)
+    z = lambda dt=torch.float64: torch.zeros(8, dtype=dt, device=d1)
+    h.integrate(T, torch.tensor(F.p, device=d1), Y, torch.tensor(F.dt, device=d1), z(), z(torch.int32),
+                z(torch.int32), mode=1, stream=torch.cuda.current_stream(d1))
+    torch.cuda.synchronize(d1)
+    assert torch.cuda.current_device() == 0

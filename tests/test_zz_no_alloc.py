@@ -36,28 +36,56 @@ def _buffers(F, dev, nsub_in):
                 naccept=torch.zeros(N, dtype=torch.int32, device=dev))
 
 
-def _call(h, F, dev, nsub_in, noalloc):
+def _call(h, F, dev, nsub_in, noalloc, trace_cap=0, **kw):
     b = _buffers(F, dev, nsub_in)
+    if trace_cap:
+        b["trace"] = torch.zeros(trace_cap * F.n_cells, dtype=torch.float64, device=dev)
     fn = h.integrate_noalloc if noalloc else (lambda *a, **k: h.integrate(*a, mode=1, **k))
-    fn(b["T"], b["p"], b["Y"], b["dt"], b["h_io"], b["nsub"], b["status"], naccept=b["naccept"])
+    fn(b["T"], b["p"], b["Y"], b["dt"], b["h_io"], b["nsub"], b["status"], naccept=b["naccept"],
+       trace=b.get("trace"), **kw)
     torch.cuda.synchronize()
-    return {k: b[k].cpu().numpy() for k in ("T", "Y", "h_io", "nsub", "status", "naccept")}
+    return {k: b[k].cpu().numpy() for k in ("T", "Y", "h_io", "nsub", "status", "naccept", "trace") if k in b}
 
 
-def test_noalloc_matches_persistent_entry_point_on_two_calls(dev):
-    m = synth.mechanism_methane_sized()
-    h = chem.create(m, 0)
-    F = synth.field_lts_mix(m, 2500, seed=17, dt_range=(1e-7, 1e-4))
+_mid = {}
+
+
+def _mid_handle():
+    if not _mid:
+        m = synth.mechanism_methane_sized()
+        _mid["m"], _mid["h"] = m, chem.create(m, 0)
+        _mid["F"] = synth.field_lts_mix(m, 2500, seed=17, dt_range=(1e-7, 1e-4))
+    return _mid["m"], _mid["h"], _mid["F"]
+
+
+@pytest.mark.parametrize("wpc,chunk,method", [(1, 1, 0), (1, 4, 0), (2, 1, 0), (2, 4, 0), (1, 4, 2), (2, 1, 2)])
+def test_noalloc_matches_persistent_entry_point_on_two_calls(dev, wpc, chunk, method):
+    """One and two warps per cell, one and four cells per queue pull, RODAS3 and RODAS4, with the step trace
+    on: the second call of each pair finds the first call's data in the static array."""
+    m, h, F = _mid_handle()
+    kw = dict(warps_per_cell=wpc, chunk=chunk, method=method, trace_cap=400)
     zeros = np.zeros(F.n_cells, dtype=np.int32)
-    ref1 = _call(h, F, dev, zeros, noalloc=False)
-    ref2 = _call(h, F, dev, ref1["nsub"], noalloc=False)       # second flow step: sorted by the counts
-    got1 = _call(h, F, dev, zeros, noalloc=True)
-    got2 = _call(h, F, dev, got1["nsub"], noalloc=True)        # the static array still holds call 1's data
+    ref1 = _call(h, F, dev, zeros, noalloc=False, **kw)
+    ref2 = _call(h, F, dev, ref1["nsub"], noalloc=False, **kw)       # second flow step: sorted by the counts
+    got1 = _call(h, F, dev, zeros, noalloc=True, **kw)
+    got2 = _call(h, F, dev, got1["nsub"], noalloc=True, **kw)        # the static array holds call 1's data
     for ref, got in ((ref1, got1), (ref2, got2)):
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k
-    assert np.all(got2["status"] == 0)
     assert len(np.unique(ref1["nsub"])) > 5
+    assert np.all(got2["status"] == 0)
+
+
+def test_noalloc_and_persistent_accept_the_largest_chunk(dev):
+    """chunk = INT_MAX is reduced to an even share of the cells per lane group: same results as chunk 1."""
+    m, h, F = _mid_handle()
+    S = F.subset(np.arange(600))
+    zeros = np.zeros(S.n_cells, dtype=np.int32)
+    base = _call(h, S, dev, zeros, noalloc=False, chunk=1)
+    for noalloc in (False, True):
+        got = _call(h, S, dev, zeros, noalloc=noalloc, chunk=2**31 - 1)
+        for k in base:
+            assert np.array_equal(base[k], got[k]), (noalloc, k)
 
 
 def test_noalloc_takes_no_device_memory_per_call(dev):

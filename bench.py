@@ -550,7 +550,10 @@ def main():
     if kernel_sources_digest() == PROFILED_SOURCES and args.workload in PROFILED_TRAFFIC_PER_CELL:
         traffic = PROFILED_TRAFFIC_PER_CELL[args.workload] * N
 
-    e2e = run.e2e(1 if args.mode == "persistent" else 0, max(1, min(args.steps, 3)))
+    # end to end over the same flow steps as the first timed ones (an evolving field's steps 2-10 differ in
+    # cost; a restored field's steps are all alike, three of them suffice)
+    e2e = run.e2e(1 if args.mode == "persistent" else 0,
+                  max(1, min(args.steps, EPISODE - 1)) if evolving else max(1, min(args.steps, 3)))
 
     mapped = None
     if args.map_tmax > 0 and not evolving:

@@ -70,6 +70,12 @@ WORKLOADS = {
     "large": {"workload": "large 150sp/1000rxn, 131072-cell bimodal jet field (512x256), per-cell dt "
                           "log-uniform 1e-6..1e-4 s",
               "n_cells": 131072, "evolving": False},
+    "small": {"workload": "small 10sp/27rxn (H, O, N), 1024 cells, p = 1 atm, T uniform 900-2200 K, Dirichlet Y, "
+                          "dt=1e-5 s",
+              "n_cells": 1024, "evolving": False},
+    "small64k": {"workload": "small 10sp/27rxn (H, O, N), 65536 cells drawn like the 1024-cell case (p = 1 atm, "
+                             "T uniform 900-2200 K, Dirichlet Y, dt=1e-5 s)",
+                 "n_cells": 65536, "evolving": False},
 }
 
 
@@ -87,6 +93,9 @@ def workload(name="lts", seed_offset=0):
     elif name == "large":
         m = synth.mechanism_large()
         F = synth.field_bimodal_jet(m, 512, 256, seed=5 + seed_offset, dt_range=(1e-6, 1e-4))
+    elif name in ("small", "small64k"):
+        m = synth.mechanism_small()
+        F = synth.field_uniform_random(m, WORKLOADS[name]["n_cells"], seed=1 + seed_offset)
     else:
         raise ValueError(name)
     return m, F
@@ -338,9 +347,10 @@ def run_reference(args):
 class Runner:
     """Timed chem_integrate steps on one workload: buffers, the step schedule and the work counts."""
 
-    def __init__(self, h, F, evolving, dev, meth, oc, world, flush, clocks_path, local):
+    def __init__(self, h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, cells_per_warp=0):
         import torch
         self.h, self.F, self.evolving, self.dev, self.meth, self.oc = h, F, evolving, dev, meth, oc
+        self.cpw = cells_per_warp
         self.world, self.flush, self.clocks_path, self.local = world, flush, clocks_path, local
         N = F.n_cells
         self.N = N
@@ -367,7 +377,7 @@ class Runner:
 
     def integrate(self, mode):
         self.h.integrate(self.T, self.P, self.Y, self.DT, self.hio, self.ns, self.st, rtol=RTOL, atol=ATOL,
-                         mode=mode, naccept=self.nacc, method=self.meth)
+                         mode=mode, naccept=self.nacc, method=self.meth, cells_per_warp=self.cpw)
 
     def step(self, mode):
         """One flow step.  Evolving: the next step of the episode.  Otherwise: from the initial state again,
@@ -466,7 +476,7 @@ class Runner:
             self.P.copy_(Ph, non_blocking=True)
             self.DT.copy_(Dh, non_blocking=True)
             self.h.integrate(self.T, self.P, self.Y, self.DT, self.hio, self.ns, self.st, rtol=RTOL, atol=ATOL,
-                             mode=mode, method=self.meth)
+                             mode=mode, method=self.meth, cells_per_warp=self.cpw)
             To.copy_(self.T, non_blocking=True)
             Yo.copy_(self.Y, non_blocking=True)
             Ho.copy_(self.hio, non_blocking=True)
@@ -502,6 +512,8 @@ def main():
                     help="also time chem_integrate_mapped with cells below this temperature mapped (0: off)")
     ap.add_argument("--method", default="rodas3", choices=list(METHODS),
                     help="Rosenbrock method of the forward integration (the headline is RODAS3)")
+    ap.add_argument("--cells-per-warp", type=int, default=0, choices=[0, 1, 2],
+                    help="2: two cells share a warp (16 lanes each); 1: one cell per warp; 0: the library's choice")
     args = ap.parse_args()
     global RTOL
     RTOL = args.rtol
@@ -530,7 +542,7 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     import tempfile
     clocks_path = os.path.join(tempfile.gettempdir(), f"chem_bench_clocks_r{rank}_{os.getpid()}.csv")
-    run = Runner(h, F, evolving, dev, meth, oc, world, flush, clocks_path, local)
+    run = Runner(h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, args.cells_per_warp)
 
     # headline mode first (W warm-up, K timed), then the other mode on the first K' of the same steps:
     # for an evolving field, the first episode's steps 2-10 (bit-identical states in both modes)
@@ -563,7 +575,7 @@ def main():
     if args.workload == "lts" and not args.no_secondary and not args.cells and args.method == "rodas3":
         secondary = jet_key(h, dev, meth, oc, world, flush, clocks_path, local, rank)
     adj = None
-    if not args.no_adjoint and not args.cells and args.method == "rodas3":
+    if not args.no_adjoint and not args.cells and args.method == "rodas3" and args.workload in ("lts", "jet", "large"):
         Fa, label = adjoint_fields(args.workload, m, F)
         adj = adjoint_bench(h, m, dev, Fa, label)
     if rank != 0:
@@ -577,7 +589,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(config(args.workload, args.mode), n_cells=N,
-                       warps_per_cell=int(h.info["auto_warps_per_cell"]), method=args.method),
+                       warps_per_cell=int(h.info["auto_warps_per_cell"]), method=args.method,
+                       cells_per_warp=args.cells_per_warp or int(h.info["auto_cells_per_warp"])),
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

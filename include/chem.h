@@ -114,11 +114,13 @@ typedef struct {
   int jac_passes;     /* passes of the Jacobian's reaction loop (their scratch shares the factor's space) */
   int smem_adjoint_per_cell;  /* bytes of shared memory one cell needs in chem_adjoint's reverse pass
                                  (checkpoint interval 16) */
-  /* launch limits on the handle's device (0 for host-only handles), per warps-per-cell choice [1, 2]:
-     the largest block in cells, the most cells resident per SM, and the library's automatic choice */
-  int max_block_cells[2];
-  int resident_cells[2];
+  /* launch limits on the handle's device (0 for host-only handles), per lane group [one warp per cell,
+     two warps per cell, two cells per warp]: the largest block in cells, the most cells resident per SM,
+     and the library's automatic choices */
+  int max_block_cells[3];
+  int resident_cells[3];
   int auto_warps_per_cell;
+  int auto_cells_per_warp;
 } chem_info_t;
 
 /* Options of chem_integrate (zero-initialise, then set; zero/negative fields take the defaults). */
@@ -157,6 +159,12 @@ typedef struct {
                              gamma = 1 + 1/sqrt(2)), 2 RODAS4 (Hairer and Wanner, Sec. VI.4; 6 stages,
                              order 4, embedded order 3, stiffly accurate, L-stable, gamma = 1/4; same
                              shared memory per cell as RODAS3).  Other values: CHEM_EINVAL. */
+  int cells_per_warp;     /* chem_integrate and chem_integrate_noalloc: 2 = two cells share a warp, 16 lanes
+                             each (for mechanisms with few species, whose loops and sparse programs leave
+                             most of a warp idle; needs warps_per_cell 0 or 1; block_cells is rounded to
+                             an even count; in mode 1 the two halves of a warp take consecutive cells of the
+                             sorted queue); 1 = one cell per warp (or per two warps); 0: automatic (see
+                             chem_info).  Results agree with one warp per cell to rounding. */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,
@@ -194,7 +202,8 @@ chem_status chem_jacobian_pattern(chem_handle h, int* row_ptr, int* col_idx);
      5 internal S entry -> CSR position of chem_jacobian_pattern (nnz_S);
      6 transposed substitution program (A^T x = b), same encoding as 1;
      7 compiled reaction order: description index of each compiled reaction (R);
-     8, 9, 10 the programs of 0, 1 and 6 for two warps per cell: 64 lane-ops per step.
+     8, 9, 10 the programs of 0, 1 and 6 for two warps per cell: 64 lane-ops per step;
+     11, 12, 13 the programs of 0, 1 and 6 for two cells per warp: 16 lane-ops per step.
    With out == NULL only *count is written.  *count: number of ints. */
 chem_status chem_export_plan(chem_handle h, int which, int* out, int* count);
 

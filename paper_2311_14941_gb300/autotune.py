@@ -1,9 +1,11 @@
 """Launch-shape autotuner for chem_integrate.
 
 Knobs searched:
-  warps_per_cell  1 (one warp integrates a cell) or 2 (two warps of a block share it: wider reaction and
-                  species loops and twice the warps in flight, at the price of more, emptier steps in the
-                  sparse factorisation and solves and of named-barrier synchronisation)
+  lane group      (warps_per_cell, cells_per_warp): (1, 1) one warp integrates a cell; (2, 1) two warps of
+                  a block share it (wider reaction and species loops and twice the warps in flight, at the
+                  price of more, emptier steps in the sparse factorisation and solves and of named-barrier
+                  synchronisation); (1, 2) two cells share a warp, 16 lanes each (mechanisms with few
+                  species, whose loops and sparse programs leave most of a warp idle)
   mode            0 = one grid over all cells, 1 = cells sorted by their previous substep count and
                   pulled by resident lane groups from an atomic queue (the on-chip form of the paper's
                   dynamic load balancing, Sec. 2.5)
@@ -11,7 +13,7 @@ Knobs searched:
                   share an SM
   chunk           cells a group claims per queue operation (mode 1)
 
-The search is staged (coordinate descent): warps per cell with the library's default block shape and
+The search is staged (coordinate descent): the lane group with the library's default block shape and
 the sorted queue; then cells per block and queue chunk for that choice; then the plain grid with the
 best block shape against the best queue.  Every run integrates the same sample of the caller's cells,
 starting from the same state, once untimed and then timed with CUDA events on the caller's stream.  The
@@ -31,7 +33,8 @@ import numpy as np
 from . import build as _build
 
 CACHE = os.path.join(_build.OUT, "autotune_cache.json")
-KEYS = ("warps_per_cell", "mode", "block_cells", "chunk")
+KEYS = ("warps_per_cell", "cells_per_warp", "mode", "block_cells", "chunk")
+GROUPS = ((1, 1), (2, 1), (1, 2))   # (warps_per_cell, cells_per_warp), in the order of chem_info's arrays
 
 
 def mechanism_digest(desc) -> str:
@@ -52,17 +55,22 @@ def max_block_cells(cell_bytes: int, smem_optin: int, warps_per_cell: int) -> in
     return max(1, c)
 
 
-def block_shapes(max_cells: int):
+def block_shapes(max_cells: int, cells_per_warp: int = 1):
+    if cells_per_warp == 2:   # half-warp cells come in pairs (whole warps)
+        return sorted({c for c in (2, 4, 8, max_cells - max_cells % 2) if 2 <= c <= max_cells})
     return sorted({c for c in (1, 2, 4, max_cells) if c <= max_cells})
 
 
 def candidates(max_cells: dict):
-    """The full launch-shape space; max_cells[w] = largest block (in cells) for w warps per cell."""
+    """The full launch-shape space; max_cells[g] = largest block (in cells) for lane group g = (warps per
+    cell, cells per warp)."""
     out = []
-    for wpc in sorted(max_cells):
-        shapes = block_shapes(max_cells[wpc])
-        out += [dict(warps_per_cell=wpc, mode=0, block_cells=c, chunk=1) for c in shapes]
-        out += [dict(warps_per_cell=wpc, mode=1, block_cells=c, chunk=k) for c in shapes for k in (1, 2, 4)]
+    for g in sorted(max_cells):
+        wpc, cpw = g
+        shapes = block_shapes(max_cells[g], cpw)
+        out += [dict(warps_per_cell=wpc, cells_per_warp=cpw, mode=0, block_cells=c, chunk=1) for c in shapes]
+        out += [dict(warps_per_cell=wpc, cells_per_warp=cpw, mode=1, block_cells=c, chunk=k) for c in shapes
+                for k in (1, 2, 4)]
     return out
 
 
@@ -104,8 +112,8 @@ def _store(key, value):
 
 def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int = 8192, use_cache: bool = True,
          repeats: int = 1, stream=None):
-    """Best launch shape for integrating these cells; returns {warps_per_cell, mode, block_cells, chunk, ms,
-    sample, table}.
+    """Best launch shape for integrating these cells; returns {warps_per_cell, cells_per_warp, mode,
+    block_cells, chunk, ms, sample, table}.
 
     T, p, dt: device tensors [N]; Y: [n*N] species-major; nsub_prev: previous substep counts (device or
     host, may be None).  The inputs are not modified."""
@@ -126,7 +134,7 @@ def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int =
     ns0 = torch.zeros(len(idx), dtype=torch.int32, device=T.device) if ns_host is None else \
         torch.as_tensor(ns_host[idx].astype(np.int32), device=T.device)
     info = mech.info
-    maxc = {w: int(info["max_block_cells"][w - 1]) for w in (1, 2)}
+    maxc = {g: int(info["max_block_cells"][i]) for i, g in enumerate(GROUPS)}
     strm = stream or torch.cuda.current_stream(T.device)
     Tw, Yw = torch.empty_like(Ts), torch.empty_like(Ys)
     hio = torch.empty(len(idx), dtype=torch.float64, device=T.device)
@@ -153,18 +161,18 @@ def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int =
         table.append(row)
         return row
 
-    # 1) warps per cell, library default block shape, sorted queue
-    best = min((timed(dict(warps_per_cell=w, mode=1, block_cells=0, chunk=1)) for w in (1, 2)),
-               key=lambda d: d["ms"])
-    w = best["warps_per_cell"]
+    # 1) lane group, library default block shape, sorted queue
+    best = min((timed(dict(warps_per_cell=w, cells_per_warp=cpw, mode=1, block_cells=0, chunk=1))
+                for w, cpw in GROUPS), key=lambda d: d["ms"])
+    w, cpw = best["warps_per_cell"], best["cells_per_warp"]
     # 2) block shape and chunk for that choice
-    for c in block_shapes(maxc[w]):
+    for c in block_shapes(maxc[(w, cpw)], cpw):
         for k in (1, 2, 4):
-            row = timed(dict(warps_per_cell=w, mode=1, block_cells=c, chunk=k))
+            row = timed(dict(warps_per_cell=w, cells_per_warp=cpw, mode=1, block_cells=c, chunk=k))
             if row["ms"] < best["ms"]:
                 best = row
     # 3) the plain grid with that block shape
-    row = timed(dict(warps_per_cell=w, mode=0, block_cells=best["block_cells"], chunk=1))
+    row = timed(dict(warps_per_cell=w, cells_per_warp=cpw, mode=0, block_cells=best["block_cells"], chunk=1))
     if row["ms"] < best["ms"]:
         best = row
     out = dict({k: best[k] for k in KEYS}, ms=best["ms"], sample=int(len(idx)), table=table)
@@ -174,5 +182,6 @@ def tune(mech, T, p, Y, dt, nsub_prev=None, rtol=1e-6, atol=1e-12, sample: int =
 
 
 def launch_options(result) -> dict:
-    """The chem_integrate keyword arguments of a `tune` result."""
-    return {k: int(result[k]) for k in KEYS}
+    """The chem_integrate keyword arguments of a `tune` result (results cached before the lane-group
+    choice existed mean one cell per warp)."""
+    return {k: int(result.get(k, 1)) for k in KEYS}

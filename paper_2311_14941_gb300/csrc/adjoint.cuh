@@ -22,16 +22,23 @@
 
 namespace chemgb {
 
+// Memory of the reverse pass.  Shared memory holds the forward cell layout L only (the factor shares
+// its region with the Jacobian's pass scratch, as in the integrator), so as many warps per SM fit as
+// for the forward pass.  Everything else of a warp lives in its own slice of global memory (offsets in
+// doubles below), read and written lane-strided, except the copies of the step's factor and Jacobian,
+// which the transposed solves and the last product with J(y)^T read by index.
 struct AdjLayout {
-  CellLayout L;        // base workspace (factor kept apart from the derivative slots)
-  int Y3, Y4, AU1, AU2, AU3, AU4, W1, W2, W3, W4, MU1, MU2, MU3, MU4, LAM, G, ZT, WS;   // m-vectors
-  int SY, UY, VY;      // S, u, v at y (the step's own Jacobian)
-  int A;               // n: participant coefficients of the parameter terms
-  int total;
+  CellLayout L;        // shared memory: the forward layout
+  int Y3, Y4, W1, W2, W3, W4, MU1, MU2, MU3, MU4, LAM, G, ZT, WS, UY, VY, HY;   // m-vectors (HY: h/RT at y)
+  int SY;              // nnz_S: S at y (the step's own Jacobian)
+  int QY;              // R: rates of progress at y
+  int LUG;             // nnz_LU + m: the step's factor and its reciprocal pivots
+  int SC;              // 8: T, rho, c_p, 1/rho at y
+  int UST;             // K * 4m: U1..U4 of every step of the current segment
+  int SEG;             // K * m: the segment's states
+  int GA, GE;          // R each: the cell's gradient accumulators (compiled reaction order)
+  int total;           // doubles per warp
 };
-// Per-warp global memory of the reverse pass (touched once per step, so kept out of shared memory):
-// the recomputed states of one segment (K*m) and the cell's gradient accumulators (2R, compiled
-// reaction order).
 
 // out = J^T w = S^T w + v (u . w) with S in the internal entry order
 template <class Sc>
@@ -50,36 +57,33 @@ __device__ __forceinline__ void vjp(const MechView& M, const Sc* S, const Sc* u,
   g.sync();
 }
 
-__device__ __forceinline__ void acc_theta(double& g, double c) { g += c; }
-__device__ __forceinline__ void acc_theta(double& g, const Dual& c) { g += c.d; }
-
-// dL/dtheta += w^T f_theta at the evaluated state (value part for double, tangent part for Dual):
-// for reaction r, q_r * E_r with E_r = sum_products a_k - sum_reactants a_k.
-template <class Sc>
-__device__ __forceinline__ void theta_terms(const MechView& M, const Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
-                                            const double* w, Sc* a, double* GA, double* GE, const Grp1& g) {
-  const Sc c1 = (w[0] * kRu) * sc.T / (sc.rho * sc.cp);
+// dL/dtheta += w^T f_theta at an evaluated state: for reaction r, q_r * E_r with E_r = sum_products a_k -
+// sum_reactants a_k, a_k = W_k w_k / rho - w_T H_k / (rho c_p).  hRT, q: the evaluation's h/RT and rates
+// of progress; a: n doubles of scratch (shared memory, read by index).
+__device__ __forceinline__ void theta_terms(const MechView& M, const double* hRT, const double* q, double T,
+                                            double rho, double cp, double irho, const double* w, double* a,
+                                            double* GA, double* GE, const Grp1& g) {
+  const double c1 = (w[0] * kRu) * T / (rho * cp);
   for (int k = g.lane; k < M.n; k += g.size)
-    a[k] = sfma(Sc(__ldg(M.sp + (size_t)k * SP_STRIDE + 1) * w[1 + k]), sc.irho, -(c1 * s[L.hRT + k]));
+    a[k] = fma(__ldg(M.sp + (size_t)k * SP_STRIDE + 1) * w[1 + k], irho, -(c1 * hRT[k]));
   g.sync();
-  const Sc iRT = 1.0 / (kRu * sc.T);
+  const double iRT = 1.0 / (kRu * T);
   for (int r = g.lane; r < M.R; r += g.size) {
     const int* I = M.rxi + (size_t)r * RX_I;
     const int nro = __ldg(I + 2), npo = __ldg(I + 3);
-    Sc E = Sc(0.0);
+    double E = 0.0;
     for (int i = 0; i < npo; ++i) E += a[__ldg(I + 7 + i)];
     for (int i = 0; i < nro; ++i) E -= a[__ldg(I + 4 + i)];
-    const Sc qE = s[L.q + r] * E;
-    acc_theta(GA[r], qE);
-    acc_theta(GE[r], -(qE * iRT));
+    const double qE = q[r] * E;
+    GA[r] += qE;
+    GE[r] += -(qE * iRT);
   }
   g.sync();
 }
 
-// x <- A^-T x (transposed substitution with the same factor)
-__device__ __forceinline__ void lu_solveT(const MechView& M, const double* s, const CellLayout& L, double* x, const Grp1& g) {
-  const double* LU = s + L.LU;
-  const double* dinv = s + L.dinv;
+// x <- A^-T x (transposed substitution with the factor LU, dinv; x in shared memory)
+__device__ __forceinline__ void lu_solveT(const MechView& M, const double* LU, const double* dinv, double* x,
+                                          const Grp1& g) {
   const ElimOp* op = M.svT_ops + g.lane;
   for (int st = 0; st < M.svT_steps; ++st, op += g.size) {
     const ElimOp o = ld_eop(op);
@@ -92,11 +96,9 @@ __device__ __forceinline__ void lu_solveT(const MechView& M, const double* s, co
 }
 
 // x <- M^-T x with M^T = A^T - v u^T:  x = A^-T x + zt (u . A^-T x) / (1 - u . zt),  zt = A^-T v
-__device__ __forceinline__ void smT_solve(const MechView& M, const double* s, const AdjLayout& A, double* x,
-                                          double idenT, const Grp1& g) {
-  lu_solveT(M, s, A.L, x, g);
-  const double* u = s + A.UY;
-  const double* zt = s + A.ZT;
+__device__ __forceinline__ void smT_solve(const MechView& M, const double* LU, const double* dinv, const double* u,
+                                          const double* zt, double* x, double idenT, const Grp1& g) {
+  lu_solveT(M, LU, dinv, x, g);
   double d = 0.0;
   for (int i = g.lane; i < M.m; i += g.size) d = fma(u[i], x[i], d);
   d = gsum(g, d) * idenT;
@@ -196,75 +198,66 @@ __device__ __forceinline__ void second_order_terms(const MechView& M, Dual4* dw,
   theta_tangents(M, dw, Ld, scd, Ws, reinterpret_cast<Dual*>(dw + Ld.z), GA, GE, g);
 }
 
-// One adjoint step at state y (a row of the segment) with step h.  lambda (A.LAM) is updated in place,
-// the parameter gradients accumulate into GA, GE.  Returns false if the factor is singular (cannot
-// happen for a step the forward pass accepted).
-__device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const AdjLayout& A, Dual4* dw,
-                                             const CellLayout& Ld, const double* y, double p, double h,
-                                             double* GA, double* GE, const Grp1& g) {
+// One adjoint step at state y with step h, whose stage vectors U1..U4 the segment recompute kept.
+// lambda (A.LAM) is updated in place, the parameter gradients accumulate into GA, GE.  Returns false if
+// the factor is singular (cannot happen for a step the forward pass accepted).
+__device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, double* ws, const AdjLayout& A, Dual4* dw,
+                                             const double* y, const double* U1, const double* U2, const double* U3,
+                                             const double* U4, double p, double h, double* GA, double* GE,
+                                             const Grp1& g) {
   const CellLayout& L = A.L;
   const int m = M.m;
   const double ih = 1.0 / h;
-  double* U1 = s + A.AU1; double* U2 = s + A.AU2; double* U3 = s + A.AU3; double* U4 = s + A.AU4;
-  double* W1 = s + A.W1; double* W2 = s + A.W2; double* W3 = s + A.W3; double* W4 = s + A.W4;
-  double* MU1 = s + A.MU1; double* MU2 = s + A.MU2; double* MU3 = s + A.MU3; double* MU4 = s + A.MU4;
-  double* LAM = s + A.LAM; double* G = s + A.G; double* Y3 = s + A.Y3; double* Y4 = s + A.Y4;
-  // ---- forward quantities of the step (same arithmetic as the forward attempt)
+  double* W1 = ws + A.W1; double* W2 = ws + A.W2; double* W3 = ws + A.W3; double* W4 = ws + A.W4;
+  double* MU1 = ws + A.MU1; double* MU2 = ws + A.MU2; double* MU3 = ws + A.MU3; double* MU4 = ws + A.MU4;
+  double* LAM = ws + A.LAM; double* G = ws + A.G; double* Y3 = ws + A.Y3; double* Y4 = ws + A.Y4;
+  double* UY = ws + A.UY; double* VY = ws + A.VY; double* ZT = ws + A.ZT;
+  double* LUg = ws + A.LUG;
+  double* dinvg = LUg + M.nnz_LU;
+  double* X = s + L.U3;      // shared scratch of the transposed solves
+  double* a = s + L.ytmp;    // shared scratch of the parameter terms (n <= m)
+  // ---- the step's Jacobian at y and its factor (same arithmetic as the forward attempt); keep what the
+  //      end of the step needs: S, u, v, q, h/RT and the mixture scalars at y
   vset(s + L.y, y, m, g);
-  eval_jac<double>(M, s, L, s + L.y, p, g);
-  vset(s + A.SY, s + L.S, M.nnz_S, g);
-  vset(s + A.UY, s + L.u, m, g);
-  vset(s + A.VY, s + L.v, m, g);
+  const ScalT<double> sy = eval_jac<double>(M, s, L, s + L.y, p, g);
+  vset(ws + A.SY, s + L.S, M.nnz_S, g);
+  vset(UY, s + L.u, m, g);
+  vset(VY, s + L.v, m, g);
+  vset(ws + A.QY, s + L.q, M.R, g);
+  vset(ws + A.HY, s + L.hRT, M.n, g);
+  if (g.lane == 0) {
+    ws[A.SC] = sy.T; ws[A.SC + 1] = sy.rho; ws[A.SC + 2] = sy.cp; ws[A.SC + 3] = sy.irho;
+  }
   if (!lu_build_factor(M, s, L, ih * (1.0 / RG), g)) return false;
-  double* z = s + L.z;
-  const double* u = s + A.UY;
-  const double* v = s + A.VY;
-  const double* f0 = s + L.f0;
-  for (int i = g.lane; i < m; i += g.size) { z[i] = u[i]; U1[i] = f0[i]; }
-  g.sync();
-  lu_solve_impl<true>(M, s, L, z, U1, g);
-  double vz = 0.0, vx = 0.0;
-  for (int i = g.lane; i < m; i += g.size) { vz = fma(v[i], z[i], vz); vx = fma(v[i], U1[i], vx); }
-  vz = gsum(g, vz);
-  vx = gsum(g, vx);
-  const double iden = 1.0 / (1.0 - vz);
-  vx *= iden;
-  for (int i = g.lane; i < m; i += g.size) U1[i] = fma(z[i], vx, U1[i]);
-  g.sync();
-  for (int i = g.lane; i < m; i += g.size) U2[i] = fma(C21 * ih, U1[i], f0[i]);
-  g.sync();
-  sm_solve(M, s, L, U2, iden, g);
-  for (int i = g.lane; i < m; i += g.size) Y3[i] = fma(A31, U1[i], y[i]);
-  g.sync();
-  eval_f<double>(M, s, L, Y3, p, U3, g);
-  for (int i = g.lane; i < m; i += g.size) U3[i] = fma(ih, fma(C31, U1[i], C32 * U2[i]), U3[i]);
-  g.sync();
-  sm_solve(M, s, L, U3, iden, g);
-  for (int i = g.lane; i < m; i += g.size) Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
-  g.sync();
-  eval_f<double>(M, s, L, Y4, p, U4, g);
-  for (int i = g.lane; i < m; i += g.size) U4[i] = fma(ih, fma(C41, U1[i], fma(C42, U2[i], C43 * U3[i])), U4[i]);
-  g.sync();
-  sm_solve(M, s, L, U4, iden, g);
-  // transposed Sherman-Morrison vector
-  double* zt = s + A.ZT;
-  vset(zt, v, m, g);
-  lu_solveT(M, s, L, zt, g);
+  const double* LUs = s + L.LU;
+  const double* dinvs = s + L.dinv;
+  // transposed Sherman-Morrison vector zt = A^-T v
+  vset(X, VY, m, g);
+  lu_solveT(M, LUs, dinvs, X, g);
   double uz = 0.0;
-  for (int i = g.lane; i < m; i += g.size) uz = fma(u[i], zt[i], uz);
+  for (int i = g.lane; i < m; i += g.size) uz = fma(UY[i], X[i], uz);
   uz = gsum(g, uz);
   const double idenT = 1.0 / (1.0 - uz);
+  vset(ZT, X, m, g);
   // ---- reverse sweep over the stages
   for (int i = g.lane; i < m; i += g.size) {
     MU1[i] = M1 * LAM[i]; MU2[i] = 0.0; MU3[i] = M3 * LAM[i]; MU4[i] = M4 * LAM[i];
   }
   g.sync();
-  // stage 4: r4 = f(Y4) + (c41 U1 + c42 U2 + c43 U3)/h, Y4 = y + a41 U1 + a43 U3
-  vset(W4, MU4, m, g);
-  smT_solve(M, s, A, W4, idenT, g);
+  // stage 4: r4 = f(Y4) + (c41 U1 + c42 U2 + c43 U3)/h, Y4 = y + a41 U1 + a43 U3 (factor still in shared
+  // memory; copied out before the Jacobian at Y4 takes its region)
+  vset(X, MU4, m, g);
+  smT_solve(M, LUs, dinvs, UY, ZT, X, idenT, g);
+  vset(W4, X, m, g);
+  vset(LUg, LUs, M.nnz_LU + m, g);
+  for (int i = g.lane; i < m; i += g.size) {
+    Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
+    Y3[i] = fma(A31, U1[i], y[i]);
+  }
+  g.sync();
   {
-    ScalT<double> sc = eval_jac<double>(M, s, L, Y4, p, g);
-    theta_terms<double>(M, s, L, sc, W4, s + A.A, GA, GE, g);
+    const ScalT<double> sc = eval_jac<double>(M, s, L, Y4, p, g);
+    theta_terms(M, s + L.hRT, s + L.q, sc.T, sc.rho, sc.cp, sc.irho, W4, a, GA, GE, g);
     vjp<double>(M, s + L.S, s + L.u, s + L.v, W4, G, s + L.part, g);
   }
   for (int i = g.lane; i < m; i += g.size) {
@@ -275,11 +268,12 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
   }
   g.sync();
   // stage 3: r3 = f(Y3) + (c31 U1 + c32 U2)/h, Y3 = y + a31 U1
-  vset(W3, MU3, m, g);
-  smT_solve(M, s, A, W3, idenT, g);
+  vset(X, MU3, m, g);
+  smT_solve(M, LUg, dinvg, UY, ZT, X, idenT, g);
+  vset(W3, X, m, g);
   {
-    ScalT<double> sc = eval_jac<double>(M, s, L, Y3, p, g);
-    theta_terms<double>(M, s, L, sc, W3, s + A.A, GA, GE, g);
+    const ScalT<double> sc = eval_jac<double>(M, s, L, Y3, p, g);
+    theta_terms(M, s + L.hRT, s + L.q, sc.T, sc.rho, sc.cp, sc.irho, W3, a, GA, GE, g);
     vjp<double>(M, s + L.S, s + L.u, s + L.v, W3, G, s + L.part, g);
   }
   for (int i = g.lane; i < m; i += g.size) {
@@ -289,55 +283,64 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, const
   }
   g.sync();
   // stage 2: r2 = f(y) + (c21/h) U1;  stage 1: r1 = f(y)
-  vset(W2, MU2, m, g);
-  smT_solve(M, s, A, W2, idenT, g);
+  vset(X, MU2, m, g);
+  smT_solve(M, LUg, dinvg, UY, ZT, X, idenT, g);
+  vset(W2, X, m, g);
   for (int i = g.lane; i < m; i += g.size) MU1[i] = fma(C21 * ih, W2[i], MU1[i]);
   g.sync();
-  vset(W1, MU1, m, g);
-  smT_solve(M, s, A, W1, idenT, g);
-  double* WS = s + A.WS;
+  vset(X, MU1, m, g);
+  smT_solve(M, LUg, dinvg, UY, ZT, X, idenT, g);
+  vset(W1, X, m, g);
+  double* WS = ws + A.WS;
   for (int i = g.lane; i < m; i += g.size) WS[i] = W1[i] + W2[i];
   g.sync();
-  vjp<double>(M, s + A.SY, s + A.UY, s + A.VY, WS, G, s + L.part, g);
+  vjp<double>(M, ws + A.SY, UY, VY, WS, G, s + L.part, g);
   for (int i = g.lane; i < m; i += g.size) LAM[i] += G[i];
   g.sync();
-  {
-    vset(s + L.y, y, m, g);
-    ScalT<double> sc = eval_f<double>(M, s, L, s + L.y, p, s + L.f0, g);
-    theta_terms<double>(M, s, L, sc, WS, s + A.A, GA, GE, g);
-  }
+  theta_terms(M, ws + A.HY, ws + A.QY, ws[A.SC], ws[A.SC + 1], ws[A.SC + 2], ws[A.SC + 3], WS, a, GA, GE, g);
   // ---- Hessian and mixed parameter terms: derivative of J(y) along U_i, contracted with w_i, for the
   //      four stages in one evaluation of the Jacobian with four tangents
   const double* Us[4] = {U1, U2, U3, U4};
   const double* Ws[4] = {W1, W2, W3, W4};
-  second_order_terms(M, dw, Ld, y, p, Us, Ws, LAM, G, GA, GE, g);
+  second_order_terms(M, dw, L, y, p, Us, Ws, LAM, G, GA, GE, g);
   return true;
 }
 
-// Reverse pass of one cell from its tape.  Returns false on a singular factor.
-__device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, const AdjLayout& A, Dual4* dw,
-                                             const CellLayout& Ld, double p, int n_acc, const double* rec_h,
-                                             const double* rec_ck, int K, int N, int cell, const Grp1& g,
-                                             const IntOpts& o, double* seg, double* GA, double* GE) {
+// Reverse pass of one cell from its tape.  ws: the warp's global workspace.  Returns false on a singular
+// factor.
+__device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, double* ws, const AdjLayout& A, Dual4* dw,
+                                             double p, int n_acc, const double* rec_h, const double* rec_ck, int K,
+                                             int N, int cell, const Grp1& g, const IntOpts& o) {
   const int m = M.m;
   const CellLayout& L = A.L;
+  double* seg = ws + A.SEG;
+  double* ust = ws + A.UST;
+  double* GA = ws + A.GA;
+  double* GE = ws + A.GE;
   const int nseg = (n_acc + K - 1) / K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int n0 = sg * K, n1 = min(n_acc, n0 + K);
     for (int i = g.lane; i < m; i += g.size) seg[i] = rec_ck[((size_t)sg * m + i) * N + cell];
     g.sync();
-    // recompute the segment's states with the forward arithmetic
-    for (int nn = n0; nn < n1 - 1; ++nn) {
+    // recompute the segment's states and stage vectors with the forward arithmetic
+    for (int nn = n0; nn < n1; ++nn) {
       vset(s + L.y, seg + (size_t)(nn - n0) * m, m, g);
       eval_jac<double>(M, s, L, s + L.y, p, g);
       const StepOut so = ros_attempt(M, s, L, p, rec_h[(size_t)nn * N + cell], o.rtol, o.atol, g);
       if (!so.good) return false;
-      vset(seg + (size_t)(nn - n0 + 1) * m, s + L.ytmp, m, g);
+      double* u4 = ust + (size_t)(nn - n0) * 4 * m;
+      for (int i = g.lane; i < m; i += g.size) {
+        u4[i] = s[L.U1 + i]; u4[m + i] = s[L.U2 + i]; u4[2 * m + i] = s[L.U3 + i]; u4[3 * m + i] = s[L.U4 + i];
+        if (nn + 1 < n1) seg[(size_t)(nn - n0 + 1) * m + i] = s[L.ytmp + i];
+      }
+      g.sync();
     }
-    for (int nn = n1 - 1; nn >= n0; --nn)
-      if (!adjoint_step(M, s, A, dw, Ld, seg + (size_t)(nn - n0) * m, p, rec_h[(size_t)nn * N + cell], GA, GE,
-                        g))
+    for (int nn = n1 - 1; nn >= n0; --nn) {
+      const double* u4 = ust + (size_t)(nn - n0) * 4 * m;
+      if (!adjoint_step(M, s, ws, A, dw, seg + (size_t)(nn - n0) * m, u4, u4 + m, u4 + 2 * m, u4 + 3 * m, p,
+                        rec_h[(size_t)nn * N + cell], GA, GE, g))
         return false;
+    }
   }
   return true;
 }

@@ -32,10 +32,12 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+constexpr int kMaxBlockCells = 32;   // cells per block at most (half-warp cells: 16 warps)
+
 struct chem_handle_s {
   int device = 0;
   HostMech hm;
-  MechView view[kMaxWarpsPerCell]{};   // view[w - 1]: the tables with the programs for w warps per cell
+  MechView view[kNumGroups]{};   // view[g]: the tables with the programs of lane group g (kGroupWidth)
   void* blob = nullptr;
   CellLayout L{};
   int cell_bytes = 0;
@@ -53,14 +55,15 @@ struct chem_handle_s {
   size_t map_scratch_bytes = 0;
   // per warps-per-cell choice (set with the attributes): the largest block that launches (in cells), the
   // block size that fits the most cells per SM, and that number of cells
-  int max_cells[kMaxWarpsPerCell] = {1, 1};
-  int default_cells[kMaxWarpsPerCell] = {1, 1};
-  int resident_cells[kMaxWarpsPerCell] = {0, 0};
-  int bps_cache[kMaxWarpsPerCell][17] = {};   // resident blocks per SM of the persistent kernel, per shape
+  int max_cells[kNumGroups] = {1, 1, 2};
+  int default_cells[kNumGroups] = {1, 1, 2};
+  int resident_cells[kNumGroups] = {0, 0, 0};
+  int bps_cache[kNumGroups][kMaxBlockCells + 1] = {};   // resident blocks per SM of the persistent kernel
   int auto_wpc = 1;                // warps per cell when the caller leaves the choice to the library
+  int auto_cpw = 1;                // cells per warp when the caller leaves the choice to the library
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
-    int N, mode, cpb, chunk, wpc;
+    int N, mode, cpb, chunk, grp;
     const void* ptr[10];
     double d[5];
     int i[4];
@@ -108,17 +111,25 @@ CellLayout make_layout(const HostMech& hm, bool separate_lu = false) {
   return L;
 }
 
+// Reverse-pass layout: shared memory = the forward cell layout; the per-warp global workspace below.
 AdjLayout make_adj_layout(const HostMech& hm, int K) {
   AdjLayout A{};
-  A.L = make_layout(hm, true);
-  int o = A.L.total;
+  A.L = make_layout(hm);
+  int o = 0;
   const int m = hm.m;
-  auto take = [&](int cnt) { int at = o; o += cnt; return at; };
-  A.Y3 = take(m); A.Y4 = take(m); A.AU1 = take(m); A.AU2 = take(m); A.AU3 = take(m); A.AU4 = take(m);
-  A.W1 = take(m); A.W2 = take(m); A.W3 = take(m); A.W4 = take(m); A.MU1 = take(m); A.MU2 = take(m);
-  A.MU3 = take(m); A.MU4 = take(m); A.LAM = take(m); A.G = take(m); A.ZT = take(m); A.WS = take(m);
-  A.SY = take(hm.nnz_S); A.UY = take(m); A.VY = take(m);
-  A.A = take(hm.n);
+  // 256-byte aligned pieces (32 doubles): coalesced lane-strided access
+  auto take = [&](int cnt) { int at = o; o += (cnt + 31) / 32 * 32; return at; };
+  A.Y3 = take(m); A.Y4 = take(m); A.W1 = take(m); A.W2 = take(m); A.W3 = take(m); A.W4 = take(m);
+  A.MU1 = take(m); A.MU2 = take(m); A.MU3 = take(m); A.MU4 = take(m); A.LAM = take(m); A.G = take(m);
+  A.ZT = take(m); A.WS = take(m); A.UY = take(m); A.VY = take(m); A.HY = take(m);
+  A.SY = take(hm.nnz_S);
+  A.QY = take(std::max(hm.R, 1));
+  A.LUG = take(hm.nnz_LU + m);
+  A.SC = take(8);
+  A.UST = take(K * 4 * m);
+  A.SEG = take(K * m);
+  A.GA = take(std::max(hm.R, 1));
+  A.GE = take(std::max(hm.R, 1));
   A.total = o;
   return A;
 }
@@ -214,7 +225,7 @@ chem_status check_handle(chem_handle h, DeviceScope& ds) {
   return CHEM_OK;
 }
 
-int max_cells_per_block(const chem_handle h, int wpc) { return h->max_cells[wpc - 1]; }
+int max_cells_per_block(const chem_handle h, int grp) { return h->max_cells[grp]; }
 
 chem_status set_attrs(chem_handle h) {
   if (h->attr_set) return CHEM_OK;
@@ -231,34 +242,38 @@ chem_status set_attrs(chem_handle h) {
       (e = cudaFuncSetAttribute(forward_kernel(KF_PERSISTENT, 2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
           cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute");
-  // largest block per warps-per-cell choice: shared memory, the threads the kernels' registers allow
-  // (both forms), at most 16 cells, and for two-warp cells the 15 named barriers besides barrier 0
-  for (int wpc = 1; wpc <= kMaxWarpsPerCell; ++wpc) {
+  // largest block per lane group: shared memory, the threads the kernels' registers allow (both forms),
+  // at most 16 cells (32 half-warp cells), for two-warp cells the 15 named barriers besides barrier 0, and
+  // for half-warp cells an even count (whole warps)
+  for (int grp = 0; grp < kNumGroups; ++grp) {
     cudaFuncAttributes fa1, fa2;
-    if ((e = cudaFuncGetAttributes(&fa1, forward_kernel(KF_PLAIN, wpc))) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa2, forward_kernel(KF_PERSISTENT, wpc))) !=
-            cudaSuccess)
+    if ((e = cudaFuncGetAttributes(&fa1, forward_kernel(KF_PLAIN, grp))) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa2, forward_kernel(KF_PERSISTENT, grp))) != cudaSuccess)
       return cuda_fail(e, "cudaFuncGetAttributes");
+    const int width = kGroupWidth[grp];
     int c = std::max(1, h->smem_optin / std::max(h->cell_bytes, 1));
-    c = std::min(c, std::min(fa1.maxThreadsPerBlock, fa2.maxThreadsPerBlock) / (wpc * kWarp));
-    if (wpc > 1) c = std::min(c, 15);
-    h->max_cells[wpc - 1] = std::max(1, std::min(c, 16));
+    c = std::min(c, std::min(fa1.maxThreadsPerBlock, fa2.maxThreadsPerBlock) / width);
+    if (grp == 1) c = std::min(c, 15);
+    c = std::min(c, grp == 2 ? kMaxBlockCells : 16);
+    if (grp == 2) c &= ~1;
+    h->max_cells[grp] = std::max(grp == 2 ? 2 : 1, c);
   }
-  // default block shape per warps-per-cell choice: the most resident cells per SM (each block also
-  // reserves some shared memory, so a few cells per block can fit one more cell per SM than single-cell
-  // blocks); ties -> fewer cells per block
-  for (int wpc = 1; wpc <= kMaxWarpsPerCell; ++wpc) {
-    int best_c = 1, best_cells = 0;
-    for (int c = 1; c <= max_cells_per_block(h, wpc); ++c) {
+  // default block shape per lane group: the most resident cells per SM (each block also reserves some
+  // shared memory, so a few cells per block can fit one more cell per SM than single-cell blocks);
+  // ties -> fewer cells per block
+  for (int grp = 0; grp < kNumGroups; ++grp) {
+    const int step = grp == 2 ? 2 : 1;
+    int best_c = step, best_cells = 0;
+    for (int c = step; c <= max_cells_per_block(h, grp); c += step) {
       int blocks = 0;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-               &blocks, forward_kernel(KF_PERSISTENT, wpc), c * wpc * kWarp,
-               (size_t)c * h->cell_bytes)) != cudaSuccess)
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, forward_kernel(KF_PERSISTENT, grp),
+                                                             c * kGroupWidth[grp], (size_t)c * h->cell_bytes)) !=
+          cudaSuccess)
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
       if (blocks * c > best_cells) { best_cells = blocks * c; best_c = c; }
     }
-    h->default_cells[wpc - 1] = best_c;
-    h->resident_cells[wpc - 1] = best_cells;
+    h->default_cells[grp] = best_c;
+    h->resident_cells[grp] = best_cells;
   }
   // automatic choice: two warps per cell when one-warp cells leave fewer than 6 warps per SM (a cell
   // larger than ~35 KB of shared memory) and two-warp cells fit as many cells
@@ -269,9 +284,11 @@ chem_status set_attrs(chem_handle h) {
 
 // Cells per block: the request (0: the default of the warps-per-cell choice) bounded by the largest block
 // that launches.
-int cells_per_block(const chem_handle h, int requested, int wpc) {
-  int c = requested > 0 ? requested : h->default_cells[wpc - 1];
-  return std::max(1, std::min(c, max_cells_per_block(h, wpc)));
+int cells_per_block(const chem_handle h, int requested, int grp) {
+  int c = requested > 0 ? requested : h->default_cells[grp];
+  c = std::max(1, std::min(c, max_cells_per_block(h, grp)));
+  if (grp == 2) c = std::max(2, c & ~1);   // half-warp cells fill whole warps
+  return c;
 }
 
 chem_status ensure_scratch(chem_handle h, int N) {
@@ -297,11 +314,11 @@ chem_status launch_check(const char* what) {
 }
 
 // Resident blocks per SM of the persistent kernel for a launch shape (cached per shape).
-chem_status persistent_blocks_per_sm(chem_handle h, int wpc, int cpb, int& bps) {
-  int& cached = h->bps_cache[wpc - 1][cpb];
+chem_status persistent_blocks_per_sm(chem_handle h, int grp, int cpb, int& bps) {
+  int& cached = h->bps_cache[grp][cpb];
   if (cached == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, forward_kernel(KF_PERSISTENT, wpc),
-                                                                  cpb * wpc * kWarp,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, forward_kernel(KF_PERSISTENT, grp),
+                                                                  cpb * kGroupWidth[grp],
                                                                   (size_t)cpb * h->cell_bytes);
     if (e != cudaSuccess) { cached = 0; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
     cached = std::max(cached, 1);
@@ -339,7 +356,7 @@ struct IntCall {
   chem_integrate_opts o{};
   IntOpts io{};
   unsigned long long budget_ns = 0;
-  int wpc = 1;     // warps per cell
+  int grp = 0;     // lane group: 0 one warp, 1 two warps, 2 half a warp per cell
   int cpb = 1;     // cells per block
   int grid = 1;    // persistent form: resident blocks on the device
   int chunk = 1;   // persistent form: cells per queue pull
@@ -353,13 +370,19 @@ chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opt
   if (o.mode != 0 && o.mode != 1) return fail(CHEM_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
   if (o.warps_per_cell < 0 || o.warps_per_cell > kMaxWarpsPerCell)
     return fail(CHEM_EINVAL, "warps_per_cell must be 0 (automatic), 1 or 2");
+  if (o.cells_per_warp < 0 || o.cells_per_warp > 2)
+    return fail(CHEM_EINVAL, "cells_per_warp must be 0 (automatic), 1 or 2");
+  if (o.cells_per_warp == 2 && o.warps_per_cell == 2)
+    return fail(CHEM_EINVAL, "cells_per_warp = 2 needs warps_per_cell 0 or 1");
   if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
   c.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-  c.wpc = o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc;
-  c.cpb = cells_per_block(h, o.block_cells, c.wpc);
+  if (o.cells_per_warp == 2) c.grp = 2;
+  else if (o.cells_per_warp == 0 && o.warps_per_cell == 0 && h->auto_cpw == 2) c.grp = 2;
+  else c.grp = (o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc) - 1;
+  c.cpb = cells_per_block(h, o.block_cells, c.grp);
   int bps = 1;
-  if ((st = persistent_blocks_per_sm(h, c.wpc, c.cpb, bps)) != CHEM_OK) return st;
+  if ((st = persistent_blocks_per_sm(h, c.grp, c.cpb, bps)) != CHEM_OK) return st;
   c.grid = h->num_sms * bps;
   // a pull larger than an even share of the cells over the resident lane groups only leaves groups idle
   const long long groups = (long long)c.grid * c.cpb;
@@ -425,10 +448,9 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   const int n_jp = (int)hm.jpass.size() / 4;
   if (n_jp > kMaxJPass) { delete h; return fail(CHEM_EUNSUPPORTED, "too many Jacobian passes"); }
   constexpr int kMaxG = 3 + kMaxJPass;
-  size_t o_g[kMaxWarpsPerCell][kMaxG][2], o_lops[kMaxWarpsPerCell], o_sops[kMaxWarpsPerCell],
-      o_tops[kMaxWarpsPerCell];
-  const HostGather* gs[kMaxWarpsPerCell][kMaxG];
-  for (int w = 0; w < kMaxWarpsPerCell; ++w) {
+  size_t o_g[kNumGroups][kMaxG][2], o_lops[kNumGroups], o_sops[kNumGroups], o_tops[kNumGroups];
+  const HostGather* gs[kNumGroups][kMaxG];
+  for (int w = 0; w < kNumGroups; ++w) {
     const HostProg& P = hm.prog[w];
     gs[w][0] = &P.g_omega; gs[w][1] = &P.g_row; gs[w][2] = &P.g_col;
     for (int i = 0; i < n_jp; ++i) gs[w][3 + i] = &P.g_jac[i];
@@ -443,7 +465,7 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
   }
   char* b = (char*)h->blob;
   h->rxd0 = (const double*)(b + o_rxd0);
-  for (int w = 0; w < kMaxWarpsPerCell; ++w) {
+  for (int w = 0; w < kNumGroups; ++w) {
     const HostProg& P = hm.prog[w];
     MechView& V = h->view[w];
     V.width = P.width;
@@ -523,19 +545,21 @@ chem_status chem_info(chem_handle h, chem_info_t* info) {
   info->smem_per_cell = h->cell_bytes;
   info->n_dslots = h->hm.n_dslot;
   info->jac_passes = (int)h->hm.jpass.size() / 4;
-  info->smem_adjoint_per_cell = make_adj_layout(h->hm, 16).total * (int)sizeof(double);
-  for (int w = 0; w < kMaxWarpsPerCell; ++w) { info->max_block_cells[w] = 0; info->resident_cells[w] = 0; }
+  info->smem_adjoint_per_cell = make_adj_layout(h->hm, 16).L.total * (int)sizeof(double);
+  for (int w = 0; w < kNumGroups; ++w) { info->max_block_cells[w] = 0; info->resident_cells[w] = 0; }
   info->auto_warps_per_cell = 0;
+  info->auto_cells_per_warp = 0;
   if (h->device >= 0) {
     DeviceScope ds;
     chem_status st = check_handle(h, ds);
     if (st == CHEM_OK) st = set_attrs(h);
     if (st != CHEM_OK) return st;
-    for (int w = 0; w < kMaxWarpsPerCell; ++w) {
+    for (int w = 0; w < kNumGroups; ++w) {
       info->max_block_cells[w] = h->max_cells[w];
       info->resident_cells[w] = h->resident_cells[w];
     }
     info->auto_warps_per_cell = h->auto_wpc;
+    info->auto_cells_per_warp = h->auto_cpw;
   }
   return CHEM_OK;
 }
@@ -572,6 +596,9 @@ chem_status chem_export_plan(chem_handle h, int which, int* out, int* count) {
     case 8: prog(P2.lu_ops, P2.lu_kind, P2.width); break;
     case 9: prog(P2.sv_ops, P2.sv_kind, P2.width); break;
     case 10: prog(P2.svT_ops, P2.svT_kind, P2.width); break;
+    case 11: prog(hm.prog[2].lu_ops, hm.prog[2].lu_kind, hm.prog[2].width); break;
+    case 12: prog(hm.prog[2].sv_ops, hm.prog[2].sv_kind, hm.prog[2].width); break;
+    case 13: prog(hm.prog[2].svT_ops, hm.prog[2].svT_kind, hm.prog[2].width); break;
     default: return fail(CHEM_EINVAL, "unknown plan part");
   }
   if (out) std::copy(v.begin(), v.end(), out);
@@ -624,8 +651,9 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   const unsigned long long budget_ns = c.budget_ns;
   cudaStream_t strm = (cudaStream_t)stream;
   cudaError_t e;
-  const int wpc = c.wpc;
-  const MechView& V = h->view[wpc - 1];
+  const int grp = c.grp;
+  const int width = kGroupWidth[grp];
+  const MechView& V = h->view[grp];
   const int cpb = c.cpb;
   if (o.mode == 0) {
     unsigned long long* stamp = nullptr;
@@ -634,8 +662,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
       stamp = (unsigned long long*)((char*)h->scratch + kScrStamp);
       k_stamp<<<1, 32, 0, strm>>>(stamp);
     }
-    launch_integrate_plain(wpc, (N + cpb - 1) / cpb, cpb * wpc * kWarp, cpb * h->cell_bytes, strm, V, h->L, N, T, p, Y,
-                           dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns);
+    launch_integrate_plain(grp, (N + cpb - 1) / cpb, cpb * width, cpb * h->cell_bytes, strm, V, h->L, N, T, p, Y, dt,
+                           h_io, nsub, status, o.naccept, io, stamp, budget_ns);
     return launch_check("chem_integrate launch");
   }
   // persistent mode: sort by previous cost, then one resident grid pulling from the queue; the whole
@@ -643,7 +671,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   if ((st = ensure_scratch(h, N)) != CHEM_OK) return st;
   const int chunk = c.chunk;
   chem_handle_s::GraphKey key{};
-  key.N = N; key.mode = 1; key.cpb = cpb; key.chunk = chunk; key.wpc = wpc;
+  key.N = N; key.mode = 1; key.cpb = cpb; key.chunk = chunk; key.grp = grp;
   const void* ptrs[10] = {T, p, Y, dt, h_io, nsub, status, o.naccept, o.trace, h->scratch};
   for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
   key.d[0] = io.rtol; key.d[1] = io.atol; key.d[2] = io.h_init; key.d[3] = io.h_min; key.d[4] = o.time_budget_s;
@@ -667,8 +695,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
     k_stamp<<<1, 32, 0, cs>>>(stamp);
     k_sort_count<<<sblocks, 256, 0, cs>>>(N, nsub, counts);
     k_sort_scatter<<<sblocks, 256, 0, cs>>>(N, nsub, counts, cursor, perm);
-    launch_integrate_persistent(wpc, grid, cpb * wpc * kWarp, cpb * h->cell_bytes, cs, V, h->L, N, T, p, Y, dt, h_io,
-                                nsub, status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+    launch_integrate_persistent(grp, grid, cpb * width, cpb * h->cell_bytes, cs, V, h->L, N, T, p, Y, dt, h_io, nsub,
+                                status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
     cudaGraph_t graph = nullptr;
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &graph);
@@ -719,7 +747,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   const HostMech& hm = h->hm;
   const int m = hm.m;
   const AdjLayout A = make_adj_layout(hm, K);
-  const int adj_bytes = A.total * (int)sizeof(double);
+  const int adj_bytes = A.L.total * (int)sizeof(double);
   if (adj_bytes > h->smem_optin)
     return fail(CHEM_EUNSUPPORTED, "adjoint needs " + std::to_string(adj_bytes) + " bytes of shared memory per cell");
   cudaError_t e;
@@ -744,7 +772,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   const size_t b_ns = align_up((size_t)N * 4, 256);
   const size_t b_gc = grad_cell ? 0 : align_up((size_t)2 * hm.R * N * 8, 256);
   const size_t b_dw = align_up((size_t)grid * h->L.total * sizeof(Dual4), 256);
-  const size_t b_ww = align_up((size_t)grid * ((size_t)K * m + 2 * (size_t)hm.R) * 8, 256);
+  const size_t b_ww = align_up((size_t)grid * (size_t)A.total * 8, 256);
   const size_t need = b_head + b_rh + b_ck + b_rn + b_hio + b_ns + b_gc + b_dw + b_ww;
   if (need > h->adj_scratch_bytes) {
     if (h->adj_scratch) cudaFree(h->adj_scratch);
@@ -784,8 +812,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts));
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, rec_n, (int*)(scr + kScrCounts), (int*)(scr + kScrCursor), perm);
   if ((e = cudaMemsetAsync(head, 0, 4, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  CellLayout Ld = h->L;
-  k_adjoint<<<grid, kWarp, adj_bytes, strm>>>(h->view[0], A, Ld, N, p, rec_h, rec_ck, rec_n, K, gT, gY, gcell, gT0, gY0,
+  k_adjoint<<<grid, kWarp, adj_bytes, strm>>>(h->view[0], A, N, p, rec_h, rec_ck, rec_n, K, gT, gY, gcell, gT0, gY0,
                                                status, head, perm, dws, wws, io);
   if ((st = launch_check("chem_adjoint reverse launch")) != CHEM_OK) return st;
   const int P = 2 * hm.R;
@@ -836,7 +863,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   if ((st = parse_integrate(h, N, &o1, c)) != CHEM_OK) return st;
   char* scr = nullptr;
   if ((st = noalloc_scratch_address(h->device, &scr)) != CHEM_OK) return st;
-  const int wpc = c.wpc, wpb = c.cpb;
+  const int grp = c.grp, wpb = c.cpb;
   const int grid = std::min(c.grid, (N + wpb - 1) / wpb);
   const int sblocks = std::min(4 * h->num_sms, (N + 255) / 256);
   int* counts = (int*)(scr + kScrCounts);
@@ -851,7 +878,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   k_stamp<<<1, 32, 0, strm>>>(stamp);
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, nsub, counts);
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, nsub, counts, cursor, perm);
-  launch_integrate_persistent(wpc, grid, wpb * wpc * kWarp, wpb * h->cell_bytes, strm, h->view[wpc - 1], h->L, N, T, p,
+  launch_integrate_persistent(grp, grid, wpb * kGroupWidth[grp], wpb * h->cell_bytes, strm, h->view[grp], h->L, N, T, p,
                               Y, dt, h_io, nsub, status, c.o.naccept, perm, head, c.chunk, c.io, stamp, c.budget_ns);
   return launch_check("chem_integrate_noalloc launch");
 }

@@ -221,7 +221,7 @@ std::vector<int> min_degree_order(int m, const std::vector<std::vector<char>>& a
 
 chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string& err) {
   hm = HostMech();
-  for (int w = 1; w <= kMaxWarpsPerCell; ++w) hm.prog[w - 1].width = w * kWarp;
+  for (int g = 0; g < kNumGroups; ++g) hm.prog[g].width = kGroupWidth[g];
   const int n = d.n_species, R = d.n_reactions;
   if (n < 1 || R < 0) { err = "n_species must be >= 1 and n_reactions >= 0"; return CHEM_EINVAL; }
   if (!d.W || !d.nasa_lo || !d.nasa_hi || !d.T_mid) { err = "species arrays must not be NULL"; return CHEM_EINVAL; }

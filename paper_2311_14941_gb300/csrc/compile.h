@@ -16,8 +16,7 @@ struct HostGather {
   std::vector<int> comb;   // triples
 };
 
-// The warp programs for one group width (lanes that share a cell: 32 per warp times the warps per
-// cell).
+// The warp programs for one group width (the lanes that integrate a cell: 32, 64 or 16).
 struct HostProg {
   int width = kWarp;
   HostGather g_omega, g_row, g_col;
@@ -31,7 +30,7 @@ struct HostMech {
   std::vector<int> rx_order;           // compiled reaction index -> description index
   std::vector<double> sp, rxd, eff_am1, dslot_am1, entry_wratio;
   std::vector<int> rxi, eff_sp, dslot_sp, dslot_mask, entry_row, entry_col;
-  HostProg prog[kMaxWarpsPerCell];     // prog[w - 1]: programs for w warps per cell
+  HostProg prog[kNumGroups];           // prog[g]: programs for lane group g (widths kGroupWidth)
   std::vector<int> jpass;              // [passes * 4]: first reaction, end reaction, first slot, reactions
   int jreg = 0;                        // doubles of the largest pass (dq/dT values + derivative slots)
   std::vector<int> perm, iperm;        // LU position -> state index, and back

@@ -57,7 +57,23 @@ struct GrpW<2> {
 using Grp1 = GrpW<1>;
 using Grp2 = GrpW<2>;
 
+// Half a warp: two cells share a warp, 16 lanes each (mechanisms with few species, whose loops and
+// sparse programs leave most of a warp's lanes idle).  Shared-memory ordering is a warp barrier over the
+// group's own lanes, and reductions are butterflies within them, so the two cells of a warp may also
+// run apart (different step sequences) without waiting for each other.
+struct GrpH {
+  static constexpr int size = kWarp / 2;
+  int lane;        // 0 .. 15
+  unsigned mask;   // the lanes of this half of the warp
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+};
+
 __device__ __forceinline__ double gsum(const Grp1&, double v) { return warp_sum(v); }
+__device__ __forceinline__ double gsum(const GrpH& g, double v) {
+#pragma unroll
+  for (int o = GrpH::size / 2; o > 0; o >>= 1) v += __shfl_xor_sync(g.mask, v, o);
+  return v;
+}
 __device__ __forceinline__ double gsum(const Grp2& g, double v) {
   v = warp_sum(v);
   g.sync();   // earlier readers of the slots are done
@@ -76,6 +92,7 @@ __device__ __forceinline__ DualN<K> gsum(const G& g, DualN<K> v) {
 }
 
 __device__ __forceinline__ bool gall(const Grp1&, bool ok) { return __all_sync(0xffffffffu, ok); }
+__device__ __forceinline__ bool gall(const GrpH& g, bool ok) { return __all_sync(g.mask, ok); }
 __device__ __forceinline__ bool gall(const Grp2& g, bool ok) {
   ok = __all_sync(0xffffffffu, ok);
   g.sync();
@@ -86,6 +103,7 @@ __device__ __forceinline__ bool gall(const Grp2& g, bool ok) {
 
 // The value of lane 0, on every lane of the group.
 __device__ __forceinline__ long long gbcast(const Grp1&, long long v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ long long gbcast(const GrpH& g, long long v) { return __shfl_sync(g.mask, v, 0, GrpH::size); }
 __device__ __forceinline__ long long gbcast(const Grp2& g, long long v) {
   g.sync();
   if (g.lane == 0) g.xch[0] = __longlong_as_double(v);
@@ -279,31 +297,11 @@ struct RxCore {
   Sc q, qn, kf, kr, Mfac, dlnkf_dT, dlnKc_dT, dlnk_dlnM, iM;
   Sc cr0, cr1, cr2, cp0, cp1, cp2;
   int so, scn;
-  unsigned need;   // NEED_* bits: occurrence counts some active lane of the warp has
+  bool rep;   // a species occurs more than once on one side (coefficient 2 or 3)
 };
-
-// Which of the optional factors of the participant products some active lane of the warp needs.  An
-// absent occurrence contributes the factor 1, so a product step that no lane needs is skipped for the
-// whole warp; one that some lane needs is taken by all (the others multiply by exactly 1), which keeps
-// every lane's result bit for bit the same as with all steps taken.
-// NEED_REP: a species occurs more than once on one side (coefficient 2 or 3), so a derivative slot may
-// sum several occurrence factors.
-enum : unsigned {
-  NEED_R1 = 1, NEED_R2 = 2, NEED_P1 = 4, NEED_P2 = 8, NEED_D1 = 16, NEED_D2 = 32, NEED_D3 = 64, NEED_REP = 128
-};
-// The shapes of nearly all reactions: A + B <=> C + D, A + B <=> C (recombination, fall-off) and
-// A <=> B + C (decomposition); a warp whose active lanes all have one of them takes a straight path.
-constexpr unsigned SHAPE_22 = NEED_R1 | NEED_P1, SHAPE_21 = NEED_R1 | NEED_D1, SHAPE_12 = NEED_P1 | NEED_D1;
-__device__ __forceinline__ unsigned warp_need(int nro, int npo, int adn, bool rep) {
-  const unsigned mine = (nro > 1 ? NEED_R1 : 0u) | (nro > 2 ? NEED_R2 : 0u) | (npo > 1 ? NEED_P1 : 0u) |
-                        (npo > 2 ? NEED_P2 : 0u) | (adn >= 1 ? NEED_D1 : 0u) | (adn >= 2 ? NEED_D2 : 0u) |
-                        (adn >= 3 ? NEED_D3 : 0u) | (rep ? NEED_REP : 0u);
-  return __reduce_or_sync(__activemask(), mine);
-}
 
 // Rate of progress of reaction r, specialised on the reaction type (0 elementary, 1 third-body,
-// 2 Troe).  Absent occurrences read index 0 and count as 1; the product steps that no lane of the warp
-// needs are skipped (warp_need).
+// 2 Troe).  Branch-free in the participant counts: absent occurrences read index 0 and count as 1.
 template <class Sc, int TYPE, bool DERIV>
 __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc* __restrict__ C,
                                               const Sc* __restrict__ eg, const Sc* __restrict__ emg,
@@ -315,57 +313,13 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
   const int p0 = __ldg(I + 7), p1 = max(__ldg(I + 8), 0), p2 = max(__ldg(I + 9), 0);
   const Sc lnA = __ldg(D), bb = __ldg(D + 1), Ta = __ldg(D + 2);
   RxCore<Sc> x;
-  const int dn = npo - nro;
-  const int adn = dn < 0 ? -dn : dn;
-  const bool rep = (nro > 1 && r1 == r0) || (nro > 2 && (r2 == r0 || r2 == r1)) || (npo > 1 && p1 == p0) ||
-                   (npo > 2 && (p2 == p0 || p2 == p1));
-  const unsigned need = warp_need(nro, npo, adn, rep);
-  x.need = need;
+  x.rep = (nro > 1 && r1 == r0) || (nro > 2 && (r2 == r0 || r2 == r1)) || (npo > 1 && p1 == p0) ||
+          (npo > 2 && (p2 == p0 || p2 == p1));
   const Sc lnkinf = sfma(-Ta, sc.invT, sfma(bb, sc.lnT, lnA));
   Sc kf = sexp(lnkinf);
   x.cr0 = C[r0]; x.cr1 = nro > 1 ? C[r1] : Sc(1.0); x.cr2 = nro > 2 ? C[r2] : Sc(1.0);
   x.cp0 = C[p0]; x.cp1 = npo > 1 ? C[p1] : Sc(1.0); x.cp2 = npo > 2 ? C[p2] : Sc(1.0);
-  // concentration products Pf, Pb and the reverse-rate factor
-  //   ik = prod exp(g)^nu'' * prod exp(-g)^nu' * (Ru T/p0)^(sum nu) = k_r / k_f,
-  // each multiplied in the same order on every path (the straight paths only leave out factors that
-  // are exactly 1 in every lane)
-  Sc Pf, Pb, ik;
-  {
-    const Sc e0 = eg[p0] * emg[r0];
-    const Sc egp1 = npo > 1 ? eg[p1] : Sc(1.0), emr1 = nro > 1 ? emg[r1] : Sc(1.0);
-    const Sc fp = dn > 0 ? sc.rtp : sc.irtp;
-    const Sc fp1 = adn >= 1 ? fp : Sc(1.0);
-    if (need == SHAPE_22) {
-      Pf = x.cr0 * x.cr1; Pb = x.cp0 * x.cp1; ik = (e0 * egp1) * emr1;
-    } else if (need == SHAPE_21) {
-      Pf = x.cr0 * x.cr1; Pb = x.cp0; ik = (e0 * emr1) * fp1;
-    } else if (need == SHAPE_12) {
-      Pf = x.cr0; Pb = x.cp0 * x.cp1; ik = (e0 * egp1) * fp1;
-    } else {
-      Pf = x.cr0; Pb = x.cp0;
-      if (need & NEED_R1) Pf *= x.cr1;
-      if (need & NEED_R2) Pf *= x.cr2;
-      if (need & NEED_P1) Pb *= x.cp1;
-      if (need & NEED_P2) Pb *= x.cp2;
-      ik = e0;
-      if (need & NEED_P1) {
-        Sc t = egp1;
-        if (need & NEED_P2) t *= (npo > 2 ? eg[p2] : Sc(1.0));
-        ik *= t;
-      }
-      if (need & NEED_R1) {
-        Sc t = emr1;
-        if (need & NEED_R2) t *= (nro > 2 ? emg[r2] : Sc(1.0));
-        ik *= t;
-      }
-      if (need & NEED_D1) {
-        Sc t = fp1;
-        if (need & NEED_D2) t *= (adn >= 2 ? fp : Sc(1.0));
-        if (need & NEED_D3) t *= (adn >= 3 ? fp : Sc(1.0));
-        ik *= t;
-      }
-    }
-  }
+  const Sc Pf = x.cr0 * x.cr1 * x.cr2, Pb = x.cp0 * x.cp1 * x.cp2;
   Sc Mv = sc.ctot;
   if (TYPE != 0) {
     const int eo = __ldg(I + 11), ec = __ldg(I + 12);
@@ -416,21 +370,20 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
       x.iM = sexp(-lnM);
     }
   }
-  // reverse rate: k_r = k_f * ik
+  // reverse rate: k_r = k_f * prod exp(g)^nu'' * prod exp(-g)^nu' * (Ru T/p0)^(sum nu)
+  const int dn = npo - nro;
+  Sc ik = eg[p0] * emg[r0];
+  ik *= (npo > 1 ? eg[p1] : Sc(1.0)) * (npo > 2 ? eg[p2] : Sc(1.0));
+  ik *= (nro > 1 ? emg[r1] : Sc(1.0)) * (nro > 2 ? emg[r2] : Sc(1.0));
+  const Sc fp = dn > 0 ? sc.rtp : sc.irtp;
+  const int adn = dn < 0 ? -dn : dn;
+  ik *= (adn >= 1 ? fp : Sc(1.0)) * (adn >= 2 ? fp : Sc(1.0)) * (adn >= 3 ? fp : Sc(1.0));
   x.kr = rev ? kf * ik : Sc(0.0);
   x.kf = kf;
   if (DERIV) {
     Sc sh = hRT[p0] - hRT[r0];
-    if (need & NEED_P1) {
-      Sc t = npo > 1 ? hRT[p1] : Sc(0.0);
-      if (need & NEED_P2) t += (npo > 2 ? hRT[p2] : Sc(0.0));
-      sh += t;
-    }
-    if (need & NEED_R1) {
-      Sc t = nro > 1 ? hRT[r1] : Sc(0.0);
-      if (need & NEED_R2) t += (nro > 2 ? hRT[r2] : Sc(0.0));
-      sh -= t;
-    }
+    sh += (npo > 1 ? hRT[p1] : Sc(0.0)) + (npo > 2 ? hRT[p2] : Sc(0.0));
+    sh -= (nro > 1 ? hRT[r1] : Sc(0.0)) + (nro > 2 ? hRT[r2] : Sc(0.0));
     const double dnd = dn == 0 ? 0.0 : dn == 1 ? 1.0 : dn == -1 ? -1.0 : dn == 2 ? 2.0 : dn == -2 ? -2.0 :
                        dn == 3 ? 3.0 : -3.0;
     x.dlnKc_dT = rev ? (sh - dnd) * sc.invT : Sc(0.0);
@@ -453,38 +406,25 @@ __device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<
   if (!valid) return;
   s[L.q + r] = x.q;
   if (!DERIV) return;
-  const unsigned need = x.need;
   const Sc kfM = x.kf * x.Mfac, krM = x.kr * x.Mfac;
-  // forward and reverse rates of progress, and the partial products d(prod)/d(occurrence i) = product of
-  // the other occurrences (an occurrence that no lane has is never read: its slot mask bit is clear)
-  Sc qf, qr, dr0, dr1, dr2, dp0, dp1, dp2;
-  if (need == SHAPE_22 || need == SHAPE_21 || need == SHAPE_12) {
-    qf = kfM * x.cr0; qr = krM * x.cp0;
-    if (need & NEED_R1) qf *= x.cr1;
-    if (need & NEED_P1) qr *= x.cp1;
-    dr0 = x.cr1; dr1 = x.cr0; dr2 = Sc(0.0);
-    dp0 = x.cp1; dp1 = x.cp0; dp2 = Sc(0.0);
-  } else {
-    qf = kfM * x.cr0; qr = krM * x.cp0;
-    if (need & NEED_R1) qf *= x.cr1;
-    if (need & NEED_R2) qf *= x.cr2;
-    if (need & NEED_P1) qr *= x.cp1;
-    if (need & NEED_P2) qr *= x.cp2;
-    const bool r2 = need & NEED_R2, p2 = need & NEED_P2;
-    dr0 = r2 ? x.cr1 * x.cr2 : x.cr1; dr1 = r2 ? x.cr0 * x.cr2 : x.cr0; dr2 = r2 ? x.cr0 * x.cr1 : Sc(0.0);
-    dp0 = p2 ? x.cp1 * x.cp2 : x.cp1; dp1 = p2 ? x.cp0 * x.cp2 : x.cp0; dp2 = p2 ? x.cp0 * x.cp1 : Sc(0.0);
-  }
+  const Sc qf = kfM * x.cr0 * x.cr1 * x.cr2, qr = krM * x.cp0 * x.cp1 * x.cp2;
   Sc dqdM = Sc(0.0);
   if (TYPE == 1) dqdM = x.qn;
   if (TYPE == 2) dqdM = x.dlnk_dlnM * x.q * x.iM;
   // [M] depends on T through the total concentration p/(Ru T)
   s[dq_off + r] = sfma(x.dlnkf_dT, qf, -((x.dlnkf_dT - x.dlnKc_dT) * qr)) - dqdM * sc.ctot * sc.invT;
+  // partial products: d(prod)/d(occurrence i) = product of the other occurrences
+  const Sc dr0 = x.cr1 * x.cr2, dr1 = x.cr0 * x.cr2, dr2 = x.cr0 * x.cr1;
+  const Sc dp0 = x.cp1 * x.cp2, dp1 = x.cp0 * x.cp2, dp2 = x.cp0 * x.cp1;
+  // a slot's factor is the sum over the slot species' occurrences; with no species repeated on a side in
+  // any active lane of the warp, it is one occurrence factor (or none): select it instead of adding
+  const bool any_rep = __any_sync(__activemask(), x.rep);
   for (int i = 0; i < x.scn; ++i) {
     const int mask = __ldg(M.dslot_mask + x.so + i);
     // elementary reactions list no colliders: their (efficiency - 1) is 0 and so is the [M] term
     Sc v = TYPE == 0 ? Sc(0.0) : __ldg(M.dslot_am1 + x.so + i) * dqdM;
     Sc fr, fq;
-    if (need & NEED_REP) {   // a slot species may occur more than once on a side: sum its factors
+    if (any_rep) {           // a slot species may occur more than once on a side: sum its factors
       fr = Sc(0.0); fq = Sc(0.0);
       if (mask & 1) fr += dr0;
       if (mask & 2) fr += dr1;

@@ -7,23 +7,24 @@
 
 namespace chemgb {
 
-// ---- discrete adjoint: resident warps pull cells; each has its own dual-number workspace in global
-// memory (the forward-layout size in Duals)
-__global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const double* __restrict__ p,
-                          const double* __restrict__ rec_h, const double* __restrict__ rec_ck,
-                          const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
-                          const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
-                          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head,
-                          const int* __restrict__ perm, Dual4* dual_ws, double* warp_ws, IntOpts o) {
+// ---- discrete adjoint: resident warps pull cells (longest tapes first).  Shared memory: the forward cell
+// layout; each warp's workspace (AdjLayout offsets) and dual-number workspace are in global memory.
+__global__ void __launch_bounds__(32, 8)
+k_adjoint(MechView M, AdjLayout A, int N, const double* __restrict__ p, const double* __restrict__ rec_h,
+          const double* __restrict__ rec_ck, const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
+          const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
+          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head, const int* __restrict__ perm,
+          Dual4* dual_ws, double* warp_ws, IntOpts o) {
   extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int gw = blockIdx.x * wpb + w;
-  double* s = smem + (size_t)w * A.total;
-  Dual4* dw = dual_ws + (size_t)gw * Ld.total;
+  const int lane = threadIdx.x % kWarp;
+  const int gw = blockIdx.x;   // one warp per block
+  double* s = smem;
+  Dual4* dw = dual_ws + (size_t)gw * A.L.total;
+  double* ws = warp_ws + (size_t)gw * A.total;
   const int m = M.m;
-  double* seg = warp_ws + (size_t)gw * ((size_t)K * m + 2 * (size_t)M.R);
-  double* GA = seg + (size_t)K * m;
-  double* GE = GA + M.R;
+  double* LAM = ws + A.LAM;
+  double* GA = ws + A.GA;
+  double* GE = ws + A.GE;
   while (true) {
     int c = 0;
     if (lane == 0) c = atomicAdd(head, 1);
@@ -31,12 +32,11 @@ __global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const d
     if (c >= N) break;
     c = perm[c];   // costliest cells (longest tapes) first
     const int na = rec_n[c];
-    double* LAM = s + A.LAM;
     for (int i = lane; i < m; i += kWarp) LAM[i] = (i == 0) ? gT[c] : gY[(size_t)(i - 1) * N + c];
     for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }
     __syncwarp();
     bool ok = na >= 0;
-    if (ok) ok = adjoint_cell(M, s, A, dw, Ld, p[c], na, rec_h, rec_ck, K, N, c, Grp1{lane}, o, seg, GA, GE);
+    if (ok) ok = adjoint_cell(M, s, ws, A, dw, p[c], na, rec_h, rec_ck, K, N, c, Grp1{lane}, o);
     if (!ok) {
       for (int i = lane; i < m; i += kWarp) LAM[i] = 0.0;
       for (int r = lane; r < M.R; r += kWarp) { GA[r] = 0.0; GE[r] = 0.0; }

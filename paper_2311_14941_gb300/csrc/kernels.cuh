@@ -33,14 +33,15 @@ void launch_integrate_persistent(int W, dim3 grid, dim3 block, size_t smem, cuda
                                  const int* perm, unsigned long long* head, int chunk, const IntOpts& o,
                                  const unsigned long long* stamp, unsigned long long budget_ns);
 
-// Discrete adjoint: resident warps pull cells (longest tapes first); per-warp dual-number workspace in
-// global memory.
-__global__ void k_adjoint(MechView M, AdjLayout A, CellLayout Ld, int N, const double* __restrict__ p,
-                          const double* __restrict__ rec_h, const double* __restrict__ rec_ck,
-                          const int* __restrict__ rec_n, int K, const double* __restrict__ gT,
-                          const double* __restrict__ gY, double* __restrict__ grad_cell, double* __restrict__ gT0,
-                          double* __restrict__ gY0, int* __restrict__ status, int* __restrict__ head,
-                          const int* __restrict__ perm, Dual4* dual_ws, double* warp_ws, IntOpts o);
+// Discrete adjoint: resident warps (one per block) pull cells, longest tapes first; shared memory holds the
+// forward cell layout, each warp's workspace (A.total doubles) and dual-number workspace are in global
+// memory.
+__global__ void k_adjoint(MechView M, AdjLayout A, int N, const double* __restrict__ p, const double* __restrict__ rec_h,
+                          const double* __restrict__ rec_ck, const int* __restrict__ rec_n, int K,
+                          const double* __restrict__ gT, const double* __restrict__ gY, double* __restrict__ grad_cell,
+                          double* __restrict__ gT0, double* __restrict__ gY0, int* __restrict__ status,
+                          int* __restrict__ head, const int* __restrict__ perm, Dual4* dual_ws, double* warp_ws,
+                          IntOpts o);
 
 __global__ void k_grad_reduce(int N, int P, const double* __restrict__ grad_cell, double* __restrict__ out1,
                               double* __restrict__ out2, int half);

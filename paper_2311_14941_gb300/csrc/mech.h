@@ -12,6 +12,11 @@ constexpr double kRu = 8.314462618;   // J/(mol K)
 constexpr double kP0 = 101325.0;      // Pa, standard state of Kc
 constexpr int kWarp = 32;
 constexpr int kMaxWarpsPerCell = 2;   // a cell is integrated by one warp or by two
+// Lane groups that integrate one cell, and the width their warp programs are built for:
+//   group 0: one warp (32 lanes), group 1: two warps of a block (64 lanes), group 2: half a warp
+//   (16 lanes; two cells share a warp, for mechanisms with few species).
+constexpr int kNumGroups = 3;
+constexpr int kGroupWidth[kNumGroups] = {32, 64, 16};
 
 // ---- species table: SP_STRIDE doubles per species
 //   [0] 1/W  [1] W  [2] T_mid  [3] unused
@@ -36,7 +41,7 @@ constexpr int RX_D = 12;
 //   [12] efficiency count  [13] derivative-slot offset  [14] derivative-slot count  [15] unused
 constexpr int RX_I = 16;
 
-// ---- warp programs, compiled for a group of `width` lanes (one warp per cell: 32, two: 64)
+// ---- warp programs, compiled for a group of `width` lanes (one warp per cell: 32, two: 64, half: 16)
 // Gather ("flattened segmented reduction"): step s, lane l executes op[s*width + l]:
 //   acc = fma(value(a, b), acc); if dst != NONE: out[dst] = acc, acc = 0.
 // dst >= PARTIAL_BIT selects the partial-sum buffer; a combine list then adds partials into outputs.
@@ -70,7 +75,7 @@ constexpr int kMaxJPass = 8;
 enum : int { JP_RB = 0, JP_RE = 1, JP_SB = 2, JP_CNT = 3 };   // first/end reaction, first slot, reactions
 
 struct MechView {
-  int width;                 // lanes of the programs below: 32 x warps per cell
+  int width;                 // lanes of the programs below: the lane group's width (32, 64 or 16)
   int n, R, m;
   int n_troe, n_tb;          // reactions [0, n_troe) Troe, [n_troe, n_troe + n_tb) third-body
   int nY;                    // Y-block entries of S (row-major by species, diagonal included)

@@ -26,13 +26,16 @@ def test_sample_without_counts_is_seeded_random_and_small_fields_are_whole():
 
 
 def test_search_space():
-    c = autotune.candidates({1: 7, 2: 3})
+    c = autotune.candidates({(1, 1): 7, (2, 1): 3, (1, 2): 13})
     assert {x["mode"] for x in c} == {0, 1} and {x["warps_per_cell"] for x in c} == {1, 2}
-    assert {x["block_cells"] for x in c if x["warps_per_cell"] == 1} == {1, 2, 4, 7}
+    one = [x for x in c if x["warps_per_cell"] == 1 and x["cells_per_warp"] == 1]
+    assert {x["block_cells"] for x in one} == {1, 2, 4, 7}
     assert {x["block_cells"] for x in c if x["warps_per_cell"] == 2} == {1, 2, 3}
+    # half-warp cells: whole warps only
+    assert {x["block_cells"] for x in c if x["cells_per_warp"] == 2} == {2, 4, 8, 12}
     assert all(x["chunk"] == 1 for x in c if x["mode"] == 0)
     assert len({json.dumps(x, sort_keys=True) for x in c}) == len(c)
-    assert {x["block_cells"] for x in autotune.candidates({1: 1})} == {1}
+    assert {x["block_cells"] for x in autotune.candidates({(1, 1): 1})} == {1}
 
 
 def test_block_bounds():
@@ -59,7 +62,8 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
     autotune._store("k2", {"warps_per_cell": 1, "mode": 0, "block_cells": 1, "chunk": 1})
     got = autotune._load()
     assert got["k1"]["block_cells"] == 2 and got["k2"]["mode"] == 0
-    assert autotune.launch_options(got["k1"]) == {"warps_per_cell": 2, "mode": 1, "block_cells": 2, "chunk": 1}
+    assert autotune.launch_options(got["k1"]) == {"warps_per_cell": 2, "cells_per_warp": 1, "mode": 1,
+                                                  "block_cells": 2, "chunk": 1}
 
 
 @pytest.mark.gpu
@@ -76,7 +80,7 @@ def test_gpu_launch_shapes_agree_and_tune_picks_one(tmp_path, monkeypatch):
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     N = F.n_cells
     ns_prev = torch.tensor(np.random.default_rng(2).integers(1, 300, N).astype(np.int32), device=dev)
-    space = autotune.candidates({w: h.info["max_block_cells"][w - 1] for w in (1, 2)})
+    space = autotune.candidates({g: h.info["max_block_cells"][i] for i, g in enumerate(autotune.GROUPS)})
     optin = torch.cuda.get_device_properties(0).shared_memory_per_block_optin
     assert all(h.info["max_block_cells"][w - 1] <= autotune.max_block_cells(h.info["smem_per_cell"], optin, w)
                for w in (1, 2))
@@ -89,15 +93,18 @@ def test_gpu_launch_shapes_agree_and_tune_picks_one(tmp_path, monkeypatch):
         st = torch.zeros(N, dtype=torch.int32, device=dev)
         h.integrate(T, t(F.p), Y, t(F.dt), hio, ns, st, **c)
         out = (T.cpu().numpy(), Y.cpu().numpy(), hio.cpu().numpy(), ns.cpu().numpy(), st.cpu().numpy())
-        w = c["warps_per_cell"]
+        w = (c["warps_per_cell"], c["cells_per_warp"])
         if w not in ref:
             ref[w] = out
         for a, b in zip(out, ref[w]):
             assert np.array_equal(a, b), c
-    assert np.all(ref[1][4] == 0) and np.array_equal(ref[1][4], ref[2][4])
-    big = np.abs(ref[1][1]) > 1e-12
-    assert np.allclose(ref[1][0], ref[2][0], rtol=1e-6, atol=0)
-    assert np.allclose(ref[1][1][big], ref[2][1][big], rtol=1e-5, atol=0)
+    a = ref[(1, 1)]
+    big = np.abs(a[1]) > 1e-12
+    for g in ((2, 1), (1, 2)):
+        b = ref[g]
+        assert np.all(a[4] == 0) and np.array_equal(a[4], b[4])
+        assert np.allclose(a[0], b[0], rtol=1e-6, atol=0)
+        assert np.allclose(a[1][big], b[1][big], rtol=1e-5, atol=0)
     r = autotune.tune(h, t(F.T), t(F.p), t(F.Y.reshape(-1)), t(F.dt), ns_prev, sample=1024)
     opts = autotune.launch_options(r)
     assert opts in [dict((k, x[k]) for k in autotune.KEYS) for x in space] or opts["block_cells"] == 0

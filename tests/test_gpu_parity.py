@@ -178,14 +178,16 @@ def _compare_integration(o, g, r, F, max_flip_frac, method=0):
     return len(flips)
 
 
-@pytest.mark.parametrize("wpc,method", [(1, 0), (2, 0), (1, 1), (1, 2), (2, 2)])
-def test_integrate_parity_small_full_config(dev, wpc, method):
+@pytest.mark.parametrize("wpc,method,cpw,mode", [(1, 0, 1, 0), (2, 0, 1, 0), (1, 1, 1, 0), (1, 2, 1, 0), (2, 2, 1, 0),
+                                              (1, 0, 2, 0), (1, 0, 2, 1), (1, 2, 2, 1)])
+def test_integrate_parity_small_full_config(dev, wpc, method, cpw, mode):
     """1024 cells, 10 species / 27 reactions, p = 1 atm, T ~ U(900, 2200) K, Dirichlet Y, dt = 1e-5 s;
-    one or two warps per cell; RODAS3 (method 0), ROS2 (method 1) or RODAS4 (method 2)."""
+    one or two warps per cell, or two cells per warp (plain and sorted-queue launches); RODAS3 (method
+    0), ROS2 (method 1) or RODAS4 (method 2)."""
     m, h, o = mech("small")
     F = synth.field_uniform_random(m, 1024, seed=1)
     r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=8000, method=method)
-    g = _integrate_gpu(h, F, dev, trace_cap=8000, warps_per_cell=wpc, method=method)
+    g = _integrate_gpu(h, F, dev, trace_cap=8000, warps_per_cell=wpc, method=method, cells_per_warp=cpw, mode=mode)
     _compare_integration(o, g, r, F, 0.02, method)
     assert np.all(g["status"] == 0)
 

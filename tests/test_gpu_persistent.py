@@ -121,3 +121,39 @@ def test_calls_leave_the_callers_current_device(dev):
                 z(torch.int32), mode=1, stream=torch.cuda.current_stream(d1))
     torch.cuda.synchronize(d1)
     assert torch.cuda.current_device() == 0
+
+
+@pytest.fixture(scope="module")
+def small():
+    m = synth.mechanism_small()
+    return m, chem.create(m, 0)
+
+
+def test_two_cells_per_warp_plain_equals_persistent(small, dev):
+    """Two cells sharing a warp (16 lanes each): the plain launch and the sorted queue (pairs of
+    consecutive queue cells per warp, several chunk sizes and block shapes, ragged cell counts) give
+    bit-identical results; they agree with one warp per cell to rounding."""
+    m, h = small
+    F = synth.field_uniform_random(m, 2049, seed=12)
+    F.dt[:] = 10.0 ** np.random.default_rng(3).uniform(-7, -4, F.n_cells)
+    plain = _run(h, F, dev, mode=0, cells_per_warp=2)
+    for kw in (dict(), dict(chunk=3, block_cells=6), dict(block_cells=3)):
+        _same(plain, _run(h, F, dev, mode=1, cells_per_warp=2, **kw))
+        _same(plain, _run(h, F, dev, nsub_in=plain["nsub"], mode=1, cells_per_warp=2, **kw))
+    for n in (1, 2, 3, 31, 33):
+        S = F.subset(np.arange(n))
+        _same(_run(h, S, dev, mode=0, cells_per_warp=2), _run(h, S, dev, mode=1, cells_per_warp=2))
+    one = _run(h, F, dev, mode=0, warps_per_cell=1, cells_per_warp=1)
+    assert np.array_equal(one["status"], plain["status"]) and np.all(plain["status"] == 0)
+    same = one["nsub"] == plain["nsub"]
+    assert same.mean() > 0.97
+    assert np.max(np.abs(one["T"][same] - plain["T"][same]) / one["T"][same]) < 1e-9
+
+
+def test_two_cells_per_warp_rejects_two_warps(small, dev):
+    m, h = small
+    F = synth.field_uniform_random(m, 4, seed=1)
+    with pytest.raises(chem.ChemError):
+        _run(h, F, dev, warps_per_cell=2, cells_per_warp=2)
+    with pytest.raises(chem.ChemError):
+        _run(h, F, dev, cells_per_warp=3)

@@ -74,12 +74,15 @@ def _run_solve(prog, LU, dinv, x, width=32):
             x[t] = x[t] * dinv[a]
 
 
-@pytest.mark.parametrize("wpc", [1, 2])
-def test_programs_reproduce_dense_solve(compiled, wpc):
-    """I/(h gamma) - S factored and solved by the warp programs (one or two warps per cell) equals numpy's
-    dense solve."""
+PLANS = {32: (0, 1, 6), 64: (8, 9, 10), 16: (11, 12, 13)}   # width -> elimination, solve, transposed solve
+
+
+@pytest.mark.parametrize("width", [32, 64, 16])
+def test_programs_reproduce_dense_solve(compiled, width):
+    """I/(h gamma) - S factored and solved by the warp programs (one warp, two warps or half a warp per
+    cell) equals numpy's dense solve."""
     m_, h = compiled
-    width, plan_lu, plan_sv = (32, 0, 1) if wpc == 1 else (64, 8, 9)
+    plan_lu, plan_sv, _ = PLANS[width]
     rng = np.random.default_rng(1)
     info = h.info
     S_csr = rng.standard_normal(info["nnz_S"])
@@ -106,11 +109,11 @@ def test_programs_reproduce_dense_solve(compiled, wpc):
         assert np.max(np.abs(x - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("wpc", [1, 2])
-def test_transposed_program_solves_the_transpose(compiled, wpc):
+@pytest.mark.parametrize("width", [32, 64, 16])
+def test_transposed_program_solves_the_transpose(compiled, width):
     """The transposed substitution program applied to the same factor solves A^T x = b."""
     m_, h = compiled
-    width, plan_lu, plan_t = (32, 0, 6) if wpc == 1 else (64, 8, 10)
+    plan_lu, _, plan_t = PLANS[width]
     rng = np.random.default_rng(2)
     S_csr = rng.standard_normal(h.info["nnz_S"])
     S_int, S_dense = _internal_S_dense(h, S_csr)

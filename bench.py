@@ -46,8 +46,8 @@ METHODS = {"rodas3": 0, "ros2": 1, "rodas4": 2}   # chem_integrate_opts.method
 PROFILED_TRAFFIC_PER_CELL = {"jet": 8.896512e6 / 16384}
 PROFILED_SOURCES = "5a5ebe9487393148"
 REF_CELLS = 256   # reference arm: cells per step (at least 16 per host core)
-KERNEL_SOURCES = ["kern_forward.cu", "kernels.cuh", "compile.cpp", "device.cuh", "elementary_tables.h", "mech.h",
-                  "scalar.cuh"]
+KERNEL_SOURCES = ["kern_forward.cuh", "kern_fwd_warp.cu", "kernels.cuh", "compile.cpp", "device.cuh",
+                  "elementary_tables.h", "mech.h", "scalar.cuh"]
 
 
 def kernel_sources_digest():
@@ -347,10 +347,12 @@ def run_reference(args):
 class Runner:
     """Timed chem_integrate steps on one workload: buffers, the step schedule and the work counts."""
 
-    def __init__(self, h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, cells_per_warp=0):
+    def __init__(self, h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, cells_per_warp=0,
+                 tab_tol=0.0):
         import torch
         self.h, self.F, self.evolving, self.dev, self.meth, self.oc = h, F, evolving, dev, meth, oc
         self.cpw = cells_per_warp
+        self.tab = dict(tabulate=1, tab_tol=tab_tol) if tab_tol > 0 else {}
         self.world, self.flush, self.clocks_path, self.local = world, flush, clocks_path, local
         N = F.n_cells
         self.N = N
@@ -377,7 +379,7 @@ class Runner:
 
     def integrate(self, mode):
         self.h.integrate(self.T, self.P, self.Y, self.DT, self.hio, self.ns, self.st, rtol=RTOL, atol=ATOL,
-                         mode=mode, naccept=self.nacc, method=self.meth, cells_per_warp=self.cpw)
+                         mode=mode, naccept=self.nacc, method=self.meth, cells_per_warp=self.cpw, **self.tab)
 
     def step(self, mode):
         """One flow step.  Evolving: the next step of the episode.  Otherwise: from the initial state again,
@@ -476,7 +478,7 @@ class Runner:
             self.P.copy_(Ph, non_blocking=True)
             self.DT.copy_(Dh, non_blocking=True)
             self.h.integrate(self.T, self.P, self.Y, self.DT, self.hio, self.ns, self.st, rtol=RTOL, atol=ATOL,
-                             mode=mode, method=self.meth, cells_per_warp=self.cpw)
+                             mode=mode, method=self.meth, cells_per_warp=self.cpw, **self.tab)
             To.copy_(self.T, non_blocking=True)
             Yo.copy_(self.Y, non_blocking=True)
             Ho.copy_(self.hio, non_blocking=True)
@@ -514,6 +516,9 @@ def main():
                     help="Rosenbrock method of the forward integration (the headline is RODAS3)")
     ap.add_argument("--cells-per-warp", type=int, default=0, choices=[0, 1, 2],
                     help="2: two cells share a warp (16 lanes each); 1: one cell per warp; 0: the library's choice")
+    ap.add_argument("--tabulate", type=float, default=0.0,
+                    help="evaluate the costly temperature functions from tables of this relative tolerance "
+                         "(an approximation; 0: exact)")
     args = ap.parse_args()
     global RTOL
     RTOL = args.rtol
@@ -542,7 +547,7 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     import tempfile
     clocks_path = os.path.join(tempfile.gettempdir(), f"chem_bench_clocks_r{rank}_{os.getpid()}.csv")
-    run = Runner(h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, args.cells_per_warp)
+    run = Runner(h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, args.cells_per_warp, args.tabulate)
 
     # headline mode first (W warm-up, K timed), then the other mode on the first K' of the same steps:
     # for an evolving field, the first episode's steps 2-10 (bit-identical states in both modes)
@@ -590,7 +595,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(config(args.workload, args.mode), n_cells=N,
                        warps_per_cell=int(h.info["auto_warps_per_cell"]), method=args.method,
-                       cells_per_warp=args.cells_per_warp or int(h.info["auto_cells_per_warp"])),
+                       cells_per_warp=args.cells_per_warp or int(h.info["auto_cells_per_warp"]),
+                       tabulated_temperature_functions=(f"tables of relative tolerance {args.tabulate:g} (an "
+                                                        "approximation)" if args.tabulate > 0 else "exact")),
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -607,6 +614,8 @@ def main():
     }
     if res["episode_steps"] is not None:
         line["episode_step_of_timed_steps"] = res["episode_steps"]
+    if args.tabulate > 0:
+        line["tabulated"] = tabulation_deviation(run, args.tabulate)
     if res_other is not None:
         o = {"value": world * N * k_other / res_other["t"], "unit": "reactor-steps/s", "steps": k_other,
              "ms_per_step": 1e3 * res_other["t"] / k_other, "step_ms": res_other["step_ms"],
@@ -630,6 +639,28 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def tabulation_deviation(run, tol):
+    """The tables' effect on one flow step from the initial field: largest relative difference of T and of
+    every Y > 1e-12 between the tabulated and the exact integration (cells with the same substep count),
+    and the share of cells whose step sequence changed."""
+    import torch
+    out = {}
+    for key, kw in (("exact", {}), ("tab", run.tab)):
+        run.reset()
+        run.h.integrate(run.T, run.P, run.Y, run.DT, run.hio, run.ns, run.st, rtol=RTOL, atol=ATOL, mode=1,
+                        method=run.meth, cells_per_warp=run.cpw, **kw)
+        torch.cuda.synchronize()
+        out[key] = (run.T.cpu().numpy(), run.Y.cpu().numpy().reshape(-1, run.N), run.ns.cpu().numpy())
+    (Te, Ye, ne), (Tt, Yt, nt) = out["exact"], out["tab"]
+    same = ne == nt
+    big = np.abs(Ye) > 1e-12
+    rel = np.where(big, np.abs(Yt - Ye) / np.where(big, np.abs(Ye), 1.0), 0.0)
+    return {"tab_tol": tol, "max_rel_dT_same_steps": float(np.max(np.abs(Tt - Te)[same] / Te[same], initial=0.0)),
+            "max_rel_dY_same_steps": float(rel[:, same].max(initial=0.0)),
+            "cells_with_other_step_sequence": float(1.0 - same.mean()),
+            "note": "one flow step from the initial field, persistent mode, tabulated vs exact"}
 
 
 def jet_key(h, dev, meth, oc, world, flush, clocks_path, local, rank):

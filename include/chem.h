@@ -165,6 +165,21 @@ typedef struct {
                              an even count; in mode 1 the two halves of a warp take consecutive cells of the
                              sorted queue); 1 = one cell per warp (or per two warps); 0: automatic (see
                              chem_info).  Results agree with one warp per cell to rounding. */
+  int tabulate;           /* chem_integrate, chem_integrate_noalloc, chem_integrate_mapped: 1 = evaluate the
+                             costly temperature functions from tables (an approximation; Sec. 2.5: SpeedCHEM
+                             interpolates costly thermodynamic functions with polynomials of optimal
+                             degree): every species' exp(+-g_k), g_k = h_k/(Ru T) - s_k/Ru, every forward rate
+                             coefficient (the high-pressure limit of a fall-off reaction) and every Troe centre
+                             F_cent, for 250 K <= T < 4000 K, as polynomials in 1/T on 640 equal intervals of
+                             1/T, one degree per class of functions (the smallest up to 8 that keeps every
+                             function within tab_tol, relative, at 17 points of every interval).  Outside
+                             that range, the fall-off ratio k_0 [M] / k_inf, all other quantities and the
+                             Jacobian's derivatives stay exact.  The tables are built on the host and kept
+                             in the handle at the first call with a new tab_tol (about a second for 53
+                             species / 325 reactions); chem_integrate_noalloc uses tables built before and
+                             returns CHEM_EINVAL otherwise.  The tables hold the description's parameters:
+                             CHEM_EINVAL after chem_set_params shifted them.  0: exact (default). */
+  double tab_tol;         /* relative error bound of the tables; 0: 1e-10 */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,

@@ -75,14 +75,70 @@ namespace {
 
 /* Optional parameter shifts: k_f,r of reaction j multiplied by exp(dlnA[j]) (both limits for Troe) and
    every activation energy of reaction j shifted by dEa[j]; used for complex-step sensitivities. */
+struct OTab;
+
 template <class S> struct Perturb {
   const S* dlnA = nullptr;
   const S* dEa = nullptr;
+  const OTab* tab = nullptr;   // tabulated temperature functions (real arithmetic only), see below
 };
+
+/* ---------------------------------------------------------------- tabulated temperature functions
+   An opt-in approximation (Sec. 2.5: SpeedCHEM evaluates costly thermodynamic functions by interpolation
+   of optimal degree).  Reading taken here: the temperature functions that each cost one or more
+   exponentials -- every species' exp(g_k) and exp(-g_k) with g_k = h_k/(Ru T) - s_k/Ru (the factors of
+   the equilibrium constants), every reaction's forward rate coefficient (the high-pressure limit of a
+   fall-off reaction) and each fall-off reaction's Troe centre F_cent -- are replaced, for
+   kTabTlo <= T < kTabThi, by piecewise polynomials in u = 1/T:
+     - kTabNI equal intervals of u over [1/kTabThi, 1/kTabTlo] (T = 1000 K, the usual NASA-7 switch, is a
+       boundary);
+     - on interval j, with tau = 2 (u - u_j)/du - 1 in [-1, 1], the polynomial of degree d through the
+       d + 1 Chebyshev points tau_i = cos(pi (2i + 1) / (2d + 2)), kept as monomial coefficients in tau;
+     - one degree per class of functions (the four classes above), the smallest d in 1..8 for which every
+       function of the class is within the relative tolerance of its exact value at 17 equispaced points
+       of every interval ("optimal degree"); a class that no degree up to 8 meets stays exact.
+   Outside the range the exact functions are used.  The fall-off variable P_r = k_0 [M] / k_inf stays
+   exact (a ratio of two Arrhenius forms), and so do the logarithmic temperature derivatives of the
+   Jacobian. */
+constexpr int kTabNI = 640;
+constexpr double kTabTlo = 250.0, kTabThi = 4000.0;
+constexpr int kTabMaxDeg = 8;
+enum { TAB_E = 0, TAB_IE = 1, TAB_KF = 2, TAB_FC = 3, TAB_CLASSES = 4 };
+
+struct OTab {
+  double tol = 0.0;
+  double u_lo = 0.0, du = 0.0;
+  int deg[TAB_CLASSES] = {0, 0, 0, 0};          // 0: the class is evaluated exactly
+  int nfun[TAB_CLASSES] = {0, 0, 0, 0};
+  std::vector<double> coef[TAB_CLASSES];        // [function][interval][deg + 1]
+  std::vector<int> troe_slot;                   // reaction -> index among the fall-off reactions, -1
+};
+
+/* Interval and local coordinate of T; false outside the tabulated range. */
+inline bool tab_locate(const OTab& t, double T, int& j, double& tau) {
+  if (!(T >= kTabTlo && T < kTabThi)) return false;
+  const double x = (1.0 / T - t.u_lo) / t.du;
+  j = std::min(kTabNI - 1, std::max(0, (int)std::floor(x)));
+  tau = 2.0 * (x - j) - 1.0;
+  return true;
+}
+
+inline double tab_poly(const double* c, int d, double tau) {
+  double v = c[d];
+  for (int i = d - 1; i >= 0; --i) v = v * tau + c[i];
+  return v;
+}
+
+/* Tabulated value of function f of class cls at (j, tau). */
+inline double tab_value(const OTab& t, int cls, int f, int j, double tau) {
+  const int d = t.deg[cls];
+  return tab_poly(&t.coef[cls][((size_t)f * kTabNI + j) * (d + 1)], d, tau);
+}
 
 /* ---------------------------------------------------------------- thermo (NASA-7) */
 template <class S> struct Thermo {
   std::vector<S> cp_R, h_RT, s_R, dcp_R_dT;
+  std::vector<double> E, iE;   // tabulated exp(g_k), exp(-g_k) (filled by rates() when a table is in use)
 };
 
 template <class S> void thermo(const OMech& m, const S& T, Thermo<S>& th) {
@@ -137,6 +193,19 @@ void rates(const OMech& m, const S& T, double p, const Thermo<S>& th, const Mix<
   rr.dlnkf_dT.assign(R, S(0)); rr.dlnkf_dlnM.assign(R, S(0)); rr.dlnKc_dT.assign(R, S(0));
   rr.nu.assign((size_t)R * n, 0.0);
   (void)p;
+  // tabulated temperature functions: real arithmetic, no parameter shifts, T inside the table
+  int tj = 0;
+  double ttau = 0.0;
+  const bool tab = std::is_same<S, double>::value && pt.tab && !pt.dlnA && !pt.dEa &&
+                   tab_locate(*pt.tab, re(T), tj, ttau);
+  std::vector<double> tE, tiE;
+  if (tab && pt.tab->deg[TAB_E] > 0 && pt.tab->deg[TAB_IE] > 0) {
+    tE.resize(n); tiE.resize(n);
+    for (int k = 0; k < n; ++k) {
+      tE[k] = tab_value(*pt.tab, TAB_E, k, tj, ttau);
+      tiE[k] = tab_value(*pt.tab, TAB_IE, k, tj, ttau);
+    }
+  }
   for (int r = 0; r < R; ++r) {
     for (int i = m.rptr[r]; i < m.rptr[r + 1]; ++i) rr.nu[(size_t)r * n + m.rsp[i]] -= m.rnu[i];
     for (int i = m.pptr[r]; i < m.pptr[r + 1]; ++i) rr.nu[(size_t)r * n + m.psp[i]] += m.pnu[i];
@@ -144,7 +213,8 @@ void rates(const OMech& m, const S& T, double p, const Thermo<S>& th, const Mix<
     S dEa = pt.dEa ? pt.dEa[r] : S(0.0);
     S Ea = m.Ea[r] + dEa;
     // modified Arrhenius
-    S kinf = m.A[r] * std::exp(dlnA) * std::pow(T, m.b[r]) * std::exp(-Ea / (kRu * T));
+    const S kinf_exact = m.A[r] * std::exp(dlnA) * std::pow(T, m.b[r]) * std::exp(-Ea / (kRu * T));
+    const S kinf = (tab && pt.tab->deg[TAB_KF] > 0) ? S(tab_value(*pt.tab, TAB_KF, r, tj, ttau)) : kinf_exact;
     S dlnkinf_dT = m.b[r] / T + Ea / (kRu * T * T);
     // third-body concentration
     S M = 0.0;
@@ -159,9 +229,10 @@ void rates(const OMech& m, const S& T, double p, const Thermo<S>& th, const Mix<
       const double* tr = &m.troe[4 * r];
       const double* lw = &m.low[3 * r];
       S Ea0 = lw[2] + dEa;
+      const int ts = pt.tab ? pt.tab->troe_slot[r] : -1;
       S k0 = lw[0] * std::exp(dlnA) * std::pow(T, lw[1]) * std::exp(-Ea0 / (kRu * T));
       S dlnk0_dT = lw[1] / T + Ea0 / (kRu * T * T);
-      S Pr = k0 * M / kinf;
+      S Pr = k0 * M / kinf_exact;
       if (re(Pr) == 0.0) {
         kf = 0.0; dlnkf_dT = 0.0; dlnkf_dlnM = 0.0;
       } else {
@@ -172,6 +243,7 @@ void rates(const OMech& m, const S& T, double p, const Thermo<S>& th, const Mix<
           Fc += std::exp(-T2 / T);
           dFc_dT += T2 / (T * T) * std::exp(-T2 / T);
         }
+        if (tab && pt.tab->deg[TAB_FC] > 0) Fc = S(tab_value(*pt.tab, TAB_FC, ts, tj, ttau));
         S Lc = std::log10(Fc);
         S c = -0.4 - 0.67 * Lc;
         S nn = 0.75 - 1.27 * Lc;
@@ -209,7 +281,17 @@ void rates(const OMech& m, const S& T, double p, const Thermo<S>& th, const Mix<
         dH += v * th.h_RT[k];
         dnu += v;
       }
-      S Kc = std::exp(-dG) * std::pow(kP0 / (kRu * T), dnu);
+      S emdG = std::exp(-dG);
+      if (!tE.empty()) {   // exp(-dG) = prod over products exp(-g)^nu * prod over reactants exp(g)^|nu|
+        double e = 1.0;
+        for (int k = 0; k < n; ++k) {
+          const double v = rr.nu[(size_t)r * n + k];
+          if (v > 0.0) e *= product_pow(tiE[k], (int)v);
+          if (v < 0.0) e *= product_pow(tE[k], (int)(-v));
+        }
+        emdG = S(e);
+      }
+      S Kc = emdG * std::pow(kP0 / (kRu * T), dnu);
       rr.kr[r] = kf / Kc;
       rr.dlnKc_dT[r] = (dH - dnu) / T;
     }
@@ -221,6 +303,91 @@ void rates(const OMech& m, const S& T, double p, const Thermo<S>& th, const Mix<
     rr.qf[r] = rr.kf[r] * Mfac * Pf;
     rr.qr[r] = m.rev[r] ? rr.kr[r] * Mfac * Pb : S(0.0);
   }
+}
+
+/* The exact value of function f of class cls at T (the functions the table stands for). */
+double tab_exact(const OMech& m, const OTab& t, int cls, int f, double T) {
+  if (cls == TAB_E || cls == TAB_IE) {
+    const double* a = (T < m.Tmid[f]) ? &m.lo[7 * f] : &m.hi[7 * f];
+    const double T2 = T * T, T3 = T2 * T, T4 = T3 * T;
+    const double hRT = a[0] + a[1] * T / 2.0 + a[2] * T2 / 3.0 + a[3] * T3 / 4.0 + a[4] * T4 / 5.0 + a[5] / T;
+    const double sR = a[0] * std::log(T) + a[1] * T + a[2] * T2 / 2.0 + a[3] * T3 / 3.0 + a[4] * T4 / 4.0 + a[6];
+    return cls == TAB_E ? std::exp(hRT - sR) : std::exp(sR - hRT);
+  }
+  if (cls == TAB_KF) return m.A[f] * std::pow(T, m.b[f]) * std::exp(-m.Ea[f] / (kRu * T));
+  int r = 0;   // the f-th fall-off reaction
+  for (int q = 0; q < m.R; ++q) if (t.troe_slot[q] == f) { r = q; break; }
+  const double* tr = &m.troe[4 * r];
+  double Fc = (1.0 - tr[0]) * std::exp(-T / tr[1]) + tr[0] * std::exp(-T / tr[2]);
+  if (tr[3] > 0.0) Fc += std::exp(-tr[3] / T);
+  return Fc;
+}
+
+/* Monomial coefficients (in tau) of the degree-d polynomial through the Chebyshev points of the interval
+   [u0, u0 + du] of function f. */
+void tab_fit(const OMech& m, const OTab& t, int cls, int f, double u0, int d, double* c) {
+  const double pi = 3.14159265358979323846;
+  std::vector<double> fv(d + 1), tv(d + 1), a(d + 1, 0.0);
+  for (int i = 0; i <= d; ++i) {
+    tv[i] = std::cos(pi * (2.0 * i + 1.0) / (2.0 * d + 2.0));
+    fv[i] = tab_exact(m, t, cls, f, 1.0 / (u0 + 0.5 * (tv[i] + 1.0) * t.du));
+  }
+  // Chebyshev coefficients a_k = (2/(d+1)) sum_i f_i T_k(tau_i), a_0 halved
+  for (int k = 0; k <= d; ++k) {
+    double acc = 0.0;
+    for (int i = 0; i <= d; ++i) acc += fv[i] * std::cos(k * std::acos(tv[i]));
+    a[k] = 2.0 * acc / (d + 1);
+  }
+  a[0] *= 0.5;
+  // sum_k a_k T_k(tau) in monomials: T_0 = 1, T_1 = tau, T_{k+1} = 2 tau T_k - T_{k-1}
+  std::vector<double> Tm1(d + 1, 0.0), T0(d + 1, 0.0), Tn(d + 1, 0.0);
+  for (int i = 0; i <= d; ++i) c[i] = 0.0;
+  T0[0] = 1.0;
+  for (int k = 0; k <= d; ++k) {
+    for (int i = 0; i <= d; ++i) c[i] += a[k] * T0[i];
+    std::fill(Tn.begin(), Tn.end(), 0.0);
+    for (int i = 0; i < d; ++i) Tn[i + 1] += (k == 0 ? 1.0 : 2.0) * T0[i];
+    if (k > 0)
+      for (int i = 0; i <= d; ++i) Tn[i] -= Tm1[i];
+    Tm1 = T0;
+    T0 = Tn;
+  }
+}
+
+/* Builds the tables of every class: the smallest degree that meets tol for every function of the class on
+   every interval, checked at 17 equispaced points per interval against the exact functions. */
+OTab* tab_build(const OMech& m, double tol) {
+  OTab* t = new OTab();
+  t->tol = tol;
+  t->u_lo = 1.0 / kTabThi;
+  t->du = (1.0 / kTabTlo - 1.0 / kTabThi) / kTabNI;
+  t->troe_slot.assign(m.R, -1);
+  int nt = 0;
+  for (int r = 0; r < m.R; ++r) if (m.type[r] == 2) t->troe_slot[r] = nt++;
+  const int nf[TAB_CLASSES] = {m.n, m.n, m.R, nt};
+  for (int cls = 0; cls < TAB_CLASSES; ++cls) {
+    t->nfun[cls] = nf[cls];
+    t->deg[cls] = 0;
+    if (nf[cls] == 0) continue;
+    for (int d = 1; d <= kTabMaxDeg; ++d) {
+      std::vector<double> cf((size_t)nf[cls] * kTabNI * (d + 1));
+      bool ok = true;
+      for (int f = 0; f < nf[cls] && ok; ++f)
+        for (int j = 0; j < kTabNI && ok; ++j) {
+          const double u0 = t->u_lo + j * t->du;
+          double* c = &cf[((size_t)f * kTabNI + j) * (d + 1)];
+          tab_fit(m, *t, cls, f, u0, d, c);
+          for (int k = 0; k <= 16 && ok; ++k) {
+            const double tau = -1.0 + k / 8.0;
+            const double ex = tab_exact(m, *t, cls, f, 1.0 / (u0 + 0.5 * (tau + 1.0) * t->du));
+            const double ap = tab_poly(c, d, tau);
+            ok = std::fabs(ap - ex) <= tol * std::fabs(ex);
+          }
+        }
+      if (ok) { t->deg[cls] = d; t->coef[cls].swap(cf); break; }
+    }
+  }
+  return t;
 }
 
 /* ---------------------------------------------------------------- right-hand side */
@@ -556,7 +723,7 @@ struct Controls {
 /* Adaptive integration of one cell over [0, dt].  y (m values) is overwritten with the result. */
 int integrate_cell(const OMech& m, double p, double* y, double dt, const Controls& cc, double h_in, double* h_out,
                    int* nsub, int* nacc, std::vector<double>* tr_h, std::vector<int>* tr_acc,
-                   const Tableau& tb = kRodas3) {
+                   const Tableau& tb = kRodas3, const OTab* tab = nullptr) {
   const int mm = m.n + 1;
   *nsub = 0; *nacc = 0;
   bool ok = finite_(y[0]) && y[0] > 0.0 && finite_(p) && p > 0.0 && finite_(dt) && dt >= 0.0;
@@ -570,6 +737,7 @@ int integrate_cell(const OMech& m, double p, double* y, double dt, const Control
   int nonfinite = 0;
   Eval<double> ev;
   Perturb<double> pt;
+  pt.tab = tab;
   std::vector<double> ynew(mm), yerr(mm);
   while (t < dt) {
     if (*nsub >= cc.max_steps) { *h_out = h; return ST_MAXSTEPS; }
@@ -744,6 +912,36 @@ int oracle_replay(const OMech* m, double p, double* y, const double* hs, int nh,
   return replay_cell(*m, p, pt, y, hs, nh, method_tableau(method)) ? 0 : 1;
 }
 
+/* The same with the tabulated temperature functions of tab (oracle_tab_build). */
+int oracle_replay_tab(const OMech* m, double p, double* y, const double* hs, int nh, int method, const void* tab) {
+  Perturb<double> pt;
+  pt.tab = (const OTab*)tab;
+  return replay_cell(*m, p, pt, y, hs, nh, method_tableau(method)) ? 0 : 1;
+}
+
+/* Tabulated temperature functions of the mechanism for relative tolerance tol (see tab_build); the caller
+   frees them with oracle_tab_free. */
+void* oracle_tab_build(const OMech* m, double tol) { return tab_build(*m, tol); }
+void oracle_tab_free(void* tab) { delete (OTab*)tab; }
+
+/* deg[4]: the degree of each class (0: exact), range[4]: T_lo, T_hi, u_lo, du; returns the interval count. */
+int oracle_tab_info(const void* tab, int* deg, double* range) {
+  const OTab* t = (const OTab*)tab;
+  for (int c = 0; c < TAB_CLASSES; ++c) deg[c] = t->deg[c];
+  range[0] = kTabTlo; range[1] = kTabThi; range[2] = t->u_lo; range[3] = t->du;
+  return kTabNI;
+}
+
+/* Value of function f of class cls (0 exp(g_k), 1 exp(-g_k), 2 k_f of reaction f, 3 F_cent of the f-th
+   fall-off reaction) at T: tabulated inside the range (for a tabulated class), else exact. */
+double oracle_tab_eval(const OMech* m, const void* tab, int cls, int f, double T) {
+  const OTab* t = (const OTab*)tab;
+  int j = 0;
+  double tau = 0.0;
+  if (t->deg[cls] > 0 && tab_locate(*t, T, j, tau)) return tab_value(*t, cls, f, j, tau);
+  return tab_exact(*m, *t, cls, f, T);
+}
+
 /* Complex-step derivative of the replayed final state with respect to one input:
    kind 0: ln A_j, kind 1: Ea_j, kind 2: initial state component y0_j.  dy[m] = d y_final / d theta. */
 int oracle_replay_sens_cs(const OMech* m, double p, const double* y0, const double* hs, int nh, int kind, int j,
@@ -765,9 +963,21 @@ int oracle_replay_sens_cs(const OMech* m, double p, const double* y0, const doub
    busy).
    h_io: in initial step (<= 0: default), out last proposed step.  Optional trace [trace_cap*N]: attempt i
    of cell c at trace[i*N + c], +h accepted, -h rejected, 0 after the last.  Returns the thread count. */
+int oracle_integrate_batch_tab(const OMech* m, int N, double* T, const double* p, double* Y, const double* dt,
+                               double rtol, double atol, int max_steps, double* h_io, int* nsub, int* nacc,
+                               int* status, int nthreads, double* trace, int trace_cap, int method, const void* tab);
+
 int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, double* Y, const double* dt,
                            double rtol, double atol, int max_steps, double* h_io, int* nsub, int* nacc, int* status,
                            int nthreads, double* trace, int trace_cap, int method) {
+  return oracle_integrate_batch_tab(m, N, T, p, Y, dt, rtol, atol, max_steps, h_io, nsub, nacc, status, nthreads,
+                                    trace, trace_cap, method, nullptr);
+}
+
+/* The batch driver with the tabulated temperature functions of tab (NULL: exact). */
+int oracle_integrate_batch_tab(const OMech* m, int N, double* T, const double* p, double* Y, const double* dt,
+                               double rtol, double atol, int max_steps, double* h_io, int* nsub, int* nacc,
+                               int* status, int nthreads, double* trace, int trace_cap, int method, const void* tab) {
   const Tableau& tb = method_tableau(method);
   Controls cc = make_controls(rtol, atol, max_steps);
   const int mm = m->n + 1;
@@ -790,7 +1000,7 @@ int oracle_integrate_batch(const OMech* m, int N, double* T, const double* p, do
     std::vector<double> th;
     std::vector<int> ta;
     int st = integrate_cell(*m, p[c], y.data(), dt[c], cc, h_io ? h_io[c] : 0.0, &hout, &ns, &na,
-                            trace ? &th : nullptr, trace ? &ta : nullptr, tb);
+                            trace ? &th : nullptr, trace ? &ta : nullptr, tb, (const OTab*)tab);
     if (trace) {
       for (int i = 0; i < trace_cap; ++i)
         trace[(size_t)i * N + c] = i < (int)th.size() ? (ta[i] ? th[i] : -th[i]) : 0.0;

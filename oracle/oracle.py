@@ -50,6 +50,14 @@ def lib():
                                             C.c_double, _dp]
         L.oracle_integrate_batch.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
                                              C.c_int, _dp, _ip, _ip, _ip, C.c_int, _dp, C.c_int, C.c_int]
+        L.oracle_integrate_batch_tab.argtypes = L.oracle_integrate_batch.argtypes + [C.c_void_p]
+        L.oracle_replay_tab.argtypes = [C.c_void_p, C.c_double, _dp, _dp, C.c_int, C.c_int, C.c_void_p]
+        L.oracle_tab_build.argtypes = [C.c_void_p, C.c_double]
+        L.oracle_tab_build.restype = C.c_void_p
+        L.oracle_tab_free.argtypes = [C.c_void_p]
+        L.oracle_tab_info.argtypes = [C.c_void_p, _ip, _dp]
+        L.oracle_tab_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double]
+        L.oracle_tab_eval.restype = C.c_double
         _lib = L
     return _lib
 
@@ -165,9 +173,39 @@ class Oracle:
             out["trace_acc"] = ta[:L].copy()
         return out
 
-    def replay(self, y0, p, hs, method=0):
+    # -------------------------------------------------------------- tabulated temperature functions
+    def tab_build(self, tol=1e-10):
+        """Build (once per tolerance) the oracle's own tables of exp(+-g_k), k_f and F_cent; returns
+        (handle, degrees[4], interval count, range (T_lo, T_hi, u_lo, du))."""
+        if not hasattr(self, "_tabs"):
+            self._tabs = {}
+        if tol not in self._tabs:
+            t = self.L.oracle_tab_build(self._p, tol)
+            deg = np.zeros(4, dtype=np.int32)
+            rng = np.zeros(4)
+            ni = self.L.oracle_tab_info(t, _i(deg), _d(rng))
+            self._tabs[tol] = (t, deg, ni, rng)
+        return self._tabs[tol]
+
+    def tab_eval(self, tol, cls, f, T):
+        t = self.tab_build(tol)[0]
+        return self.L.oracle_tab_eval(self._p, t, cls, f, float(T))
+
+    def __del__(self):
+        try:
+            for t in getattr(self, "_tabs", {}).values():
+                self.L.oracle_tab_free(t[0])
+        except Exception:
+            pass
+
+    def replay(self, y0, p, hs, method=0, tab_tol=0.0):
         y = np.array(y0, dtype=np.float64)
         hs = np.ascontiguousarray(hs, dtype=np.float64)
+        if tab_tol > 0:
+            rc = self.L.oracle_replay_tab(self._p, p, _d(y), _d(hs), len(hs), method, self.tab_build(tab_tol)[0])
+            if rc:
+                raise RuntimeError("singular iteration matrix in replay")
+            return y
         rc = self.L.oracle_replay(self._p, p, _d(y), _d(hs), len(hs), method)
         if rc:
             raise RuntimeError("singular iteration matrix in replay")
@@ -183,7 +221,7 @@ class Oracle:
         return dy
 
     def integrate_batch(self, T, p, Y, dt, rtol=1e-6, atol=1e-12, h_io=None, max_steps=100000, nthreads=0,
-                        trace_cap=0, method=0):
+                        trace_cap=0, method=0, tab_tol=0.0):
         """Structure-of-arrays batch (Y[k, c]); returns a dict of new arrays and the thread count."""
         N = int(T.shape[0])
         T = np.array(T, dtype=np.float64)
@@ -193,8 +231,10 @@ class Oracle:
         h = np.zeros(N) if h_io is None else np.array(h_io, dtype=np.float64)
         ns = np.zeros(N, dtype=np.int32); na = np.zeros(N, dtype=np.int32); st = np.zeros(N, dtype=np.int32)
         tr = np.zeros((trace_cap, N)) if trace_cap > 0 else None
-        used = self.L.oracle_integrate_batch(self._p, N, _d(T), _d(p), _d(Yc), _d(dt), rtol, atol, max_steps,
-                                             _d(h), _i(ns), _i(na), _i(st), nthreads, _d(tr), trace_cap, method)
+        tab = self.tab_build(tab_tol)[0] if tab_tol > 0 else None
+        used = self.L.oracle_integrate_batch_tab(self._p, N, _d(T), _d(p), _d(Yc), _d(dt), rtol, atol, max_steps,
+                                                 _d(h), _i(ns), _i(na), _i(st), nthreads, _d(tr), trace_cap, method,
+                                                 tab)
         out = dict(T=T, Y=Yc, h=h, nsub=ns, nacc=na, status=st, threads=used)
         if tr is not None:
             out["trace"] = tr

@@ -1,8 +1,9 @@
 """Build the CUDA library ``_native/libchemgb.so`` in-tree (sm_103a only).
 
-Five translation units compiled in parallel: the host mechanism compiler and the load-balance planner
-(C++), the C ABI with its small kernels, the forward (rate, Jacobian, integration) kernels and the
-adjoint kernels (CUDA).  Called by ``__graft_entry__.build()``; also runnable as a script.
+Seven translation units compiled in parallel: the host mechanism compiler and the load-balance planner
+(C++), the C ABI with its small kernels, the integration kernels of each lane group (one warp, two
+warps, half a warp per cell; the rate and Jacobian kernels with the first) and the adjoint kernels
+(CUDA).  Called by ``__graft_entry__.build()``; also runnable as a script.
 """
 import os
 import subprocess
@@ -16,6 +17,12 @@ OUT = os.path.join(HERE, "_native")
 LIB = os.path.join(OUT, "libchemgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
+# kernel translation units besides capi.cu: the integration kernels per lane group, and the adjoint
+# The integration kernels are held to 128 registers per thread: 16 warps per SM where shared memory allows
+# it (small mechanisms), and no spills (ptxas -v).
+REG_CAP = {f: ["-maxrregcount=128"] for f in ("kern_fwd_warp", "kern_fwd_warp_plain", "kern_fwd_pair", "kern_fwd_half")}
+CUDA_UNITS = ("kern_fwd_warp", "kern_fwd_warp_plain", "kern_fwd_pair", "kern_fwd_half", "kern_rates",
+              "kern_adjoint")
 
 
 def _sources():
@@ -43,8 +50,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         [*host, "-c", os.path.join(CSRC, "compile.cpp"), "-o", os.path.join(OUT, "compile.o")],
         [*host, "-c", os.path.join(CSRC, "balance.cpp"), "-o", os.path.join(OUT, "balance.o")],
         [*cu_flags, "-c", os.path.join(CSRC, "capi.cu"), "-o", os.path.join(OUT, "capi.o")],
-        [*cu_flags, "-c", os.path.join(CSRC, "kern_forward.cu"), "-o", os.path.join(OUT, "kern_forward.o")],
-        [*cu_flags, "-c", os.path.join(CSRC, "kern_adjoint.cu"), "-o", os.path.join(OUT, "kern_adjoint.o")],
+        *([*cu_flags, *REG_CAP.get(f, []), "-c", os.path.join(CSRC, f + ".cu"), "-o", os.path.join(OUT, f + ".o")]
+          for f in CUDA_UNITS),
     ]
 
     def run(cmd):
@@ -60,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         list(ex.map(run, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     run([NVCC, *ARCH, "-shared", "-o", tmp, *(os.path.join(OUT, f + ".o") for f in
-                                              ("compile", "balance", "capi", "kern_forward", "kern_adjoint"))])
+                                              ("compile", "balance", "capi", *CUDA_UNITS))])
     os.replace(tmp, LIB)
     return LIB
 

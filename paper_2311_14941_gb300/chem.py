@@ -48,7 +48,8 @@ class OptsC(C.Structure):
                 ("time_budget_s", C.c_double), ("max_substeps", C.c_int), ("max_nonfinite", C.c_int),
                 ("mode", C.c_int), ("block_cells", C.c_int), ("chunk", C.c_int), ("naccept", _vp),
                 ("trace", _vp), ("trace_cap", C.c_int), ("ckpt_every", C.c_int), ("tape_steps", C.c_int),
-                ("warps_per_cell", C.c_int), ("method", C.c_int), ("cells_per_warp", C.c_int)]
+                ("warps_per_cell", C.c_int), ("method", C.c_int), ("cells_per_warp", C.c_int),
+                ("tabulate", C.c_int), ("tab_tol", C.c_double)]
 
 
 class MapOptsC(C.Structure):
@@ -226,14 +227,14 @@ class Mechanism:
 
     def integrate(self, T, p, Y, dt, h_io, nsub, status, rtol=1e-6, atol=1e-12, h_init=0.0, h_min=0.0,
                   time_budget_s=0.0, max_substeps=0, max_nonfinite=0, mode=0, block_cells=0, chunk=0, naccept=None,
-                  trace=None, warps_per_cell=0, method=0, cells_per_warp=0, stream=None):
+                  trace=None, warps_per_cell=0, method=0, cells_per_warp=0, tabulate=0, tab_tol=0.0, stream=None):
         """chem_integrate on device tensors: T, Y, h_io, nsub, status (and naccept) are updated in place."""
         import torch
         N = T.numel()
         cap = trace.numel() // max(N, 1) if trace is not None else 0
         o = OptsC(rtol, atol, h_init, h_min, time_budget_s, max_substeps, max_nonfinite, mode, block_cells, chunk,
                   _dptr(naccept, torch.int32, N, "naccept"), _dptr(trace, torch.float64, cap * N, "trace"), cap,
-                  0, 0, warps_per_cell, method, cells_per_warp)
+                  0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol)
         _check(lib().chem_integrate(self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
                                     _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
                                     _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
@@ -266,7 +267,8 @@ class Mechanism:
 
     def integrate_noalloc(self, T, p, Y, dt, h_io, nsub, status, rtol=1e-6, atol=1e-12, h_init=0.0, h_min=0.0,
                           time_budget_s=0.0, max_substeps=0, max_nonfinite=0, block_cells=0, chunk=0, naccept=None,
-                          trace=None, warps_per_cell=0, method=0, cells_per_warp=0, stream=None):
+                          trace=None, warps_per_cell=0, method=0, cells_per_warp=0, tabulate=0, tab_tol=0.0,
+                          stream=None):
         """chem_integrate_noalloc: the sorted work-queue integration with its scratch in the library's
         static device memory (no allocation in the call; at most 1,048,576 cells; calls must not overlap
         on the GPU).  In-place like ``integrate``."""
@@ -275,7 +277,7 @@ class Mechanism:
         cap = trace.numel() // max(N, 1) if trace is not None else 0
         o = OptsC(rtol, atol, h_init, h_min, time_budget_s, max_substeps, max_nonfinite, 1, block_cells, chunk,
                   _dptr(naccept, torch.int32, N, "naccept"), _dptr(trace, torch.float64, cap * N, "trace"), cap,
-                  0, 0, warps_per_cell, method, cells_per_warp)
+                  0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol)
         _check(lib().chem_integrate_noalloc(
             self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
             _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
@@ -285,14 +287,15 @@ class Mechanism:
 
     def integrate_mapped(self, T, p, Y, dt, h_io, nsub, status, ref, mapping=None, rtol=1e-6, atol=1e-12,
                          h_init=0.0, h_min=0.0, max_substeps=0, max_nonfinite=0, mode=0, block_cells=0, chunk=0,
-                         warps_per_cell=0, method=0, cells_per_warp=0, stream=None) -> int:
+                         warps_per_cell=0, method=0, cells_per_warp=0, tabulate=0, tab_tol=0.0,
+                         stream=None) -> int:
         """chem_integrate_mapped: like `integrate`, with zonal reference-cell mapping.  mapping: None or
         dict(T_max, dT, species=[...], dY=[...]).  ref (int32 [N], device) receives each cell's reference.
         Returns the number of cells integrated."""
         import torch
         N = T.numel()
         o = OptsC(rtol, atol, h_init, h_min, 0.0, max_substeps, max_nonfinite, mode, block_cells, chunk, None, None,
-                  0, 0, 0, warps_per_cell, method, cells_per_warp)
+                  0, 0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol)
         mp = None
         if mapping is not None:
             sp = list(mapping.get("species", ()))

@@ -61,12 +61,16 @@ struct chem_handle_s {
   int bps_cache[kNumGroups][kMaxBlockCells + 1] = {};   // resident blocks per SM of the persistent kernel
   int auto_wpc = 1;                // warps per cell when the caller leaves the choice to the library
   int auto_cpw = 1;                // cells per warp when the caller leaves the choice to the library
+  // tabulated temperature functions (built at the first call that asks for a tolerance)
+  HostTables tabs;
+  void* tab_dev = nullptr;
+  bool params_shifted = false;     // chem_set_params moved the Arrhenius parameters off the description's
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
     int N, mode, cpb, chunk, grp;
     const void* ptr[10];
-    double d[5];
-    int i[4];
+    double d[6];
+    int i[5];
     bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
   } gkey{};
   cudaGraphExec_t gexec = nullptr;
@@ -360,6 +364,8 @@ struct IntCall {
   int cpb = 1;     // cells per block
   int grid = 1;    // persistent form: resident blocks on the device
   int chunk = 1;   // persistent form: cells per queue pull
+  int tab = 0;     // tabulated temperature functions
+  double tab_tol = 0.0;
 };
 
 chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opts, IntCall& c) {
@@ -375,6 +381,12 @@ chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opt
   if (o.cells_per_warp == 2 && o.warps_per_cell == 2)
     return fail(CHEM_EINVAL, "cells_per_warp = 2 needs warps_per_cell 0 or 1");
   if (!(o.time_budget_s >= 0.0) || !std::isfinite(o.time_budget_s)) return fail(CHEM_EINVAL, "bad time_budget_s");
+  if (o.tabulate != 0 && o.tabulate != 1) return fail(CHEM_EINVAL, "tabulate must be 0 or 1");
+  if (!(o.tab_tol >= 0.0 && o.tab_tol < 1.0)) return fail(CHEM_EINVAL, "tab_tol must lie in [0, 1)");
+  c.tab = o.tabulate;
+  c.tab_tol = o.tab_tol > 0.0 ? o.tab_tol : 1e-10;
+  if (c.tab && h->params_shifted)
+    return fail(CHEM_EINVAL, "tabulate: the tables hold the description's parameters, which chem_set_params shifted");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
   c.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
   if (o.cells_per_warp == 2) c.grp = 2;
@@ -389,6 +401,58 @@ chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opt
   const long long share = std::max(1LL, ((long long)N + groups - 1) / groups);
   c.chunk = (int)std::min<long long>(o.chunk > 0 ? o.chunk : 1, share);
   return CHEM_OK;
+}
+
+// The tables of tolerance tol in device memory: built on the host and uploaded when the handle holds
+// none for tol (allocating; may_allocate false: only tables already built are accepted).
+chem_status ensure_tables(chem_handle h, double tol, bool may_allocate) {
+  if (h->tab_dev && h->tabs.tol == tol) return CHEM_OK;
+  if (!may_allocate)
+    return fail(CHEM_EINVAL, "tabulate: no tables of this tab_tol in the handle yet (chem_integrate builds them)");
+  std::string err;
+  HostTables t;
+  chem_status st = build_tables(h->hm, tol, t, err);
+  if (st != CHEM_OK) return fail(st, err);
+  size_t bytes = 0;
+  for (int c = 0; c < kTabClasses; ++c) bytes += align_up(t.coef[c].size() * sizeof(double), 256);
+  void* dev = nullptr;
+  if (bytes > 0 && cudaMalloc(&dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CHEM_ENOMEM, "cudaMalloc of the tables failed");
+  }
+  size_t off = 0;
+  for (int c = 0; c < kTabClasses; ++c) {
+    if (!t.coef[c].empty()) {
+      cudaError_t e = cudaMemcpy((char*)dev + off, t.coef[c].data(), t.coef[c].size() * sizeof(double),
+                                 cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(e, "cudaMemcpy of the tables"); }
+    }
+    off += align_up(t.coef[c].size() * sizeof(double), 256);
+  }
+  if (h->tab_dev) cudaFree(h->tab_dev);
+  h->tab_dev = dev;
+  h->tabs = std::move(t);
+  return CHEM_OK;
+}
+
+// The view of lane group grp, with the handle's tables switched on when tab is set.
+MechView view_for(const chem_handle h, int grp, int tab) {
+  MechView V = h->view[grp];
+  V.tab_on = 0;
+  if (!tab || !h->tab_dev) return V;
+  V.tab_on = 1;
+  size_t off = 0;
+  for (int c = 0; c < kTabClasses; ++c) {
+    V.tab_deg[c] = h->tabs.deg[c];
+    V.tab[c] = h->tabs.deg[c] > 0 ? (const double*)((const char*)h->tab_dev + off) : nullptr;
+    off += align_up(h->tabs.coef[c].size() * sizeof(double), 256);
+  }
+  V.tab_ulo = h->tabs.u_lo;
+  V.tab_du = h->tabs.du;
+  V.tab_tlo = kTabTlo;
+  V.tab_thi = kTabThi;
+  V.tab_ni = kTabIntervals;
+  return V;
 }
 
 }  // namespace
@@ -529,6 +593,7 @@ chem_status chem_destroy(chem_handle h) {
   if (h->scratch) cudaFree(h->scratch);
   if (h->adj_scratch) cudaFree(h->adj_scratch);
   if (h->map_scratch) cudaFree(h->map_scratch);
+  if (h->tab_dev) cudaFree(h->tab_dev);
   delete h;
   return CHEM_OK;
 }
@@ -615,7 +680,7 @@ chem_status chem_rates(chem_handle h, int N, const double* T, const double* p, c
   if (N == 0) return CHEM_OK;
   if (!T || !p || !Y || !dTdt || !dYdt) return fail(CHEM_EINVAL, "null array argument");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
-  const int wpb = cells_per_block(h, 4, 1);
+  const int wpb = cells_per_block(h, 4, 0);
   k_rates<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view[0], h->L, N, T, p, Y,
                                                                                            dTdt, dYdt, wdot);
   return launch_check("chem_rates launch");
@@ -630,7 +695,7 @@ chem_status chem_jacobian(chem_handle h, int N, const double* T, const double* p
   if (N == 0) return CHEM_OK;
   if (!T || !p || !Y || !S_vals || !u || !v) return fail(CHEM_EINVAL, "null array argument");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
-  const int wpb = cells_per_block(h, 4, 1);
+  const int wpb = cells_per_block(h, 4, 0);
   k_jacobian<<<(N + wpb - 1) / wpb, wpb * kWarp, wpb * h->cell_bytes, (cudaStream_t)stream>>>(h->view[0], h->L, N, T, p,
                                                                                               Y, S_vals, u, v);
   return launch_check("chem_jacobian launch");
@@ -653,7 +718,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   cudaError_t e;
   const int grp = c.grp;
   const int width = kGroupWidth[grp];
-  const MechView& V = h->view[grp];
+  if (c.tab && (st = ensure_tables(h, c.tab_tol, true)) != CHEM_OK) return st;
+  const MechView V = view_for(h, grp, c.tab);
   const int cpb = c.cpb;
   if (o.mode == 0) {
     unsigned long long* stamp = nullptr;
@@ -662,8 +728,9 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
       stamp = (unsigned long long*)((char*)h->scratch + kScrStamp);
       k_stamp<<<1, 32, 0, strm>>>(stamp);
     }
-    launch_integrate_plain(grp, (N + cpb - 1) / cpb, cpb * width, cpb * h->cell_bytes, strm, V, h->L, N, T, p, Y, dt,
-                           h_io, nsub, status, o.naccept, io, stamp, budget_ns);
+    if ((e = launch_integrate_plain(grp, (N + cpb - 1) / cpb, cpb * width, cpb * h->cell_bytes, strm, V, h->L, N, T, p,
+                                    Y, dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns)) != cudaSuccess)
+      return cuda_fail(e, "chem_integrate launch shape");
     return launch_check("chem_integrate launch");
   }
   // persistent mode: sort by previous cost, then one resident grid pulling from the queue; the whole
@@ -676,6 +743,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
   key.d[0] = io.rtol; key.d[1] = io.atol; key.d[2] = io.h_init; key.d[3] = io.h_min; key.d[4] = o.time_budget_s;
   key.i[0] = io.max_substeps; key.i[1] = io.max_nonfinite; key.i[2] = io.trace_cap; key.i[3] = io.method;
+  key.i[4] = c.tab;
+  key.d[5] = c.tab ? c.tab_tol : 0.0;
   if (!h->gexec || !(h->gkey == key)) {
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -695,10 +764,11 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
     k_stamp<<<1, 32, 0, cs>>>(stamp);
     k_sort_count<<<sblocks, 256, 0, cs>>>(N, nsub, counts);
     k_sort_scatter<<<sblocks, 256, 0, cs>>>(N, nsub, counts, cursor, perm);
-    launch_integrate_persistent(grp, grid, cpb * width, cpb * h->cell_bytes, cs, V, h->L, N, T, p, Y, dt, h_io, nsub,
-                                status, o.naccept, perm, head, chunk, io, stamp, budget_ns);
+    const cudaError_t se = launch_integrate_persistent(grp, grid, cpb * width, cpb * h->cell_bytes, cs, V, h->L, N, T,
+                                                       p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io,
+                                                       stamp, budget_ns);
     cudaGraph_t graph = nullptr;
-    cudaError_t le = cudaGetLastError();
+    cudaError_t le = se != cudaSuccess ? se : cudaGetLastError();
     e = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(le, "persistent launch capture"); }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -717,6 +787,7 @@ extern "C" chem_status chem_set_params(chem_handle h, const double* dlnA, const 
   DeviceScope ds;
   chem_status st = check_handle(h, ds);
   if (st != CHEM_OK) return st;
+  h->params_shifted = dlnA != nullptr || dEa != nullptr;
   if (h->hm.R == 0) return CHEM_OK;
   k_set_params<<<(h->hm.R + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->view[0], h->rxd0, (double*)h->view[0].rxd,
                                                                          dlnA, dEa);
@@ -737,6 +808,7 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   chem_integrate_opts o{};
   if (opts) o = *opts;
   if (o.method != 0) return fail(CHEM_EINVAL, "chem_adjoint differentiates RODAS3 steps only (method 0)");
+  if (o.tabulate) return fail(CHEM_EINVAL, "chem_adjoint differentiates the exact functions only (tabulate 0)");
   o.trace = nullptr;   // the adjoint records its own tape instead
   IntOpts io;
   if ((st = tolerance_opts(o, N, io)) != CHEM_OK) return st;
@@ -799,8 +871,9 @@ extern "C" chem_status chem_adjoint(chem_handle h, int N, double* T, const doubl
   // forward pass with the tape
   io.rec_h = rec_h; io.rec_ck = rec_ck; io.rec_n = rec_n; io.rec_cap = cap; io.rec_K = K;
   if ((e = cudaMemsetAsync(hio, 0, (size_t)N * 8, strm)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  launch_integrate_plain(1, N, kWarp, h->cell_bytes, strm, h->view[0], h->L, N, T, p, Y, dt, hio, nsub, status, nullptr,
-                         io, nullptr, 0ull);
+  if ((e = launch_integrate_plain(0, N, kWarp, h->cell_bytes, strm, h->view[0], h->L, N, T, p, Y, dt, hio, nsub, status,
+                                  nullptr, io, nullptr, 0ull)) != cudaSuccess)
+    return cuda_fail(e, "chem_adjoint forward launch shape");
   if ((st = launch_check("chem_adjoint forward launch")) != CHEM_OK) return st;
   // reverse pass, cells ordered by tape length (longest first) as in the sorted work queue
   io.rec_h = nullptr; io.rec_ck = nullptr; io.rec_n = nullptr;
@@ -861,6 +934,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   o1.mode = 1;   // always the sorted work queue
   IntCall c;
   if ((st = parse_integrate(h, N, &o1, c)) != CHEM_OK) return st;
+  if (c.tab && (st = ensure_tables(h, c.tab_tol, false)) != CHEM_OK) return st;
   char* scr = nullptr;
   if ((st = noalloc_scratch_address(h->device, &scr)) != CHEM_OK) return st;
   const int grp = c.grp, wpb = c.cpb;
@@ -878,8 +952,10 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   k_stamp<<<1, 32, 0, strm>>>(stamp);
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, nsub, counts);
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, nsub, counts, cursor, perm);
-  launch_integrate_persistent(grp, grid, wpb * kGroupWidth[grp], wpb * h->cell_bytes, strm, h->view[grp], h->L, N, T, p,
-                              Y, dt, h_io, nsub, status, c.o.naccept, perm, head, c.chunk, c.io, stamp, c.budget_ns);
+  if ((e = launch_integrate_persistent(grp, grid, wpb * kGroupWidth[grp], wpb * h->cell_bytes, strm,
+                                       view_for(h, grp, c.tab), h->L, N, T, p, Y, dt, h_io, nsub, status, c.o.naccept,
+                                       perm, head, c.chunk, c.io, stamp, c.budget_ns)) != cudaSuccess)
+    return cuda_fail(e, "chem_integrate_noalloc launch shape");
   return launch_check("chem_integrate_noalloc launch");
 }
 

@@ -651,6 +651,99 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
 
 }  // namespace chemgb
 
+// ------------------------------------------------------------------------ tabulated temperature functions
+// Sec. 2.5 credits part of SpeedCHEM's speed to interpolating costly thermodynamic functions with
+// polynomials of optimal degree.  Here the temperature functions that cost exponentials per evaluation are
+// tabulated: exp(+-g_k) of every species (the factors of the equilibrium constants), every forward rate
+// coefficient and every Troe centre.  Each is, on each of kTabIntervals equal intervals of u = 1/T, the
+// polynomial through the Chebyshev points of the interval; one degree per class, the smallest in 1..8
+// whose polynomials are within tol (relative) of the function at 17 equispaced points of every interval.
+namespace chemgb {
+namespace {
+
+constexpr int kTabMaxDeg = 8;
+
+// The function itself (double arithmetic, the same formulas as the exact device path).
+double tab_function(const HostMech& hm, int cls, int f, double T) {
+  const double lnT = std::log(T), invT = 1.0 / T;
+  if (cls == TC_E || cls == TC_IE) {
+    const double* s = &hm.sp[(size_t)f * SP_STRIDE];
+    const double* c = s + 4 + (T < s[2] ? 0 : SP_RANGE);
+    const double g = c[0] * (1.0 - lnT) + T * (c[9] + T * (c[10] + T * (c[11] + T * c[12]))) + c[13] * invT - c[14];
+    return std::exp(cls == TC_E ? g : -g);
+  }
+  const double* D = &hm.rxd[(size_t)f * RX_D];
+  if (cls == TC_KF) return std::exp(D[0] + D[1] * lnT - D[2] * invT);
+  return D[6] * std::exp(-T * D[8]) + D[7] * std::exp(-T * D[9]) + (D[10] > 0.0 ? std::exp(-D[10] * invT) : 0.0);
+}
+
+// mono[d][k][i]: coefficient of tau^i in the Chebyshev polynomial T_k, for every degree bound d <= 8.
+struct ChebToMono {
+  double c[kTabMaxDeg + 1][kTabMaxDeg + 1];
+  ChebToMono() {
+    for (auto& row : c) for (double& x : row) x = 0.0;
+    c[0][0] = 1.0;
+    c[1][1] = 1.0;
+    for (int k = 2; k <= kTabMaxDeg; ++k)
+      for (int i = 0; i <= k; ++i) c[k][i] = (i > 0 ? 2.0 * c[k - 1][i - 1] : 0.0) - c[k - 2][i];
+  }
+};
+
+}  // namespace
+
+chem_status build_tables(const HostMech& hm, double tol, HostTables& t, std::string& err) {
+  if (!(tol > 0.0 && tol < 1.0)) { err = "tab_tol must lie in (0, 1)"; return CHEM_EINVAL; }
+  static const ChebToMono cm;
+  const double kPi = 3.14159265358979323846;
+  t = HostTables();
+  t.tol = tol;
+  t.u_lo = 1.0 / kTabThi;
+  t.du = (1.0 / kTabTlo - 1.0 / kTabThi) / kTabIntervals;
+  const int nf[kTabClasses] = {hm.n, hm.n, hm.R, hm.n_troe};
+  for (int cls = 0; cls < kTabClasses; ++cls) {
+    t.nfun[cls] = nf[cls];
+    if (nf[cls] == 0) continue;
+    for (int d = 1; d <= kTabMaxDeg && t.deg[cls] == 0; ++d) {
+      std::vector<double> out((size_t)kTabIntervals * nf[cls] * (d + 1));
+      double node[kTabMaxDeg + 1], val[kTabMaxDeg + 1], ch[kTabMaxDeg + 1];
+      for (int i = 0; i <= d; ++i) node[i] = std::cos(kPi * (2 * i + 1) / (2.0 * (d + 1)));
+      bool ok = true;
+      for (int j = 0; j < kTabIntervals && ok; ++j) {
+        const double u0 = t.u_lo + j * t.du;
+        for (int f = 0; f < nf[cls] && ok; ++f) {
+          for (int i = 0; i <= d; ++i) val[i] = tab_function(hm, cls, f, 1.0 / (u0 + 0.5 * (node[i] + 1.0) * t.du));
+          // Chebyshev coefficients by discrete orthogonality at the nodes (T_k(node_i) = cos(k theta_i))
+          for (int k = 0; k <= d; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i <= d; ++i) acc += val[i] * std::cos(k * kPi * (2 * i + 1) / (2.0 * (d + 1)));
+            ch[k] = acc * (k == 0 ? 1.0 : 2.0) / (d + 1);
+          }
+          double* mono = &out[((size_t)j * nf[cls] + f) * (d + 1)];
+          for (int i = 0; i <= d; ++i) {
+            double acc = 0.0;
+            for (int k = i; k <= d; ++k) acc += ch[k] * cm.c[k][i];
+            mono[i] = acc;
+          }
+          for (int q = 0; q <= 16 && ok; ++q) {
+            const double tau = -1.0 + q / 8.0;
+            double v = mono[d];
+            for (int i = d - 1; i >= 0; --i) v = v * tau + mono[i];
+            const double ex = tab_function(hm, cls, f, 1.0 / (u0 + 0.5 * (tau + 1.0) * t.du));
+            ok = std::fabs(v - ex) <= tol * std::fabs(ex);
+          }
+        }
+      }
+      if (ok) {
+        t.deg[cls] = d;
+        t.coef[cls].swap(out);
+      }
+    }
+  }
+  return CHEM_OK;
+}
+
+}  // namespace chemgb
+
 // ------------------------------------------------------------------------ mechanism description in JSON
 namespace chemgb {
 namespace {

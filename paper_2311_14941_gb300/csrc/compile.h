@@ -43,6 +43,25 @@ struct HostMech {
 // Validates and compiles; returns CHEM_OK or an error code with a message in err.
 chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string& err);
 
+// Tabulated temperature functions (the opt-in approximation of chem_integrate_opts.tabulate): per class
+// TC_E exp(g_k), TC_IE exp(-g_k) (species), TC_KF the forward rate coefficient (compiled reaction order;
+// the high-pressure limit of a fall-off reaction), TC_FC the Troe centre of the fall-off reactions (the
+// first n_troe compiled reactions), a polynomial in tau on each of kTabIntervals equal intervals of
+// u = 1/T over [1/kTabThi, 1/kTabTlo]; coefficients of class c at
+// coef[c][((j * nfun_c + f) * (deg[c] + 1)) + i] (interval j, function f, power i of tau).
+enum : int { TC_E = 0, TC_IE = 1, TC_KF = 2, TC_FC = 3, kTabClasses = 4 };
+constexpr int kTabIntervals = 640;
+constexpr double kTabTlo = 250.0, kTabThi = 4000.0;
+struct HostTables {
+  double tol = 0.0;
+  double u_lo = 0.0, du = 0.0;
+  int deg[kTabClasses] = {0, 0, 0, 0};   // 0: the class stays exact (no degree up to 8 meets tol)
+  int nfun[kTabClasses] = {0, 0, 0, 0};
+  std::vector<double> coef[kTabClasses];
+};
+// Builds the tables for relative tolerance tol (0 < tol < 1).
+chem_status build_tables(const HostMech& hm, double tol, HostTables& t, std::string& err);
+
 // A mechanism description read from JSON: the arrays, and a chem_mech_desc pointing into them.
 struct JsonMech {
   std::vector<double> W, T_mid, nasa_lo, nasa_hi, A, b, Ea, eff_alpha, troe, low;

@@ -21,6 +21,7 @@
 //          where J = S + u v^T is inverted by Sherman-Morrison around the sparse LU of I/(h gamma) - S.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "mech.h"
 #include "scalar.cuh"
@@ -169,11 +170,37 @@ __device__ __forceinline__ ElimOp ld_eop(const ElimOp* p) {
   return o;
 }
 
-// Per-cell scalars shared by all lanes (every lane holds the same values).
+// Per-cell scalars shared by all lanes (every lane holds the same values).  tj, ttau: interval and local
+// coordinate of T in the tables of tabulated temperature functions (tj < 0: exact evaluation).
 template <class Sc>
 struct ScalT {
   Sc T, lnT, invT, Wbar, rho, irho, cp, ctot, rtp, irtp, dcps;
+  int tj;
+  double ttau;
 };
+
+template <class Sc>
+constexpr bool is_real() { return std::is_same<Sc, double>::value; }
+
+// Polynomial in tau with coefficients c[0..d] (table memory, read-only path).
+__device__ __forceinline__ double tab_poly(const double* c, int d, double tau) {
+  double v = __ldg(c + d);
+  for (int i = d - 1; i >= 0; --i) v = fma(v, tau, __ldg(c + i));
+  return v;
+}
+
+// The table coordinates of T: interval j of u = 1/T and tau = 2 (u - u_j)/du - 1 (-1 outside the range or
+// without tables; computed with the division, so that every implementation of the tables locates T alike).
+__device__ __forceinline__ void tab_locate(const MechView& M, double T, double invT, int& tj, double& ttau) {
+  tj = -1;
+  ttau = 0.0;
+  if (M.tab_on && T >= M.tab_tlo && T < M.tab_thi) {
+    const double x = (invT - M.tab_ulo) / M.tab_du;
+    const int j = min(M.tab_ni - 1, max(0, (int)floor(x)));
+    tj = j;
+    ttau = 2.0 * (x - j) - 1.0;
+  }
+}
 using Scal = ScalT<double>;
 
 // Coefficient nu of the omega and Dtil gather programs: the op carries the top 16 bits of the IEEE
@@ -217,11 +244,12 @@ __device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F
 // One species at T: cp/R, h/RT, g = h/RT - s/R and its exponential (NASA-7, range by T vs T_mid).
 template <class Sc>
 struct SpOut {
-  Sc cpR, hRT, eg, yw, dcp;
+  Sc cpR, hRT, eg, emg, yw, dcp;
 };
 
 template <class Sc, bool DERIV>
-__device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, const Sc* y, Sc T, Sc lnT, Sc invT) {
+__device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, const Sc* y, Sc T, Sc lnT, Sc invT,
+                                                  int tj, double ttau) {
   const double* t = M.sp + (size_t)k * SP_STRIDE;
   const double iw = __ldg(t);
   const double* c = t + 4 + (val(T) < __ldg(t + 2) ? 0 : SP_RANGE);
@@ -235,7 +263,18 @@ __device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, cons
   const Sc gp = sfma(T, sfma(T, sfma(T, sfma(T, Sc(__ldg(c + 12)), Sc(__ldg(c + 11))), Sc(__ldg(c + 10))),
                              Sc(__ldg(c + 9))),
                      sfma(a5, invT, -a6));
-  o.eg = sexp(sfma(a0, 1.0 - lnT, gp));
+  bool tabd = false;
+  if constexpr (is_real<Sc>()) {
+    if (tj >= 0 && M.tab_deg[0] > 0 && M.tab_deg[1] > 0) {
+      o.eg = tab_poly(M.tab[0] + ((size_t)tj * M.n + k) * (M.tab_deg[0] + 1), M.tab_deg[0], ttau);
+      o.emg = tab_poly(M.tab[1] + ((size_t)tj * M.n + k) * (M.tab_deg[1] + 1), M.tab_deg[1], ttau);
+      tabd = true;
+    }
+  }
+  if (!tabd) {
+    o.eg = sexp(sfma(a0, 1.0 - lnT, gp));
+    o.emg = 1.0 / o.eg;
+  }
   o.yw = y[1 + k] * iw;
   o.dcp = DERIV ? sfma(T, sfma(T, Sc(__ldg(c + 17)) * T + Sc(__ldg(c + 16)), Sc(__ldg(c + 15))), a1) : Sc(0.0);
   return o;
@@ -250,6 +289,9 @@ __device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, cons
   sc.T = y[0];
   sc.lnT = slog(sc.T);
   sc.invT = 1.0 / sc.T;
+  sc.tj = -1;
+  sc.ttau = 0.0;
+  if constexpr (is_real<Sc>()) tab_locate(M, sc.T, sc.invT, sc.tj, sc.ttau);
   const Sc T = sc.T;
   Sc sig = Sc(0.0), cps = Sc(0.0), dcps = Sc(0.0);
   Sc* __restrict__ hRT = s + L.hRT;
@@ -260,9 +302,9 @@ __device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, cons
   for (int k = g.lane; k < M.n; k += 2 * g.size) {
     const bool v2 = k + g.size < M.n;
     const int k2 = v2 ? k + g.size : k;
-    const SpOut<Sc> a = species_item<Sc, DERIV>(M, k, y, T, sc.lnT, sc.invT);
-    const SpOut<Sc> b = species_item<Sc, DERIV>(M, k2, y, T, sc.lnT, sc.invT);
-    const Sc ia = 1.0 / a.eg, ib = 1.0 / b.eg;
+    const SpOut<Sc> a = species_item<Sc, DERIV>(M, k, y, T, sc.lnT, sc.invT, sc.tj, sc.ttau);
+    const SpOut<Sc> b = species_item<Sc, DERIV>(M, k2, y, T, sc.lnT, sc.invT, sc.tj, sc.ttau);
+    const Sc ia = a.emg, ib = b.emg;
     sig += a.yw + (v2 ? b.yw : Sc(0.0));
     cps = sfma(a.yw, a.cpR, cps);
     if (v2) cps = sfma(b.yw, b.cpR, cps);
@@ -316,7 +358,15 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
   x.rep = (nro > 1 && r1 == r0) || (nro > 2 && (r2 == r0 || r2 == r1)) || (npo > 1 && p1 == p0) ||
           (npo > 2 && (p2 == p0 || p2 == p1));
   const Sc lnkinf = sfma(-Ta, sc.invT, sfma(bb, sc.lnT, lnA));
-  Sc kf = sexp(lnkinf);
+  Sc kf;
+  bool tkf = false;
+  if constexpr (is_real<Sc>()) {
+    if (sc.tj >= 0 && M.tab_deg[2] > 0) {
+      kf = tab_poly(M.tab[2] + ((size_t)sc.tj * M.R + r) * (M.tab_deg[2] + 1), M.tab_deg[2], sc.ttau);
+      tkf = true;
+    }
+  }
+  if (!tkf) kf = sexp(lnkinf);
   x.cr0 = C[r0]; x.cr1 = nro > 1 ? C[r1] : Sc(1.0); x.cr2 = nro > 2 ? C[r2] : Sc(1.0);
   x.cp0 = C[p0]; x.cp1 = npo > 1 ? C[p1] : Sc(1.0); x.cp2 = npo > 2 ? C[p2] : Sc(1.0);
   const Sc Pf = x.cr0 * x.cr1 * x.cr2, Pb = x.cp0 * x.cp1 * x.cp2;
@@ -333,10 +383,21 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
     const Sc lnM = slog(Mv);
     const Sc lnPr = lnk0 - lnkinf + lnM;
     const Sc Pr = sexp(lnPr);
-    const Sc e3 = sexp(-sc.T * __ldg(D + 8)), e1 = sexp(-sc.T * __ldg(D + 9));
     const double T2 = __ldg(D + 10);
-    const Sc e2 = T2 > 0.0 ? sexp(-T2 * sc.invT) : Sc(0.0);
-    const Sc Fc = sfma(Sc(__ldg(D + 6)), e3, sfma(Sc(__ldg(D + 7)), e1, e2));
+    // the Troe centre: tabulated (Troe reactions are the first compiled ones), or from its three
+    // exponentials, which the Jacobian's temperature derivative needs in any case
+    bool tfc = false;
+    if constexpr (is_real<Sc>()) tfc = sc.tj >= 0 && M.tab_deg[3] > 0;
+    Sc e3 = Sc(0.0), e1 = Sc(0.0), e2 = Sc(0.0), Fc;
+    if (!tfc || DERIV) {
+      e3 = sexp(-sc.T * __ldg(D + 8));
+      e1 = sexp(-sc.T * __ldg(D + 9));
+      e2 = T2 > 0.0 ? sexp(-T2 * sc.invT) : Sc(0.0);
+    }
+    if constexpr (is_real<Sc>()) {
+      if (tfc) Fc = tab_poly(M.tab[3] + ((size_t)sc.tj * M.n_troe + r) * (M.tab_deg[3] + 1), M.tab_deg[3], sc.ttau);
+    }
+    if (!tfc) Fc = sfma(Sc(__ldg(D + 6)), e3, sfma(Sc(__ldg(D + 7)), e1, e2));
     const Sc Lc = slog(Fc) * kInvLn10;
     const Sc cc = sfma(Sc(-0.67), Lc, Sc(-0.4));
     const Sc nn = sfma(Sc(-1.27), Lc, Sc(0.75));

@@ -1,4 +1,6 @@
-// kern_forward.cu -- the rate, Jacobian and integration kernels (one lane group per cell).
+// kern_forward.cuh -- the integration kernels (one lane group per cell) and the rate and Jacobian kernels,
+// included by one translation unit per lane group (kern_fwd_warp.cu, kern_fwd_pair.cu, kern_fwd_half.cu).
+#pragma once
 #include <cuda_runtime.h>
 
 #include "../../include/chem.h"
@@ -66,46 +68,6 @@ __device__ __forceinline__ void load_tile(double* smem, const CellLayout& L, int
   __syncthreads();
 }
 
-__global__ void k_rates(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
-                        const double* __restrict__ Y, double* __restrict__ dTdt, double* __restrict__ dYdt,
-                        double* __restrict__ wdot) {
-  extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int c0 = blockIdx.x * wpb;
-  double* s = smem + (size_t)w * L.total;
-  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
-  const int c = c0 + w;
-  if (c >= N) return;
-  const Grp1 g{lane};
-  double* f = s + L.f0;
-  Scal sc = eval_f<double>(M, s, L, s + L.y, p[c], f, g);
-  for (int i = lane; i < M.m; i += kWarp) {
-    if (i == 0) dTdt[c] = f[0];
-    else dYdt[(size_t)(i - 1) * N + c] = f[i];
-  }
-  if (wdot) {
-    for (int k = lane; k < M.n; k += kWarp) wdot[(size_t)k * N + c] = f[1 + k] * sc.rho * __ldg(M.sp + (size_t)k * SP_STRIDE);
-  }
-}
-
-__global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __restrict__ T, const double* __restrict__ p,
-                           const double* __restrict__ Y, double* __restrict__ Sv, double* __restrict__ u,
-                           double* __restrict__ v) {
-  extern __shared__ double smem[];
-  const int wpb = blockDim.x / kWarp, w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  const int c0 = blockIdx.x * wpb;
-  double* s = smem + (size_t)w * L.total;
-  load_tile(smem, L, M.m, N, c0, wpb, T, Y);
-  const int c = c0 + w;
-  if (c >= N) return;
-  eval_jac<double>(M, s, L, s + L.y, p[c], Grp1{lane});
-  for (int e = lane; e < M.nnz_S; e += kWarp) Sv[(size_t)__ldg(M.s_out + e) * N + c] = s[L.S + e];
-  for (int i = lane; i < M.m; i += kWarp) {
-    u[(size_t)i * N + c] = s[L.u + i];
-    v[(size_t)i * N + c] = s[L.v + i];
-  }
-}
-
 // Plain form: one lane group per cell, cells in index order, one launch.
 template <class Gp>
 __global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __restrict__ T, const double* __restrict__ p,
@@ -113,6 +75,7 @@ __global__ void k_integrate_plain(MechView M, CellLayout L, int N, double* __res
                                   int* __restrict__ nsub, int* __restrict__ status, int* __restrict__ nacc_out,
                                   IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
   extern __shared__ double smem[];
+  if (blockDim.x % Gp::size != 0 || blockDim.x % kWarp != 0) return;   // the launch wrapper rejects such shapes
   const int cpb = blockDim.x / Gp::size;
   int w = 0;
   double* s = nullptr;
@@ -167,6 +130,7 @@ __global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* 
                                        const int* __restrict__ perm, unsigned long long* __restrict__ head, int chunk,
                                        IntOpts o, const unsigned long long* stamp, unsigned long long budget_ns) {
   extern __shared__ double smem[];
+  if (blockDim.x % Gp::size != 0 || blockDim.x % kWarp != 0) return;   // the launch wrapper rejects such shapes
   int w = 0;
   double* s = nullptr;
   const Gp g = cell_group<Gp>(L, smem, w, s);
@@ -204,33 +168,39 @@ __global__ void k_integrate_persistent(MechView M, CellLayout L, int N, double* 
 }
 
 
-// Host-side handles and launches of the instantiations (lane group g: 0 one warp, 1 two warps, 2 half a
-// warp per cell).
-const void* forward_kernel(ForwardKernel kind, int g) {
-  if (kind == KF_PLAIN)
-    return g == 0 ? (const void*)k_integrate_plain<Grp1> : g == 1 ? (const void*)k_integrate_plain<Grp2>
-                                                                  : (const void*)k_integrate_plain<GrpH>;
-  return g == 0 ? (const void*)k_integrate_persistent<Grp1> : g == 1 ? (const void*)k_integrate_persistent<Grp2>
-                                                                     : (const void*)k_integrate_persistent<GrpH>;
+// Host-side handles and launches of the instantiations for lane group Gp (explicitly instantiated in one
+// translation unit per group and form).
+template <class Gp>
+const void* plain_kernel() {
+  return (const void*)k_integrate_plain<Gp>;
 }
 
-void launch_integrate_plain(int g, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
-                            const CellLayout& L, int N, double* T, const double* p, double* Y, const double* dt,
-                            double* h_io, int* nsub, int* status, int* nacc_out, const IntOpts& o,
-                            const unsigned long long* stamp, unsigned long long budget_ns) {
-  auto kern = g == 0 ? k_integrate_plain<Grp1> : g == 1 ? k_integrate_plain<Grp2> : k_integrate_plain<GrpH>;
-  kern<<<grid, block, smem, stream>>>(M, L, N, T, p, Y, dt, h_io, nsub, status, nacc_out, o, stamp, budget_ns);
+template <class Gp>
+const void* persistent_kernel() {
+  return (const void*)k_integrate_persistent<Gp>;
 }
 
-void launch_integrate_persistent(int g, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
-                                 const CellLayout& L, int N, double* T, const double* p, double* Y,
-                                 const double* dt, double* h_io, int* nsub, int* status, int* nacc_out,
-                                 const int* perm, unsigned long long* head, int chunk, const IntOpts& o,
-                                 const unsigned long long* stamp, unsigned long long budget_ns) {
-  auto kern = g == 0 ? k_integrate_persistent<Grp1>
-                     : g == 1 ? k_integrate_persistent<Grp2> : k_integrate_persistent<GrpH>;
-  kern<<<grid, block, smem, stream>>>(M, L, N, T, p, Y, dt, h_io, nsub, status, nacc_out, perm, head, chunk, o,
-                                      stamp, budget_ns);
+template <class Gp>
+cudaError_t launch_plain_g(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+                           const CellLayout& L, int N, double* T, const double* p, double* Y, const double* dt,
+                           double* h_io, int* nsub, int* status, int* nacc_out, const IntOpts& o,
+                           const unsigned long long* stamp, unsigned long long budget_ns) {
+  if (block.x % Gp::size != 0 || block.x % kWarp != 0 || block.y != 1 || block.z != 1) return cudaErrorInvalidValue;
+  k_integrate_plain<Gp><<<grid, block, smem, stream>>>(M, L, N, T, p, Y, dt, h_io, nsub, status, nacc_out, o, stamp,
+                                                       budget_ns);
+  return cudaSuccess;
+}
+
+template <class Gp>
+cudaError_t launch_persistent_g(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+                                const CellLayout& L, int N, double* T, const double* p, double* Y, const double* dt,
+                                double* h_io, int* nsub, int* status, int* nacc_out, const int* perm,
+                                unsigned long long* head, int chunk, const IntOpts& o,
+                                const unsigned long long* stamp, unsigned long long budget_ns) {
+  if (block.x % Gp::size != 0 || block.x % kWarp != 0 || block.y != 1 || block.z != 1) return cudaErrorInvalidValue;
+  k_integrate_persistent<Gp><<<grid, block, smem, stream>>>(M, L, N, T, p, Y, dt, h_io, nsub, status, nacc_out, perm,
+                                                            head, chunk, o, stamp, budget_ns);
+  return cudaSuccess;
 }
 
 }  // namespace chemgb

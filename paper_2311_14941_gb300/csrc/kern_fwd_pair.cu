@@ -1,0 +1,16 @@
+// kern_fwd_pair.cu -- integration kernels with two warps per cell.
+#include "kern_forward.cuh"
+
+namespace chemgb {
+
+template const void* plain_kernel<Grp2>();
+template cudaError_t launch_plain_g<Grp2>(dim3, dim3, size_t, cudaStream_t, const MechView&, const CellLayout&, int, double*,
+                                  const double*, double*, const double*, double*, int*, int*, int*, const IntOpts&,
+                                  const unsigned long long*, unsigned long long);
+template const void* persistent_kernel<Grp2>();
+template cudaError_t launch_persistent_g<Grp2>(dim3, dim3, size_t, cudaStream_t, const MechView&, const CellLayout&, int,
+                                       double*, const double*, double*, const double*, double*, int*, int*, int*,
+                                       const int*, unsigned long long*, int, const IntOpts&,
+                                       const unsigned long long*, unsigned long long);
+
+}  // namespace chemgb

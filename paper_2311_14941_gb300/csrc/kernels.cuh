@@ -1,7 +1,8 @@
 // kernels.cuh -- the integration, rate, Jacobian and adjoint kernels, declared for the C ABI.
 //
-// Each group is compiled in its own translation unit (kern_forward.cu, kern_adjoint.cu) so that the
-// library builds in parallel; capi.cu launches them through these declarations.
+// The kernels are compiled in several translation units (one per lane group of the integration kernels,
+// kern_fwd_*.cu, and kern_adjoint.cu) so that the library builds in parallel; capi.cu launches them
+// through these declarations.
 #pragma once
 #include "adjoint.cuh"
 #include "device.cuh"
@@ -16,22 +17,40 @@ __global__ void k_jacobian(MechView M, CellLayout L, int N, const double* __rest
                            const double* __restrict__ Y, double* __restrict__ Sv, double* __restrict__ u,
                            double* __restrict__ v);
 
-// The integration kernels are templates on the warps per cell W (1 or 2); their instantiations keep
-// internal linkage inside kern_forward.cu, so the ABI reaches them through these host functions.
-//   plain form: one lane group (W warps) per cell, cells in index order;
+// The integration kernels are templates on the lane group (one warp, two warps or half a warp per cell);
+// their instantiations keep internal linkage inside their translation unit, so the ABI reaches them
+// through these host functions (group g: 0 one warp, 1 two warps, 2 half a warp per cell).
+//   plain form: one lane group per cell, cells in index order;
 //   persistent form: resident lane groups pull `chunk` cells at a time from the sorted queue `perm`.
 enum ForwardKernel { KF_PLAIN = 0, KF_PERSISTENT = 1 };
 // Host-side handle of the kernel (for cudaFuncSetAttribute, cudaFuncGetAttributes and occupancy queries).
-const void* forward_kernel(ForwardKernel kind, int W);
-void launch_integrate_plain(int W, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+const void* forward_kernel(ForwardKernel kind, int g);
+cudaError_t launch_integrate_plain(int g, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
                             const CellLayout& L, int N, double* T, const double* p, double* Y, const double* dt,
                             double* h_io, int* nsub, int* status, int* nacc_out, const IntOpts& o,
                             const unsigned long long* stamp, unsigned long long budget_ns);
-void launch_integrate_persistent(int W, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+cudaError_t launch_integrate_persistent(int g, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
                                  const CellLayout& L, int N, double* T, const double* p, double* Y,
                                  const double* dt, double* h_io, int* nsub, int* status, int* nacc_out,
                                  const int* perm, unsigned long long* head, int chunk, const IntOpts& o,
                                  const unsigned long long* stamp, unsigned long long budget_ns);
+
+// Per-group pieces, one translation unit each.
+template <class Gp>
+const void* plain_kernel();
+template <class Gp>
+const void* persistent_kernel();
+template <class Gp>
+cudaError_t launch_plain_g(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M, const CellLayout& L,
+                    int N, double* T, const double* p, double* Y, const double* dt, double* h_io, int* nsub,
+                    int* status, int* nacc_out, const IntOpts& o, const unsigned long long* stamp,
+                    unsigned long long budget_ns);
+template <class Gp>
+cudaError_t launch_persistent_g(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const MechView& M,
+                         const CellLayout& L, int N, double* T, const double* p, double* Y, const double* dt,
+                         double* h_io, int* nsub, int* status, int* nacc_out, const int* perm,
+                         unsigned long long* head, int chunk, const IntOpts& o, const unsigned long long* stamp,
+                         unsigned long long budget_ns);
 
 // Discrete adjoint: resident warps (one per block) pull cells, longest tapes first; shared memory holds the
 // forward cell layout, each warp's workspace (A.total doubles) and dual-number workspace are in global

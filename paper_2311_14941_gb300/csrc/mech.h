@@ -111,6 +111,15 @@ struct MechView {
   int svT_steps;
   const int* rx_order;       // [R] compiled reaction -> description index
   const int* s_out;          // [nnz_S] position of internal S entry in the CSR output order
+  // tabulated temperature functions (an opt-in approximation; tab_on == 0: every function exact):
+  // class c (0 exp(g_k), 1 exp(-g_k), 2 forward rate coefficient, 3 Troe centre) at interval j, function f
+  // has its deg[c] + 1 polynomial coefficients (powers of tau) at tab[c] + (j * nfun_c + f) * (deg[c] + 1)
+  int tab_on;
+  int tab_deg[4];            // 0: the class stays exact
+  const double* tab[4];
+  double tab_ulo, tab_du;    // interval j covers u = 1/T in [tab_ulo + j du, tab_ulo + (j + 1) du)
+  double tab_tlo, tab_thi;   // tabulated range of T
+  int tab_ni;                // intervals
 };
 
 // Per-cell shared-memory layout (offsets in doubles).

@@ -124,21 +124,21 @@ def _integrate_gpu(h, F, dev, trace_cap=0, **kw):
     return out
 
 
-def _noise_floor(o, F, c, trace_col, method=0):
+def _noise_floor(o, F, c, trace_col, method=0, tab_tol=0.0):
     """Sensitivity of the oracle's own result for cell c to a 1e-15 relative perturbation of its input
     (same step sequence): the floor below which two correct FP64 implementations cannot agree."""
     hs = trace_col[trace_col > 0]
     y0 = o.state(F.T[c], F.Y[:, c])
-    base = o.replay(y0, F.p[c], hs, method=method)
+    base = o.replay(y0, F.p[c], hs, method=method, tab_tol=tab_tol)
     rng = np.random.default_rng(c)
     sig = np.zeros_like(base)
     for _ in range(3):
         yp = y0 * (1.0 + 1e-15 * rng.standard_normal(y0.shape))
-        sig = np.maximum(sig, np.abs(o.replay(yp, F.p[c], hs, method=method) - base))
+        sig = np.maximum(sig, np.abs(o.replay(yp, F.p[c], hs, method=method, tab_tol=tab_tol) - base))
     return sig
 
 
-def _compare_integration(o, g, r, F, max_flip_frac, method=0):
+def _compare_integration(o, g, r, F, max_flip_frac, method=0, tab_tol=0.0):
     """Cells with the same accept/reject sequence: every T and Y > 1e-12 within 1e-8 relative, or within
     10x the oracle's own rounding-propagation floor where that is larger (tiny species set by fast
     balances).  Cells whose sequence differs (a decision at err ~ 1 flipped by rounding): within
@@ -163,7 +163,7 @@ def _compare_integration(o, g, r, F, max_flip_frac, method=0):
     floor_cells = 0
     worst = 0.0
     for c in np.where(same & ~np.all(ok, axis=0))[0]:
-        sig = _noise_floor(o, F, c, r["trace"][:, c], method)
+        sig = _noise_floor(o, F, c, r["trace"][:, c], method, tab_tol)
         bad = big[:, c] & (d[:, c] > np.maximum(RTOL_INT * np.abs(yr[:, c]), 10.0 * sig))
         assert not bad.any(), (c, np.where(bad)[0], d[bad, c], yr[bad, c], sig[bad])
         floor_cells += 1
@@ -298,3 +298,34 @@ def test_sorted_queue_parity_long_dt_regime(dev, wpc):
              status=st.cpu().numpy(), trace=tr.cpu().numpy().reshape(cap, N))
     assert np.all(g["status"] == 0)
     _compare_integration(o, g, r, F, 0.1)
+
+
+@pytest.mark.parametrize("name,mode", [("small", 0), ("mid", 1)])
+def test_tabulated_parity_against_the_oracles_tables(dev, name, mode):
+    """Tabulated temperature functions (tolerance 1e-10): the GPU's tables (built by the library) against
+    the oracle's own tables, trace-matched as above, on the small mechanism's 1024-cell field and a jet
+    and LTS sample of the methane-sized one; and the tabulated GPU result stays within 1e-6 of the
+    exact GPU result."""
+    m, h, o = mech(name)
+    if name == "small":
+        F = synth.field_uniform_random(m, 1024, seed=1)
+    else:
+        G = synth.field_bimodal_jet(m, 256, 256, seed=2)
+        rng = np.random.default_rng(8)
+        idx = np.sort(np.concatenate([rng.choice(np.where(G.kind == k)[0], 30, replace=False) for k in (0, 1, 2)]))
+        F = G.subset(idx)
+    r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=4000, tab_tol=1e-10)
+    g = _integrate_gpu(h, F, dev, trace_cap=4000, tabulate=1, tab_tol=1e-10, mode=mode)
+    _compare_integration(o, g, r, F, 0.03, tab_tol=1e-10)
+    e = _integrate_gpu(h, F, dev, mode=mode)
+    same = e["nsub"] == g["nsub"]
+    assert same.mean() > 0.9 and np.any(e["T"] != g["T"])
+    assert np.max(np.abs(e["T"][same] - g["T"][same]) / e["T"][same]) < 1e-6
+
+
+def test_tabulated_options_are_checked(dev):
+    m, h, o = mech("small")
+    F = synth.field_uniform_random(m, 8, seed=2)
+    for kw in (dict(tabulate=2), dict(tabulate=1, tab_tol=1.5), dict(tabulate=1, tab_tol=-1.0)):
+        with pytest.raises(chem.ChemError):
+            _integrate_gpu(h, F, dev, **kw)

@@ -236,16 +236,13 @@ chem_status set_attrs(chem_handle h) {
   const int bytes = h->smem_optin;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(forward_kernel(KF_PLAIN, 1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(forward_kernel(KF_PLAIN, 2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(forward_kernel(KF_PERSISTENT, 1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(forward_kernel(KF_PERSISTENT, 2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-          cudaSuccess)
+      (e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute");
+  for (int grp = 0; grp < kNumGroups; ++grp)
+    for (ForwardKernel kind : {KF_PLAIN, KF_PERSISTENT})
+      if ((e = cudaFuncSetAttribute(forward_kernel(kind, grp), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
+          cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute");
   // largest block per lane group: shared memory, the threads the kernels' registers allow (both forms),
   // at most 16 cells (32 half-warp cells), for two-warp cells the 15 named barriers besides barrier 0, and
   // for half-warp cells an even count (whole warps)

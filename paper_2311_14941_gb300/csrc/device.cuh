@@ -191,7 +191,8 @@ __device__ __forceinline__ double tab_poly(const double* c, int d, double tau) {
 
 // The table coordinates of T: interval j of u = 1/T and tau = 2 (u - u_j)/du - 1 (-1 outside the range or
 // without tables; computed with the division, so that every implementation of the tables locates T alike).
-__device__ __forceinline__ void tab_locate(const MechView& M, double T, double invT, int& tj, double& ttau) {
+template <class MV>
+__device__ __forceinline__ void tab_locate(const MV& M, double T, double invT, int& tj, double& ttau) {
   tj = -1;
   ttau = 0.0;
   if (M.tab_on && T >= M.tab_tlo && T < M.tab_thi) {
@@ -210,8 +211,8 @@ __device__ __forceinline__ double nu_of(int b) { return __hiloint2double(b << 16
 // -------------------------------------------------------------------------------------- gathers
 // out[g] = sum over the group's terms of val(a, b); partial sums of split groups are combined after.
 // ACC: out[g] += sum instead (outputs without terms in the program are left as they are).
-template <bool ACC = false, class Sc, class F, class Gp>
-__device__ __forceinline__ void run_gather(const Gather& G, Sc* out, Sc* part, F valf, const Gp& g) {
+template <bool ACC = false, class Sc, class F, class Gp, class GT>
+__device__ __forceinline__ void run_gather(const GT& G, Sc* out, Sc* part, F valf, const Gp& g) {
   Sc acc = Sc(0.0);
   const GatherOp* op = G.ops + g.lane;
   const int NS = G.steps;
@@ -247,8 +248,8 @@ struct SpOut {
   Sc cpR, hRT, eg, emg, yw, dcp;
 };
 
-template <class Sc, bool DERIV>
-__device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, const Sc* y, Sc T, Sc lnT, Sc invT,
+template <class Sc, bool DERIV, class MV>
+__device__ __forceinline__ SpOut<Sc> species_item(const MV& M, int k, const Sc* y, Sc T, Sc lnT, Sc invT,
                                                   int tj, double ttau) {
   const double* t = M.sp + (size_t)k * SP_STRIDE;
   const double iw = __ldg(t);
@@ -282,8 +283,8 @@ __device__ __forceinline__ SpOut<Sc> species_item(const MechView& M, int k, cons
 
 // NASA-7 at T for every species, two species per lane at a time (independent exp chains in flight);
 // fills C, hRT, eg = exp(g), emg = 1/eg, cpR.
-template <class Sc, bool DERIV, class Gp>
-__device__ __forceinline__ ScalT<Sc> eval_species(const MechView& M, Sc* s, const CellLayout& L, const Sc* y,
+template <class Sc, bool DERIV, class Gp, class MV, class LT>
+__device__ __forceinline__ ScalT<Sc> eval_species(const MV& M, Sc* s, const LT& L, const Sc* y,
                                                   double p, const Gp& g) {
   ScalT<Sc> sc;
   sc.T = y[0];
@@ -344,8 +345,8 @@ struct RxCore {
 
 // Rate of progress of reaction r, specialised on the reaction type (0 elementary, 1 third-body,
 // 2 Troe).  Branch-free in the participant counts: absent occurrences read index 0 and count as 1.
-template <class Sc, int TYPE, bool DERIV>
-__device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc* __restrict__ C,
+template <class Sc, int TYPE, bool DERIV, class MV>
+__device__ __forceinline__ RxCore<Sc> rx_core(const MV& M, int r, const Sc* __restrict__ C,
                                               const Sc* __restrict__ eg, const Sc* __restrict__ emg,
                                               const Sc* __restrict__ hRT, const ScalT<Sc>& sc) {
   const int* I = M.rxi + (size_t)r * RX_I;
@@ -461,8 +462,8 @@ __device__ __forceinline__ RxCore<Sc> rx_core(const MechView& M, int r, const Sc
 
 // Store q (and with DERIV: dq/dT at fixed C into s[dq_off + r], and the derivative slots dq/dC_j into
 // s[d_off + slot]) of reaction r.
-template <class Sc, int TYPE, bool DERIV>
-__device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<Sc>& x, Sc* s, const CellLayout& L,
+template <class Sc, int TYPE, bool DERIV, class MV, class LT>
+__device__ __forceinline__ void rx_store(const MV& M, int r, const RxCore<Sc>& x, Sc* s, const LT& L,
                                          const ScalT<Sc>& sc, bool valid, int dq_off, int d_off) {
   if (!valid) return;
   s[L.q + r] = x.q;
@@ -505,8 +506,8 @@ __device__ __forceinline__ void rx_store(const MechView& M, int r, const RxCore<
 
 // Rates of progress of reactions [rb, re).  Reactions are ordered Troe, third-body, elementary, so every
 // segment has warp-uniform control flow; elementary reactions go two per lane (two exp chains).
-template <class Sc, bool DERIV, class Gp>
-__device__ __forceinline__ void eval_reactions(const MechView& M, Sc* s, const CellLayout& L, const ScalT<Sc>& sc,
+template <class Sc, bool DERIV, class Gp, class MV, class LT>
+__device__ __forceinline__ void eval_reactions(const MV& M, Sc* s, const LT& L, const ScalT<Sc>& sc,
                                                const Gp& g, int rb, int re, int dq_off = 0, int d_off = 0) {
   const Sc* C = s + L.C;
   const Sc* eg = s + L.eg;
@@ -530,8 +531,8 @@ __device__ __forceinline__ void eval_reactions(const MechView& M, Sc* s, const C
 
 // -------------------------------------------------------------------------------------- f and J
 // f(y) into out[m].  Uses C/hRT/eg/emg/cpR/q scratch.  Returns the scalars of the evaluation.
-template <class Sc, class Gp>
-__device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
+template <class Sc, class Gp, class MV, class LT>
+__device__ __forceinline__ ScalT<Sc> eval_f(const MV& M, Sc* s, const LT& L, const Sc* y, double p,
                                             Sc* out, const Gp& g) {
   ScalT<Sc> sc = eval_species<Sc, false>(M, s, L, y, p, g);
   eval_reactions<Sc, false>(M, s, L, sc, g, 0, M.R);
@@ -555,8 +556,8 @@ __device__ __forceinline__ ScalT<Sc> eval_f(const MechView& M, Sc* s, const Cell
 // U1 (g), U2 (t).  The reactions run in passes (see MechView::jpass): each pass leaves dq/dT and the
 // derivative slots of its reactions in the region, and its gather adds them into the Y block of S
 // (Dtil) and into the T-column slots of S, which hold w_T until the T column is formed below.
-template <class Sc, class Gp>
-__device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const CellLayout& L, const Sc* y, double p,
+template <class Sc, class Gp, class MV, class LT>
+__device__ __forceinline__ ScalT<Sc> eval_jac(const MV& M, Sc* s, const LT& L, const Sc* y, double p,
                                               const Gp& g) {
   ScalT<Sc> sc = eval_species<Sc, true>(M, s, L, y, p, g);
   Sc* part = s + L.part;
@@ -624,8 +625,8 @@ __device__ __forceinline__ ScalT<Sc> eval_jac(const MechView& M, Sc* s, const Ce
 // -------------------------------------------------------------------------------------- linear algebra
 // LU of A = I/(h gamma) - S, in place, by the precomputed elimination program.  false if a pivot is 0
 // or not finite.
-template <class Gp>
-__device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, const CellLayout& L, double gh,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ bool lu_build_factor(const MV& M, double* s, const LT& L, double gh,
                                                 const Gp& g) {
   double* LU = s + L.LU;
   double* dinv = s + L.dinv;
@@ -666,8 +667,8 @@ __device__ __forceinline__ bool lu_build_factor(const MechView& M, double* s, co
 
 // x <- A^{-1} x (forward and backward substitution by the precomputed program; state-order vector).
 // With x2 != nullptr the same program solves a second right-hand side in the same steps.
-template <bool TWO, class Gp>
-__device__ __forceinline__ void lu_solve_impl(const MechView& M, const double* s, const CellLayout& L, double* x,
+template <bool TWO, class Gp, class MV, class LT>
+__device__ __forceinline__ void lu_solve_impl(const MV& M, const double* s, const LT& L, double* x,
                                               double* x2, const Gp& g) {
   const double* LU = s + L.LU;
   const double* dinv = s + L.dinv;
@@ -698,15 +699,15 @@ __device__ __forceinline__ void lu_solve_impl(const MechView& M, const double* s
   }
 }
 
-template <class Gp>
-__device__ __forceinline__ void lu_solve(const MechView& M, const double* s, const CellLayout& L, double* x,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ void lu_solve(const MV& M, const double* s, const LT& L, double* x,
                                          const Gp& g) {
   lu_solve_impl<false>(M, s, L, x, nullptr, g);
 }
 
 // x <- M^{-1} x with M = A - u v^T:  x = A^-1 x + z (v . A^-1 x) / (1 - v . z),  z = A^-1 u
-template <class Gp>
-__device__ __forceinline__ void sm_solve(const MechView& M, const double* s, const CellLayout& L, double* x,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ void sm_solve(const MV& M, const double* s, const LT& L, double* x,
                                          double iden, const Gp& g) {
   lu_solve(M, s, L, x, g);
   const double* v = s + L.v;
@@ -726,8 +727,8 @@ struct StepOut {
 
 // One RODAS3 attempt of size h from y (f0, S, u, v already evaluated at y).  ynew into ytmp, err into
 // the return value.  U1..U4, x, z, LU are scratch.
-template <class Gp>
-__device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, const CellLayout& L, double p, double h,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ StepOut ros_attempt(const MV& M, double* s, const LT& L, double p, double h,
                                                double rtol, double atol, const Gp& g) {
   StepOut so{false, 0.0};
   const int m = M.m;
@@ -796,8 +797,8 @@ __device__ __forceinline__ StepOut ros_attempt(const MechView& M, double* s, con
 }
 
 // One ROS2 attempt of size h from y (f0, S, u, v already evaluated at y); ynew into ytmp.
-template <class Gp>
-__device__ __forceinline__ StepOut ros2_attempt(const MechView& M, double* s, const CellLayout& L, double p, double h,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ StepOut ros2_attempt(const MV& M, double* s, const LT& L, double p, double h,
                                                 double rtol, double atol, const Gp& g) {
   StepOut so{false, 0.0};
   const int m = M.m;
@@ -853,8 +854,8 @@ __device__ __forceinline__ StepOut ros2_attempt(const MechView& M, double* s, co
 // the Jacobian's w_k vector (x), which is scratch until the next Jacobian evaluation; stage 6's
 // coefficient sum is gathered into U1 and its solution U6 takes U2's place, so the attempt needs no
 // shared memory beyond RODAS3's.
-template <class Gp>
-__device__ __forceinline__ StepOut ros4_attempt(const MechView& M, double* s, const CellLayout& L, double p, double h,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ StepOut ros4_attempt(const MV& M, double* s, const LT& L, double p, double h,
                                                 double rtol, double atol, const Gp& g) {
   StepOut so{false, 0.0};
   const int m = M.m;
@@ -971,8 +972,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Adaptive integration of the cell whose state sits in y (shared memory) over [0, dt].
-template <class Gp>
-__device__ __forceinline__ void integrate_cell(const MechView& M, double* s, const CellLayout& L, double p, double dt,
+template <class Gp, class MV, class LT>
+__device__ __forceinline__ void integrate_cell(const MV& M, double* s, const LT& L, double p, double dt,
                                                double& h_io, int& nsub, int& nacc, int& status, const IntOpts& o,
                                                const Gp& g, int cell) {
   double* y = s + L.y;

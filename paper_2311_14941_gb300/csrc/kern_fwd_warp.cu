@@ -10,6 +10,36 @@ template cudaError_t launch_persistent_g<Grp1>(dim3, dim3, size_t, cudaStream_t,
                                        const int*, unsigned long long*, int, const IntOpts&,
                                        const unsigned long long*, unsigned long long);
 
+// instantiated in the other lane groups' translation units (kern_fwd_warp_plain.cu, kern_fwd_pair.cu,
+// kern_fwd_half.cu): declared here so that the dispatch below does not instantiate them again
+extern template const void* plain_kernel<Grp1>();
+extern template cudaError_t launch_plain_g<Grp1>(dim3, dim3, size_t, cudaStream_t, const MechView&, const CellLayout&,
+                                               int, double*, const double*, double*, const double*, double*, int*,
+                                               int*, int*, const IntOpts&, const unsigned long long*,
+                                               unsigned long long);
+extern template const void* plain_kernel<Grp2>();
+extern template cudaError_t launch_plain_g<Grp2>(dim3, dim3, size_t, cudaStream_t, const MechView&, const CellLayout&,
+                                               int, double*, const double*, double*, const double*, double*, int*,
+                                               int*, int*, const IntOpts&, const unsigned long long*,
+                                               unsigned long long);
+extern template const void* persistent_kernel<Grp2>();
+extern template cudaError_t launch_persistent_g<Grp2>(dim3, dim3, size_t, cudaStream_t, const MechView&,
+                                                    const CellLayout&, int, double*, const double*, double*,
+                                                    const double*, double*, int*, int*, int*, const int*,
+                                                    unsigned long long*, int, const IntOpts&,
+                                                    const unsigned long long*, unsigned long long);
+extern template const void* plain_kernel<GrpH>();
+extern template cudaError_t launch_plain_g<GrpH>(dim3, dim3, size_t, cudaStream_t, const MechView&, const CellLayout&,
+                                               int, double*, const double*, double*, const double*, double*, int*,
+                                               int*, int*, const IntOpts&, const unsigned long long*,
+                                               unsigned long long);
+extern template const void* persistent_kernel<GrpH>();
+extern template cudaError_t launch_persistent_g<GrpH>(dim3, dim3, size_t, cudaStream_t, const MechView&,
+                                                    const CellLayout&, int, double*, const double*, double*,
+                                                    const double*, double*, int*, int*, int*, const int*,
+                                                    unsigned long long*, int, const IntOpts&,
+                                                    const unsigned long long*, unsigned long long);
+
 const void* forward_kernel(ForwardKernel kind, int g) {
   if (kind == KF_PLAIN) return g == 0 ? plain_kernel<Grp1>() : g == 1 ? plain_kernel<Grp2>() : plain_kernel<GrpH>();
   return g == 0 ? persistent_kernel<Grp1>() : g == 1 ? persistent_kernel<Grp2>() : persistent_kernel<GrpH>();

@@ -46,7 +46,7 @@ METHODS = {"rodas3": 0, "ros2": 1, "rodas4": 2}   # chem_integrate_opts.method
 PROFILED_TRAFFIC_PER_CELL = {"jet": 8.896512e6 / 16384}
 PROFILED_SOURCES = "5a5ebe9487393148"
 REF_CELLS = 256   # reference arm: cells per step (at least 16 per host core)
-KERNEL_SOURCES = ["kern_forward.cuh", "kern_fwd_warp.cu", "kernels.cuh", "compile.cpp", "device.cuh",
+KERNEL_SOURCES = ["integrate.cuh", "kern_forward.cuh", "kern_fwd_warp.cu", "kernels.cuh", "compile.cpp", "device.cuh",
                   "elementary_tables.h", "mech.h", "scalar.cuh"]
 
 
@@ -348,10 +348,11 @@ class Runner:
     """Timed chem_integrate steps on one workload: buffers, the step schedule and the work counts."""
 
     def __init__(self, h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, cells_per_warp=0,
-                 tab_tol=0.0):
+                 tab_tol=0.0, specialized=0):
         import torch
         self.h, self.F, self.evolving, self.dev, self.meth, self.oc = h, F, evolving, dev, meth, oc
         self.cpw = cells_per_warp
+        self.spec = specialized
         self.tab = dict(tabulate=1, tab_tol=tab_tol) if tab_tol > 0 else {}
         self.world, self.flush, self.clocks_path, self.local = world, flush, clocks_path, local
         N = F.n_cells
@@ -379,7 +380,8 @@ class Runner:
 
     def integrate(self, mode):
         self.h.integrate(self.T, self.P, self.Y, self.DT, self.hio, self.ns, self.st, rtol=RTOL, atol=ATOL,
-                         mode=mode, naccept=self.nacc, method=self.meth, cells_per_warp=self.cpw, **self.tab)
+                         mode=mode, naccept=self.nacc, method=self.meth, cells_per_warp=self.cpw,
+                         specialized=self.spec, **self.tab)
 
     def step(self, mode):
         """One flow step.  Evolving: the next step of the episode.  Otherwise: from the initial state again,
@@ -478,7 +480,8 @@ class Runner:
             self.P.copy_(Ph, non_blocking=True)
             self.DT.copy_(Dh, non_blocking=True)
             self.h.integrate(self.T, self.P, self.Y, self.DT, self.hio, self.ns, self.st, rtol=RTOL, atol=ATOL,
-                             mode=mode, method=self.meth, cells_per_warp=self.cpw, **self.tab)
+                             mode=mode, method=self.meth, cells_per_warp=self.cpw, specialized=self.spec,
+                             **self.tab)
             To.copy_(self.T, non_blocking=True)
             Yo.copy_(self.Y, non_blocking=True)
             Ho.copy_(self.hio, non_blocking=True)
@@ -519,6 +522,10 @@ def main():
     ap.add_argument("--tabulate", type=float, default=0.0,
                     help="evaluate the costly temperature functions from tables of this relative tolerance "
                          "(an approximation; 0: exact)")
+    ap.add_argument("--specialized", action="store_true",
+                    help="headline on the mechanism-specialised kernels (run-time compiled, one warp per cell)")
+    ap.add_argument("--no-specialized-ab", action="store_true",
+                    help="skip timing the specialised kernels beside the library's (default line)")
     args = ap.parse_args()
     global RTOL
     RTOL = args.rtol
@@ -542,12 +549,23 @@ def main():
     evolving = WORKLOADS[args.workload]["evolving"]
     meth = METHODS[args.method]
     h = chem.create(m, local)
+    spec_info = None
+    if args.specialized or not args.no_specialized_ab:
+        try:   # compiled before any timing; the time is reported, not counted
+            spec_info = {"compile_s": h.specialize()}
+        except chem.ChemError as e:
+            if args.specialized:
+                raise
+            spec_info = {"unavailable": str(e)}
+    one_warp = (args.cells_per_warp or int(h.info["auto_cells_per_warp"])) == 1 and \
+        int(h.info["auto_warps_per_cell"]) == 1
     oc = opcount.model(m, h.export_plan(0), h.export_plan(1), method=meth)
     N = F.n_cells
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     import tempfile
     clocks_path = os.path.join(tempfile.gettempdir(), f"chem_bench_clocks_r{rank}_{os.getpid()}.csv")
-    run = Runner(h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, args.cells_per_warp, args.tabulate)
+    run = Runner(h, F, evolving, dev, meth, oc, world, flush, clocks_path, local, args.cells_per_warp, args.tabulate,
+                 1 if args.specialized else 0)
 
     # headline mode first (W warm-up, K timed), then the other mode on the first K' of the same steps:
     # for an evolving field, the first episode's steps 2-10 (bit-identical states in both modes)
@@ -557,6 +575,12 @@ def main():
     k_other = min(args.steps, EPISODE - 1) if evolving else args.steps
     if not args.no_other_mode:
         res_other = run.run(other, 1, k_other, count_work=False)
+    # A/B of the kernels: the other build (specialised vs the library's) in the headline mode, same steps
+    res_ab = None
+    if spec_info is not None and "compile_s" in spec_info and one_warp and not args.no_specialized_ab:
+        run.spec = 0 if args.specialized else 1
+        res_ab = run.run(args.mode, 1, k_other, count_work=False)
+        run.spec = 1 if args.specialized else 0
     t_total = res["t"]
     value = world * N * args.steps / t_total
 
@@ -597,7 +621,8 @@ def main():
                        warps_per_cell=int(h.info["auto_warps_per_cell"]), method=args.method,
                        cells_per_warp=args.cells_per_warp or int(h.info["auto_cells_per_warp"]),
                        tabulated_temperature_functions=(f"tables of relative tolerance {args.tabulate:g} (an "
-                                                        "approximation)" if args.tabulate > 0 else "exact")),
+                                                        "approximation)" if args.tabulate > 0 else "exact"),
+                       kernels="mechanism-specialised (run-time compiled)" if args.specialized else "library"),
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -625,6 +650,20 @@ def main():
         o[f"{args.mode}_value_same_steps"] = world * N * k_other / t_same
         o[f"{args.mode}_over_{other}_same_steps"] = res_other["t"] / t_same
         line[other] = o
+    if spec_info is not None:
+        sp = dict(spec_info)
+        if res_ab is not None:
+            t_same = sum(res["step_ms"][:k_other]) / 1e3
+            ab = "library" if args.specialized else "specialized"
+            sp.update({f"{ab}_value": world * N * k_other / res_ab["t"], "unit": "reactor-steps/s",
+                       "steps": k_other, f"{ab}_step_ms": res_ab["step_ms"],
+                       "headline_value_same_steps": world * N * k_other / t_same,
+                       # throughput ratio, specialised over library, on the same flow steps
+                       "specialized_over_library": (t_same / res_ab["t"]) if not args.specialized
+                       else (res_ab["t"] / t_same), "mode": args.mode})
+        elif not one_warp:
+            sp["note"] = "not timed: the specialised kernels run one cell per warp, this workload's choice differs"
+        line["specialized"] = sp
     if res["clocks"]:
         line["clocks"] = res["clocks"]
     if secondary is not None:

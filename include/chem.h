@@ -180,6 +180,12 @@ typedef struct {
                              returns CHEM_EINVAL otherwise.  The tables hold the description's parameters:
                              CHEM_EINVAL after chem_set_params shifted them.  0: exact (default). */
   double tab_tol;         /* relative error bound of the tables; 0: 1e-10 */
+  int specialized;        /* chem_integrate and chem_integrate_noalloc: 1 = run the mechanism-specialised
+                             one-warp-per-cell kernels that chem_specialize compiled for this handle
+                             (CHEM_EINVAL before that, or with warps_per_cell or cells_per_warp 2);
+                             results agree with the library's own one-warp kernels to rounding (the
+                             compiler may contract or order floating-point operations differently).
+                             0: the library's kernels (default). */
 } chem_integrate_opts;
 
 /* Compile a mechanism for `device`: validation (indices, positive W and A, finite parameters,
@@ -198,6 +204,27 @@ chem_status chem_create(const chem_mech_desc* desc, int device, chem_handle* out
    inconsistent lengths; then as chem_create. */
 chem_status chem_create_from_json(const char* json_text, int device, chem_handle* out);
 chem_status chem_destroy(chem_handle h);
+
+/* Mechanism-specialised integration kernels (opt-in).  The one-warp-per-cell integration kernels (plain
+   and persistent form) are compiled again at run time (NVRTC, loaded with dlopen) with this mechanism's
+   sizes (species, reactions, nonzeros of S and of the factor, steps of the elimination and substitution
+   programs) and the cell's shared-memory offsets as compile-time constants, so that the compiler folds
+   the trip counts and addresses of the sparse-analytical evaluation into the code (Sec. 2.5: SpeedCHEM
+   manages the mechanism's sparse algebra internally).  The tables and
+   programs stay in device memory; only sizes and offsets become constants.  The kernels are loaded into
+   the handle's device and used by calls with chem_integrate_opts.specialized = 1 until chem_destroy.
+   Compiled code is cached on disk (directory CHEM_RTC_CACHE, else rtc_cache beside the library), keyed
+   by the source, the headers, the options and the compiler's version; a second handle of the same
+   mechanism loads it from there.  *compile_s (optional) receives the compile time in seconds (0 when
+   both kernels came from the cache or the handle holds them already).  CHEM_EUNSUPPORTED when
+   libnvrtc.so.13 cannot be loaded; CHEM_ECUDA with the compiler's log when compiling or loading fails.
+   Calling it again on the same handle does nothing.  On a host-only handle (device -1) it compiles into
+   the cache and loads nothing (no GPU needed), e.g. to fill the cache ahead of a run. */
+chem_status chem_specialize(chem_handle h, double* compile_s);
+/* The generated source of chem_specialize (the views with constant members; it includes the library's
+   device headers).  buf: host memory of *len bytes, or NULL to query; on return *len = bytes needed
+   (terminating NUL included); CHEM_EINVAL when buf is too small.  Works on host-only handles. */
+chem_status chem_specialized_source(chem_handle h, char* buf, int* len);
 
 /* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
 const char* chem_last_error(void);

@@ -49,7 +49,7 @@ class OptsC(C.Structure):
                 ("mode", C.c_int), ("block_cells", C.c_int), ("chunk", C.c_int), ("naccept", _vp),
                 ("trace", _vp), ("trace_cap", C.c_int), ("ckpt_every", C.c_int), ("tape_steps", C.c_int),
                 ("warps_per_cell", C.c_int), ("method", C.c_int), ("cells_per_warp", C.c_int),
-                ("tabulate", C.c_int), ("tab_tol", C.c_double)]
+                ("tabulate", C.c_int), ("tab_tol", C.c_double), ("specialized", C.c_int)]
 
 
 class MapOptsC(C.Structure):
@@ -94,9 +94,11 @@ def lib():
         L.chem_balance_plan.argtypes = [C.c_int, _vp, _vp, _vp]
         L.chem_integrate_mapped.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(OptsC),
                                             C.POINTER(MapOptsC), _vp, C.POINTER(C.c_int), _vp]
+        L.chem_specialize.argtypes = [_vp, C.POINTER(C.c_double)]
+        L.chem_specialized_source.argtypes = [_vp, C.c_char_p, C.POINTER(C.c_int)]
         for f in ("chem_integrate_mapped", "chem_balance_plan", "chem_eval_elementary", "chem_create_from_json", "chem_create", "chem_destroy", "chem_info", "chem_jacobian_pattern", "chem_export_plan",
                   "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_noalloc", "chem_set_params",
-                  "chem_adjoint"):
+                  "chem_adjoint", "chem_specialize", "chem_specialized_source"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -204,6 +206,21 @@ class Mechanism:
         _check(lib().chem_export_plan(self._h, which, out.ctypes.data_as(_ip), C.byref(cnt)), "chem_export_plan")
         return out[: cnt.value]
 
+    def specialize(self) -> float:
+        """chem_specialize: compile (or load from the cache) the mechanism-specialised one-warp kernels for
+        this handle; returns the compile time in seconds (0 from the cache)."""
+        t = C.c_double(0.0)
+        _check(lib().chem_specialize(self._h, C.byref(t)), "chem_specialize")
+        return t.value
+
+    def specialized_source(self) -> str:
+        """chem_specialized_source: the run-time compiled source of ``specialize``."""
+        n = C.c_int(0)
+        _check(lib().chem_specialized_source(self._h, None, C.byref(n)), "chem_specialized_source")
+        buf = C.create_string_buffer(n.value)
+        _check(lib().chem_specialized_source(self._h, buf, C.byref(n)), "chem_specialized_source")
+        return buf.value.decode()
+
     # ---------------------------------------------------------------------------------- compute
     def rates(self, T, p, Y, dTdt, dYdt, wdot=None, stream=None):
         """chem_rates on device tensors (outputs written in place)."""
@@ -227,14 +244,16 @@ class Mechanism:
 
     def integrate(self, T, p, Y, dt, h_io, nsub, status, rtol=1e-6, atol=1e-12, h_init=0.0, h_min=0.0,
                   time_budget_s=0.0, max_substeps=0, max_nonfinite=0, mode=0, block_cells=0, chunk=0, naccept=None,
-                  trace=None, warps_per_cell=0, method=0, cells_per_warp=0, tabulate=0, tab_tol=0.0, stream=None):
-        """chem_integrate on device tensors: T, Y, h_io, nsub, status (and naccept) are updated in place."""
+                  trace=None, warps_per_cell=0, method=0, cells_per_warp=0, tabulate=0, tab_tol=0.0, specialized=0,
+                  stream=None):
+        """chem_integrate on device tensors: T, Y, h_io, nsub, status (and naccept) are updated in place.
+        specialized=1 runs the kernels ``specialize()`` compiled for this mechanism."""
         import torch
         N = T.numel()
         cap = trace.numel() // max(N, 1) if trace is not None else 0
         o = OptsC(rtol, atol, h_init, h_min, time_budget_s, max_substeps, max_nonfinite, mode, block_cells, chunk,
                   _dptr(naccept, torch.int32, N, "naccept"), _dptr(trace, torch.float64, cap * N, "trace"), cap,
-                  0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol)
+                  0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol, specialized)
         _check(lib().chem_integrate(self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
                                     _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),
                                     _dptr(h_io, torch.float64, N, "h_io"), _dptr(nsub, torch.int32, N, "nsub"),
@@ -268,7 +287,7 @@ class Mechanism:
     def integrate_noalloc(self, T, p, Y, dt, h_io, nsub, status, rtol=1e-6, atol=1e-12, h_init=0.0, h_min=0.0,
                           time_budget_s=0.0, max_substeps=0, max_nonfinite=0, block_cells=0, chunk=0, naccept=None,
                           trace=None, warps_per_cell=0, method=0, cells_per_warp=0, tabulate=0, tab_tol=0.0,
-                          stream=None):
+                          specialized=0, stream=None):
         """chem_integrate_noalloc: the sorted work-queue integration with its scratch in the library's
         static device memory (no allocation in the call; at most 1,048,576 cells; calls must not overlap
         on the GPU).  In-place like ``integrate``."""
@@ -277,7 +296,7 @@ class Mechanism:
         cap = trace.numel() // max(N, 1) if trace is not None else 0
         o = OptsC(rtol, atol, h_init, h_min, time_budget_s, max_substeps, max_nonfinite, 1, block_cells, chunk,
                   _dptr(naccept, torch.int32, N, "naccept"), _dptr(trace, torch.float64, cap * N, "trace"), cap,
-                  0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol)
+                  0, 0, warps_per_cell, method, cells_per_warp, tabulate, tab_tol, specialized)
         _check(lib().chem_integrate_noalloc(
             self._h, N, _dptr(T, torch.float64, N, "T"), _dptr(p, torch.float64, N, "p"),
             _dptr(Y, torch.float64, self.n * N, "Y"), _dptr(dt, torch.float64, N, "dt"),

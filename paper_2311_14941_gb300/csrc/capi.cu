@@ -12,8 +12,14 @@
 #include "../../include/chem.h"
 #include "compile.h"
 #include "kernels.cuh"
+#include "specialize.h"
 
 using namespace chemgb;
+
+static_assert(kCellOk == CHEM_CELL_OK && kCellMaxSteps == CHEM_CELL_MAXSTEPS && kCellHmin == CHEM_CELL_HMIN &&
+                  kCellNonfinite == CHEM_CELL_NONFINITE && kCellBadInput == CHEM_CELL_BADINPUT &&
+                  kCellTimeout == CHEM_CELL_TIMEOUT,
+              "device status codes differ from chem.h");
 
 namespace {
 
@@ -65,6 +71,10 @@ struct chem_handle_s {
   HostTables tabs;
   void* tab_dev = nullptr;
   bool params_shifted = false;     // chem_set_params moved the Arrhenius parameters off the description's
+  // mechanism-specialised one-warp kernels (chem_specialize), their largest block and occupancy
+  SpecKernels spec;
+  int spec_max_cells = 1;
+  int spec_bps_cache[kMaxBlockCells + 1] = {};
   // CUDA graph of the persistent sequence, re-captured when its arguments change
   struct GraphKey {
     int N, mode, cpb, chunk, grp;
@@ -314,11 +324,14 @@ chem_status launch_check(const char* what) {
   return CHEM_OK;
 }
 
-// Resident blocks per SM of the persistent kernel for a launch shape (cached per shape).
-chem_status persistent_blocks_per_sm(chem_handle h, int grp, int cpb, int& bps) {
-  int& cached = h->bps_cache[grp][cpb];
+// Resident blocks per SM of the persistent kernel for a launch shape (cached per shape; spec: the
+// mechanism-specialised kernel, one warp per cell).
+chem_status persistent_blocks_per_sm(chem_handle h, int grp, int cpb, int& bps, bool spec = false) {
+  int& cached = spec ? h->spec_bps_cache[cpb] : h->bps_cache[grp][cpb];
   if (cached == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, forward_kernel(KF_PERSISTENT, grp),
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached,
+                                                                  spec ? h->spec.persistent
+                                                                       : forward_kernel(KF_PERSISTENT, grp),
                                                                   cpb * kGroupWidth[grp],
                                                                   (size_t)cpb * h->cell_bytes);
     if (e != cudaSuccess) { cached = 0; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
@@ -363,6 +376,7 @@ struct IntCall {
   int chunk = 1;   // persistent form: cells per queue pull
   int tab = 0;     // tabulated temperature functions
   double tab_tol = 0.0;
+  int spec = 0;    // the mechanism-specialised kernels (one warp per cell)
 };
 
 chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opts, IntCall& c) {
@@ -384,20 +398,65 @@ chem_status parse_integrate(chem_handle h, int N, const chem_integrate_opts* opt
   c.tab_tol = o.tab_tol > 0.0 ? o.tab_tol : 1e-10;
   if (c.tab && h->params_shifted)
     return fail(CHEM_EINVAL, "tabulate: the tables hold the description's parameters, which chem_set_params shifted");
+  if (o.specialized != 0 && o.specialized != 1) return fail(CHEM_EINVAL, "specialized must be 0 or 1");
+  c.spec = o.specialized;
+  if (c.spec && !h->spec.plain)
+    return fail(CHEM_EINVAL, "specialized: chem_specialize has not compiled this handle's kernels");
+  if (c.spec && (o.warps_per_cell > 1 || o.cells_per_warp > 1))
+    return fail(CHEM_EINVAL, "specialized kernels integrate one cell per warp (warps_per_cell, cells_per_warp <= 1)");
   if ((st = set_attrs(h)) != CHEM_OK) return st;
   c.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-  if (o.cells_per_warp == 2) c.grp = 2;
+  if (c.spec) c.grp = 0;
+  else if (o.cells_per_warp == 2) c.grp = 2;
   else if (o.cells_per_warp == 0 && o.warps_per_cell == 0 && h->auto_cpw == 2) c.grp = 2;
   else c.grp = (o.warps_per_cell > 0 ? o.warps_per_cell : h->auto_wpc) - 1;
   c.cpb = cells_per_block(h, o.block_cells, c.grp);
+  if (c.spec) c.cpb = std::min(c.cpb, h->spec_max_cells);
   int bps = 1;
-  if ((st = persistent_blocks_per_sm(h, c.grp, c.cpb, bps)) != CHEM_OK) return st;
+  if ((st = persistent_blocks_per_sm(h, c.grp, c.cpb, bps, c.spec != 0)) != CHEM_OK) return st;
   c.grid = h->num_sms * bps;
   // a pull larger than an even share of the cells over the resident lane groups only leaves groups idle
   const long long groups = (long long)c.grid * c.cpb;
   const long long share = std::max(1LL, ((long long)N + groups - 1) / groups);
   c.chunk = (int)std::min<long long>(o.chunk > 0 ? o.chunk : 1, share);
   return CHEM_OK;
+}
+
+// Launches of the integration kernel chosen by an integration call: the library's instantiation of lane
+// group c.grp, or the mechanism-specialised kernel (same parameters, launched through its handle).
+cudaError_t launch_plain(const chem_handle h, const IntCall& c, dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t strm, const MechView& V, int N, double* T, const double* p, double* Y,
+                         const double* dt, double* h_io, int* nsub, int* status, const unsigned long long* stamp) {
+  if (!c.spec)
+    return launch_integrate_plain(c.grp, grid, block, smem, strm, V, h->L, N, T, p, Y, dt, h_io, nsub, status,
+                                  c.o.naccept, c.io, stamp, c.budget_ns);
+  if (block.x % kWarp != 0 || block.y != 1 || block.z != 1) return cudaErrorInvalidValue;
+  MechView v = V;
+  CellLayout L = h->L;
+  int* nacc = c.o.naccept;
+  IntOpts io = c.io;
+  unsigned long long budget = c.budget_ns;
+  void* args[] = {&v, &L, &N, &T, (void*)&p, &Y, (void*)&dt, &h_io, &nsub, &status, &nacc, &io, (void*)&stamp, &budget};
+  return cudaLaunchKernel(h->spec.plain, grid, block, args, smem, strm);
+}
+
+cudaError_t launch_persistent(const chem_handle h, const IntCall& c, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t strm, const MechView& V, int N, double* T, const double* p, double* Y,
+                              const double* dt, double* h_io, int* nsub, int* status, const int* perm,
+                              unsigned long long* head, const unsigned long long* stamp) {
+  if (!c.spec)
+    return launch_integrate_persistent(c.grp, grid, block, smem, strm, V, h->L, N, T, p, Y, dt, h_io, nsub, status,
+                                       c.o.naccept, perm, head, c.chunk, c.io, stamp, c.budget_ns);
+  if (block.x % kWarp != 0 || block.y != 1 || block.z != 1) return cudaErrorInvalidValue;
+  MechView v = V;
+  CellLayout L = h->L;
+  int* nacc = c.o.naccept;
+  int chunk = c.chunk;
+  IntOpts io = c.io;
+  unsigned long long budget = c.budget_ns;
+  void* args[] = {&v,    &L,     &N,    &T,         (void*)&p, &Y,  (void*)&dt,     &h_io,  &nsub,
+                  &status, &nacc, (void*)&perm, &head, &chunk,   &io, (void*)&stamp, &budget};
+  return cudaLaunchKernel(h->spec.persistent, grid, block, args, smem, strm);
 }
 
 // The tables of tolerance tol in device memory: built on the host and uploaded when the handle holds
@@ -591,8 +650,57 @@ chem_status chem_destroy(chem_handle h) {
   if (h->adj_scratch) cudaFree(h->adj_scratch);
   if (h->map_scratch) cudaFree(h->map_scratch);
   if (h->tab_dev) cudaFree(h->tab_dev);
+  release_specialized(h->spec);
   delete h;
   return CHEM_OK;
+}
+
+chem_status chem_specialize(chem_handle h, double* compile_s) {
+  if (h && h->device < 0) {   // host-only handle: compile into the cache, load nothing
+    std::string err;
+    SpecKernels k;
+    chem_status st = compile_specialized(h->hm, h->L, false, k, err);
+    if (st != CHEM_OK) return fail(st, err);
+    if (compile_s) *compile_s = k.compile_s;
+    return CHEM_OK;
+  }
+  DeviceScope ds;
+  chem_status st = check_handle(h, ds);
+  if (st != CHEM_OK) return st;
+  if (h->spec.plain) {   // already compiled for this handle (graphs may hold the loaded kernels)
+    if (compile_s) *compile_s = 0.0;
+    return CHEM_OK;
+  }
+  if ((st = set_attrs(h)) != CHEM_OK) return st;
+  std::string err;
+  SpecKernels k;
+  if ((st = compile_specialized(h->hm, h->L, true, k, err)) != CHEM_OK) return fail(st, err);
+  cudaError_t e = cudaSuccess;
+  cudaFuncAttributes fa1, fa2;
+  for (const void* f : {k.plain, k.persistent})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_optin);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa1, k.plain);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa2, k.persistent);
+  if (e != cudaSuccess) {
+    release_specialized(k);
+    return cuda_fail(e, "attributes of the specialised kernels");
+  }
+  // largest block: the generic one-warp bound and the threads the specialised kernels' registers allow
+  h->spec_max_cells =
+      std::max(1, std::min(h->max_cells[0], std::min(fa1.maxThreadsPerBlock, fa2.maxThreadsPerBlock) / kWarp));
+  h->spec = k;
+  if (compile_s) *compile_s = k.compile_s;
+  return CHEM_OK;
+}
+
+chem_status chem_specialized_source(chem_handle h, char* buf, int* len) {
+  if (!h || !len) return fail(CHEM_EINVAL, "null argument");
+  const std::string src = specialized_source(h->hm, h->L);
+  const int need = (int)src.size() + 1;
+  if (buf && *len >= need) std::memcpy(buf, src.c_str(), (size_t)need);
+  const bool small = buf && *len < need;
+  *len = need;
+  return small ? fail(CHEM_EINVAL, "buffer too small (len now holds the size needed)") : CHEM_OK;
 }
 
 chem_status chem_info(chem_handle h, chem_info_t* info) {
@@ -725,8 +833,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
       stamp = (unsigned long long*)((char*)h->scratch + kScrStamp);
       k_stamp<<<1, 32, 0, strm>>>(stamp);
     }
-    if ((e = launch_integrate_plain(grp, (N + cpb - 1) / cpb, cpb * width, cpb * h->cell_bytes, strm, V, h->L, N, T, p,
-                                    Y, dt, h_io, nsub, status, o.naccept, io, stamp, budget_ns)) != cudaSuccess)
+    if ((e = launch_plain(h, c, (N + cpb - 1) / cpb, cpb * width, cpb * h->cell_bytes, strm, V, N, T, p, Y, dt, h_io,
+                          nsub, status, stamp)) != cudaSuccess)
       return cuda_fail(e, "chem_integrate launch shape");
     return launch_check("chem_integrate launch");
   }
@@ -740,7 +848,7 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
   for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
   key.d[0] = io.rtol; key.d[1] = io.atol; key.d[2] = io.h_init; key.d[3] = io.h_min; key.d[4] = o.time_budget_s;
   key.i[0] = io.max_substeps; key.i[1] = io.max_nonfinite; key.i[2] = io.trace_cap; key.i[3] = io.method;
-  key.i[4] = c.tab;
+  key.i[4] = c.tab + 2 * c.spec;
   key.d[5] = c.tab ? c.tab_tol : 0.0;
   if (!h->gexec || !(h->gkey == key)) {
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
@@ -761,9 +869,8 @@ chem_status chem_integrate(chem_handle h, int N, double* T, const double* p, dou
     k_stamp<<<1, 32, 0, cs>>>(stamp);
     k_sort_count<<<sblocks, 256, 0, cs>>>(N, nsub, counts);
     k_sort_scatter<<<sblocks, 256, 0, cs>>>(N, nsub, counts, cursor, perm);
-    const cudaError_t se = launch_integrate_persistent(grp, grid, cpb * width, cpb * h->cell_bytes, cs, V, h->L, N, T,
-                                                       p, Y, dt, h_io, nsub, status, o.naccept, perm, head, chunk, io,
-                                                       stamp, budget_ns);
+    const cudaError_t se = launch_persistent(h, c, grid, cpb * width, cpb * h->cell_bytes, cs, V, N, T, p, Y, dt,
+                                             h_io, nsub, status, perm, head, stamp);
     cudaGraph_t graph = nullptr;
     cudaError_t le = se != cudaSuccess ? se : cudaGetLastError();
     e = cudaStreamEndCapture(cs, &graph);
@@ -949,9 +1056,8 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int N, double* T, c
   k_stamp<<<1, 32, 0, strm>>>(stamp);
   k_sort_count<<<sblocks, 256, 0, strm>>>(N, nsub, counts);
   k_sort_scatter<<<sblocks, 256, 0, strm>>>(N, nsub, counts, cursor, perm);
-  if ((e = launch_integrate_persistent(grp, grid, wpb * kGroupWidth[grp], wpb * h->cell_bytes, strm,
-                                       view_for(h, grp, c.tab), h->L, N, T, p, Y, dt, h_io, nsub, status, c.o.naccept,
-                                       perm, head, c.chunk, c.io, stamp, c.budget_ns)) != cudaSuccess)
+  if ((e = launch_persistent(h, c, grid, wpb * kGroupWidth[grp], wpb * h->cell_bytes, strm, view_for(h, grp, c.tab),
+                             N, T, p, Y, dt, h_io, nsub, status, perm, head, stamp)) != cudaSuccess)
     return cuda_fail(e, "chem_integrate_noalloc launch shape");
   return launch_check("chem_integrate_noalloc launch");
 }

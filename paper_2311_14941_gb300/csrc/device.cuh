@@ -20,9 +20,6 @@
 //            y_new = y + sum m_i U_i,  err = sum e_i U_i,
 //          where J = S + u v^T is inverted by Sherman-Morrison around the sparse LU of I/(h gamma) - S.
 #pragma once
-#include <cstdint>
-#include <type_traits>
-
 #include "mech.h"
 #include "scalar.cuh"
 
@@ -179,8 +176,16 @@ struct ScalT {
   double ttau;
 };
 
+template <class A, class B>
+struct same_type {
+  static constexpr bool value = false;
+};
+template <class A>
+struct same_type<A, A> {
+  static constexpr bool value = true;
+};
 template <class Sc>
-constexpr bool is_real() { return std::is_same<Sc, double>::value; }
+__host__ __device__ constexpr bool is_real() { return same_type<Sc, double>::value; }
 
 // Polynomial in tau with coefficients c[0..d] (table memory, read-only path).
 __device__ __forceinline__ double tab_poly(const double* c, int d, double tau) {
@@ -991,7 +996,7 @@ __device__ __forceinline__ void integrate_cell(const MV& M, double* s, const LT&
   nsub = 0;
   nacc = 0;
   if (!ok) {
-    status = CHEM_CELL_BADINPUT;
+    status = kCellBadInput;
     if (o.rec_h && g.lane == 0) o.rec_n[cell] = -1;
     return;
   }
@@ -999,18 +1004,18 @@ __device__ __forceinline__ void integrate_cell(const MV& M, double* s, const LT&
   if (dt > 0.0) h = fmin(h, dt);
   double t = 0.0;
   bool rejected_last = false, needJ = true;
-  int nonfinite = 0, ns = 0, na = 0, st = CHEM_CELL_OK;
+  int nonfinite = 0, ns = 0, na = 0, st = kCellOk;
   if (o.rec_h)
     for (int i = g.lane; i < m; i += g.size) o.rec_ck[(size_t)i * o.N + cell] = y[i];
   while (t < dt) {
-    if (ns >= o.max_substeps) { st = CHEM_CELL_MAXSTEPS; break; }
+    if (ns >= o.max_substeps) { st = kCellMaxSteps; break; }
     if (o.deadline_ns) {
       const unsigned long long now = (unsigned long long)gbcast(g, g.lane == 0 ? (long long)global_ns() : 0ll);
-      if (now > o.deadline_ns) { st = CHEM_CELL_TIMEOUT; break; }
+      if (now > o.deadline_ns) { st = kCellTimeout; break; }
     }
     const bool last = (t + h >= dt * (1.0 - 1e-14));
     const double hu = last ? dt - t : h;
-    if (hu < o.h_min) { st = CHEM_CELL_HMIN; break; }
+    if (hu < o.h_min) { st = kCellHmin; break; }
     ++ns;
     if (needJ) {
       eval_jac<double>(M, s, L, y, p, g);
@@ -1022,7 +1027,7 @@ __device__ __forceinline__ void integrate_cell(const MV& M, double* s, const LT&
     if (o.trace && g.lane == 0 && ns <= o.trace_cap)
       o.trace[(size_t)(ns - 1) * o.N + cell] = (so.good && isfinite(so.err) && so.err <= 1.0) ? hu : -hu;
     if (!so.good || !isfinite(so.err)) {
-      if (++nonfinite >= o.max_nonfinite) { st = CHEM_CELL_NONFINITE; break; }
+      if (++nonfinite >= o.max_nonfinite) { st = kCellNonfinite; break; }
       h = hu * 0.1;
       rejected_last = true;
       continue;
@@ -1051,7 +1056,7 @@ __device__ __forceinline__ void integrate_cell(const MV& M, double* s, const LT&
     }
   }
   if (o.trace && g.lane == 0 && ns < o.trace_cap) o.trace[(size_t)ns * o.N + cell] = 0.0;
-  if (o.rec_h && g.lane == 0) o.rec_n[cell] = (na <= o.rec_cap && st == CHEM_CELL_OK) ? na : -1;
+  if (o.rec_h && g.lane == 0) o.rec_n[cell] = (na <= o.rec_cap && st == kCellOk) ? na : -1;
   h_io = h;
   nsub = ns;
   nacc = na;

@@ -4,9 +4,21 @@
 // kernels by value.  Index fields of the warp programs are 16 bits wide, which bounds reactions,
 // derivative slots and factor entries to 65535 (chem_create reports CHEM_EUNSUPPORTED beyond).
 #pragma once
+#ifdef __CUDACC_RTC__
+// run-time compilation (mechanism-specialised kernels) has no C library headers
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#else
 #include <cstdint>
+#endif
 
 namespace chemgb {
+
+// Per-cell status codes of the device code (the same values as chem.h's CHEM_CELL_*, checked there).
+enum : int { kCellOk = 0, kCellMaxSteps = 1, kCellHmin = 2, kCellNonfinite = 3, kCellBadInput = 4, kCellTimeout = 5 };
 
 constexpr double kRu = 8.314462618;   // J/(mol K)
 constexpr double kP0 = 101325.0;      // Pa, standard state of Kc

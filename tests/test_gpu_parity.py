@@ -329,3 +329,59 @@ def test_tabulated_options_are_checked(dev):
     for kw in (dict(tabulate=2), dict(tabulate=1, tab_tol=1.5), dict(tabulate=1, tab_tol=-1.0)):
         with pytest.raises(chem.ChemError):
             _integrate_gpu(h, F, dev, **kw)
+
+
+# ------------------------------------------------------------------ mechanism-specialised kernels
+_spec = {}
+
+
+def spec_handle(name):
+    """A handle of its own with the run-time compiled kernels (the cached handles above stay generic)."""
+    if name not in _spec:
+        h = chem.create(MECHS[name](), 0)
+        h.specialize()
+        _spec[name] = h
+    return _spec[name]
+
+
+def _spec_field(m, name):
+    if name == "small":
+        return synth.field_uniform_random(m, 1024, seed=1), 8000, 0.02
+    if name == "mid":
+        G = synth.field_bimodal_jet(m, 256, 256, seed=2)
+        rng = np.random.default_rng(9)
+        idx = np.sort(np.concatenate([rng.choice(np.where(G.kind == k)[0], 40, replace=False) for k in (0, 1, 2)]))
+        return G.subset(idx), 4000, 0.03
+    G = synth.field_bimodal_jet(m, 16, 16, seed=5, dt_range=(1e-6, 1e-4))
+    return G.subset(np.arange(0, 256, 16)), 2000, 0.07
+
+
+@pytest.mark.parametrize("name,mode", [("small", 0), ("small", 1), ("mid", 1), ("large", 0)])
+def test_specialized_kernels_parity(dev, name, mode):
+    """Mechanism-specialised one-warp kernels (sizes and shared-memory offsets compiled in at run time)
+    against the oracle, trace-matched as above, on the three mechanisms (plain and sorted-queue form); and
+    against the library's own one-warp kernels on the same inputs: the same step counts on almost every
+    cell, the same results there to the integration tolerance."""
+    m, _, o = mech(name)
+    h = spec_handle(name)
+    F, cap, flips = _spec_field(m, name)
+    r = o.integrate_batch(F.T, F.p, F.Y, F.dt, trace_cap=cap)
+    g = _integrate_gpu(h, F, dev, trace_cap=cap, warps_per_cell=1, mode=mode, specialized=1)
+    _compare_integration(o, g, r, F, flips)
+    e = _integrate_gpu(h, F, dev, warps_per_cell=1, mode=mode)
+    same = e["nsub"] == g["nsub"]
+    assert same.mean() >= 0.95, same.mean()
+    assert np.max(np.abs(e["T"][same] - g["T"][same]) / e["T"][same]) <= RTOL_INT
+    print(f"{name}: bit-identical to the library's kernels on {int(np.sum(e['T'] == g['T']))} of {F.n_cells} cells")
+
+
+def test_specialized_options_are_checked(dev):
+    m, plain_h, _ = mech("small")
+    F = synth.field_uniform_random(m, 8, seed=2)
+    with pytest.raises(chem.ChemError):                      # never specialised
+        _integrate_gpu(plain_h, F, dev, specialized=1)
+    h = spec_handle("small")
+    for kw in (dict(specialized=2), dict(specialized=1, warps_per_cell=2), dict(specialized=1, cells_per_warp=2)):
+        with pytest.raises(chem.ChemError):
+            _integrate_gpu(h, F, dev, **kw)
+    assert h.specialize() == 0.0                             # a second call does nothing

@@ -76,6 +76,23 @@ def test_noalloc_matches_persistent_entry_point_on_two_calls(dev, wpc, chunk, me
     assert np.all(got2["status"] == 0)
 
 
+def test_noalloc_specialized_matches_persistent_entry_point(dev):
+    """The mechanism-specialised kernels behind both entry points: bit-equal results, two calls."""
+    m, h, F = _mid_handle()
+    h.specialize()
+    S = F.subset(np.arange(800))
+    kw = dict(warps_per_cell=1, chunk=2, specialized=1)
+    zeros = np.zeros(S.n_cells, dtype=np.int32)
+    ref1 = _call(h, S, dev, zeros, noalloc=False, **kw)
+    got1 = _call(h, S, dev, zeros, noalloc=True, **kw)
+    ref2 = _call(h, S, dev, ref1["nsub"], noalloc=False, **kw)
+    got2 = _call(h, S, dev, got1["nsub"], noalloc=True, **kw)
+    for ref, got in ((ref1, got1), (ref2, got2)):
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+    assert np.all(got2["status"] == 0)
+
+
 def test_noalloc_and_persistent_accept_the_largest_chunk(dev):
     """chunk = INT_MAX is reduced to an even share of the cells per lane group: same results as chunk 1."""
     m, h, F = _mid_handle()

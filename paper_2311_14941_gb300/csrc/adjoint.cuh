@@ -25,15 +25,19 @@ namespace chemgb {
 // Memory of the reverse pass.  Shared memory holds the forward cell layout L only (the factor shares
 // its region with the Jacobian's pass scratch, as in the integrator), so as many warps per SM fit as
 // for the forward pass.  Everything else of a warp lives in its own slice of global memory (offsets in
-// doubles below), read and written lane-strided, except the copies of the step's factor and Jacobian,
-// which the transposed solves and the last product with J(y)^T read by index.
+// doubles below), read and written lane-strided, except the step records (the step's Jacobian and
+// factor), which the transposed solves and the products with J(y)^T read by index.
 struct AdjLayout {
   CellLayout L;        // shared memory: the forward layout
-  int Y3, Y4, W1, W2, W3, W4, MU1, MU2, MU3, MU4, LAM, G, ZT, WS, UY, VY, HY;   // m-vectors (HY: h/RT at y)
+  int Y3, Y4, W1, W2, W3, W4, MU1, MU2, MU3, MU4, LAM, G, ZT, WS;   // m-vectors
+  // step record, kept by the segment recompute for every step of the segment (offsets within a record):
   int SY;              // nnz_S: S at y (the step's own Jacobian)
+  int UY, VY;          // m each: the rank-one part u v^T at y
+  int HY;              // n: h/RT at y
   int QY;              // R: rates of progress at y
-  int LUG;             // nnz_LU + m: the step's factor and its reciprocal pivots
   int SC;              // 8: T, rho, c_p, 1/rho at y
+  int LUG;             // nnz_LU + m: the step's factor and its reciprocal pivots
+  int JREC, jstride;   // K records of jstride doubles
   int UST;             // K * 4m: U1..U4 of every step of the current segment
   int SEG;             // K * m: the segment's states
   int GA, GE;          // R each: the cell's gradient accumulators (compiled reaction order)
@@ -111,50 +115,61 @@ __device__ __forceinline__ void vset(double* dst, const double* src, int m, cons
   g.sync();
 }
 
+// Tangents carried per dual-number evaluation of the Jacobian in the second-order terms: the four stages
+// take 4 / kTangentsPerPass passes (fewer live registers per dual number against a little more
+// arithmetic per pass).
+constexpr int kTangentsPerPass = 2;
+
 // sum_st (d_st J)^T W_st into out (m), J = S + u v^T at the dual point (d_st: tangent st):
 //   d(J^T w) = dS^T w + dv (u . w) + v (du . w).
-__device__ __forceinline__ void vjp_tangents(const MechView& M, const Dual4* S, const Dual4* u, const Dual4* v,
-                                             const double* const* Ws, double* out, double* part, const Grp1& g) {
+template <int NT>
+__device__ __forceinline__ void vjp_tangents(const MechView& M, const DualN<NT>* S, const DualN<NT>* u,
+                                             const DualN<NT>* v, const double* const* Ws, double* out, double* part,
+                                             const Grp1& g) {
   run_gather(M.g_col, out + 1, part, [&](int a, int b) {
     double acc = 0.0;
 #pragma unroll
-    for (int st = 0; st < 4; ++st) acc = fma(S[a].d[st], Ws[st][1 + b], acc);
+    for (int st = 0; st < NT; ++st) acc = fma(S[a].d[st], Ws[st][1 + b], acc);
     return acc;
   }, g);
-  double t0 = 0.0, uw[4] = {0.0, 0.0, 0.0, 0.0}, duw[4] = {0.0, 0.0, 0.0, 0.0};
+  double t0 = 0.0, uw[NT], duw[NT];
+#pragma unroll
+  for (int st = 0; st < NT; ++st) { uw[st] = 0.0; duw[st] = 0.0; }
   for (int k = g.lane; k < M.n; k += g.size)
 #pragma unroll
-    for (int st = 0; st < 4; ++st) t0 = fma(S[M.nY + k].d[st], Ws[st][1 + k], t0);
+    for (int st = 0; st < NT; ++st) t0 = fma(S[M.nY + k].d[st], Ws[st][1 + k], t0);
   for (int i = g.lane; i < M.m; i += g.size)
 #pragma unroll
-    for (int st = 0; st < 4; ++st) {
+    for (int st = 0; st < NT; ++st) {
       uw[st] = fma(u[i].v, Ws[st][i], uw[st]);
       duw[st] = fma(u[i].d[st], Ws[st][i], duw[st]);
     }
   t0 = gsum(g, t0);
 #pragma unroll
-  for (int st = 0; st < 4; ++st) { uw[st] = gsum(g, uw[st]); duw[st] = gsum(g, duw[st]); }
+  for (int st = 0; st < NT; ++st) { uw[st] = gsum(g, uw[st]); duw[st] = gsum(g, duw[st]); }
   for (int c = g.lane; c < M.m; c += g.size) {
     double acc = (c == 0) ? t0 : out[c];
-    const Dual4& vc = v[c];
-    const Dual4& sT = S[M.nY + M.n + c];
+    const DualN<NT>& vc = v[c];
+    const DualN<NT>& sT = S[M.nY + M.n + c];
 #pragma unroll
-    for (int st = 0; st < 4; ++st)
+    for (int st = 0; st < NT; ++st)
       acc += fma(vc.d[st], uw[st], fma(vc.v, duw[st], sT.d[st] * Ws[st][0]));
     out[c] = acc;
   }
   g.sync();
 }
 
-__device__ __forceinline__ Dual tangent_of(const Dual4& x, int st) { return Dual(x.v, x.d[st]); }
+template <int NT>
+__device__ __forceinline__ Dual tangent_of(const DualN<NT>& x, int st) { return Dual(x.v, x.d[st]); }
 
-// The mixed parameter terms of the four stages: GA_r, GE_r += sum_st d_st [q_r E_r(W_st)] with the
-// parameter contraction of theta_terms evaluated in the dual number of tangent st.
-__device__ __forceinline__ void theta_tangents(const MechView& M, const Dual4* s, const CellLayout& L,
-                                               const ScalT<Dual4>& sc, const double* const* Ws, Dual* a,
+// The mixed parameter terms of the stages of this pass: GA_r, GE_r += sum_st d_st [q_r E_r(W_st)] with
+// the parameter contraction of theta_terms evaluated in the dual number of tangent st.
+template <int NT>
+__device__ __forceinline__ void theta_tangents(const MechView& M, const DualN<NT>* s, const CellLayout& L,
+                                               const ScalT<DualN<NT>>& sc, const double* const* Ws, Dual* a,
                                                double* GA, double* GE, const Grp1& g) {
 #pragma unroll
-  for (int st = 0; st < 4; ++st) {
+  for (int st = 0; st < NT; ++st) {
     const double* w = Ws[st];
     const Dual T = tangent_of(sc.T, st), rho = tangent_of(sc.rho, st), cp = tangent_of(sc.cp, st);
     const Dual irho = tangent_of(sc.irho, st);
@@ -177,58 +192,51 @@ __device__ __forceinline__ void theta_tangents(const MechView& M, const Dual4* s
   }
 }
 
-// All second-order terms of one step: the Jacobian at y differentiated along U1..U4 at once, then the
-// state part into LAM and the parameter part into GA, GE.  tmp: m doubles of scratch.
-__device__ __forceinline__ void second_order_terms(const MechView& M, Dual4* dw, const CellLayout& Ld,
+// Second-order terms of NT stages of one step: the Jacobian at y differentiated along their U_i at once,
+// then the state part into LAM and the parameter part into GA, GE.  dwv: the dual workspace (the cell
+// layout in DualN<NT>); tmp: m doubles of scratch.
+template <int NT>
+__device__ __forceinline__ void second_order_terms(const MechView& M, void* dwv, const CellLayout& Ld,
                                                    const double* y, double p, const double* const* Us,
                                                    const double* const* Ws, double* LAM, double* tmp, double* GA,
                                                    double* GE, const Grp1& g) {
-  Dual4* yd = dw + Ld.y;
+  using DT = DualN<NT>;
+  DT* dw = static_cast<DT*>(dwv);
+  DT* yd = dw + Ld.y;
   for (int i = g.lane; i < M.m; i += g.size) {
-    Dual4 x(y[i]);
+    DT x(y[i]);
 #pragma unroll
-    for (int st = 0; st < 4; ++st) x.d[st] = Us[st][i];
+    for (int st = 0; st < NT; ++st) x.d[st] = Us[st][i];
     yd[i] = x;
   }
   g.sync();
-  const ScalT<Dual4> scd = eval_jac<Dual4>(M, dw, Ld, yd, p, g);
-  vjp_tangents(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws, tmp, reinterpret_cast<double*>(dw + Ld.part), g);
+  const ScalT<DT> scd = eval_jac<DT>(M, dw, Ld, yd, p, g);
+  vjp_tangents<NT>(M, dw + Ld.S, dw + Ld.u, dw + Ld.v, Ws, tmp, reinterpret_cast<double*>(dw + Ld.part), g);
   for (int i = g.lane; i < M.m; i += g.size) LAM[i] += tmp[i];
   g.sync();
-  theta_tangents(M, dw, Ld, scd, Ws, reinterpret_cast<Dual*>(dw + Ld.z), GA, GE, g);
+  theta_tangents<NT>(M, dw, Ld, scd, Ws, reinterpret_cast<Dual*>(dw + Ld.z), GA, GE, g);
 }
 
-// One adjoint step at state y with step h, whose stage vectors U1..U4 the segment recompute kept.
-// lambda (A.LAM) is updated in place, the parameter gradients accumulate into GA, GE.  Returns false if
-// the factor is singular (cannot happen for a step the forward pass accepted).
-__device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, double* ws, const AdjLayout& A, Dual4* dw,
-                                             const double* y, const double* U1, const double* U2, const double* U3,
-                                             const double* U4, double p, double h, double* GA, double* GE,
-                                             const Grp1& g) {
+// One adjoint step at state y with step h, whose stage vectors U1..U4 and step record jr (the Jacobian
+// at y and the factor of the step) the segment recompute kept.  lambda (A.LAM) is updated in place, the
+// parameter gradients accumulate into GA, GE.
+__device__ __forceinline__ void adjoint_step(const MechView& M, double* s, double* ws, const AdjLayout& A, Dual4* dw,
+                                             const double* jr, const double* y, const double* U1, const double* U2,
+                                             const double* U3, const double* U4, double p, double h, double* GA,
+                                             double* GE, const Grp1& g) {
   const CellLayout& L = A.L;
   const int m = M.m;
   const double ih = 1.0 / h;
   double* W1 = ws + A.W1; double* W2 = ws + A.W2; double* W3 = ws + A.W3; double* W4 = ws + A.W4;
   double* MU1 = ws + A.MU1; double* MU2 = ws + A.MU2; double* MU3 = ws + A.MU3; double* MU4 = ws + A.MU4;
   double* LAM = ws + A.LAM; double* G = ws + A.G; double* Y3 = ws + A.Y3; double* Y4 = ws + A.Y4;
-  double* UY = ws + A.UY; double* VY = ws + A.VY; double* ZT = ws + A.ZT;
-  double* LUg = ws + A.LUG;
-  double* dinvg = LUg + M.nnz_LU;
+  const double* UY = jr + A.UY; const double* VY = jr + A.VY; double* ZT = ws + A.ZT;
+  const double* LUg = jr + A.LUG;
+  const double* dinvg = LUg + M.nnz_LU;
   double* X = s + L.U3;      // shared scratch of the transposed solves
   double* a = s + L.ytmp;    // shared scratch of the parameter terms (n <= m)
-  // ---- the step's Jacobian at y and its factor (same arithmetic as the forward attempt); keep what the
-  //      end of the step needs: S, u, v, q, h/RT and the mixture scalars at y
-  vset(s + L.y, y, m, g);
-  const ScalT<double> sy = eval_jac<double>(M, s, L, s + L.y, p, g);
-  vset(ws + A.SY, s + L.S, M.nnz_S, g);
-  vset(UY, s + L.u, m, g);
-  vset(VY, s + L.v, m, g);
-  vset(ws + A.QY, s + L.q, M.R, g);
-  vset(ws + A.HY, s + L.hRT, M.n, g);
-  if (g.lane == 0) {
-    ws[A.SC] = sy.T; ws[A.SC + 1] = sy.rho; ws[A.SC + 2] = sy.cp; ws[A.SC + 3] = sy.irho;
-  }
-  if (!lu_build_factor(M, s, L, ih * (1.0 / RG), g)) return false;
+  // ---- the step's factor (kept by the recompute) into shared memory for the first solves
+  vset(s + L.LU, LUg, M.nnz_LU + m, g);
   const double* LUs = s + L.LU;
   const double* dinvs = s + L.dinv;
   // transposed Sherman-Morrison vector zt = A^-T v
@@ -249,7 +257,6 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, doubl
   vset(X, MU4, m, g);
   smT_solve(M, LUs, dinvs, UY, ZT, X, idenT, g);
   vset(W4, X, m, g);
-  vset(LUg, LUs, M.nnz_LU + m, g);
   for (int i = g.lane; i < m; i += g.size) {
     Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
     Y3[i] = fma(A31, U1[i], y[i]);
@@ -294,16 +301,17 @@ __device__ __forceinline__ bool adjoint_step(const MechView& M, double* s, doubl
   double* WS = ws + A.WS;
   for (int i = g.lane; i < m; i += g.size) WS[i] = W1[i] + W2[i];
   g.sync();
-  vjp<double>(M, ws + A.SY, UY, VY, WS, G, s + L.part, g);
+  vjp<double>(M, jr + A.SY, UY, VY, WS, G, s + L.part, g);
   for (int i = g.lane; i < m; i += g.size) LAM[i] += G[i];
   g.sync();
-  theta_terms(M, ws + A.HY, ws + A.QY, ws[A.SC], ws[A.SC + 1], ws[A.SC + 2], ws[A.SC + 3], WS, a, GA, GE, g);
+  theta_terms(M, jr + A.HY, jr + A.QY, jr[A.SC], jr[A.SC + 1], jr[A.SC + 2], jr[A.SC + 3], WS, a, GA, GE, g);
   // ---- Hessian and mixed parameter terms: derivative of J(y) along U_i, contracted with w_i, for the
   //      four stages in one evaluation of the Jacobian with four tangents
   const double* Us[4] = {U1, U2, U3, U4};
   const double* Ws[4] = {W1, W2, W3, W4};
-  second_order_terms(M, dw, L, y, p, Us, Ws, LAM, G, GA, GE, g);
-  return true;
+#pragma unroll 1
+  for (int s0 = 0; s0 < 4; s0 += kTangentsPerPass)
+    second_order_terms<kTangentsPerPass>(M, dw, L, y, p, Us + s0, Ws + s0, LAM, G, GA, GE, g);
 }
 
 // Reverse pass of one cell from its tape.  ws: the warp's global workspace.  Returns false on a singular
@@ -322,12 +330,23 @@ __device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, doubl
     const int n0 = sg * K, n1 = min(n_acc, n0 + K);
     for (int i = g.lane; i < m; i += g.size) seg[i] = rec_ck[((size_t)sg * m + i) * N + cell];
     g.sync();
-    // recompute the segment's states and stage vectors with the forward arithmetic
+    // recompute the segment's states and stage vectors with the forward arithmetic, and keep each step's
+    // Jacobian at y and its factor for the reverse sweep
     for (int nn = n0; nn < n1; ++nn) {
+      double* jr = ws + A.JREC + (size_t)(nn - n0) * A.jstride;
       vset(s + L.y, seg + (size_t)(nn - n0) * m, m, g);
-      eval_jac<double>(M, s, L, s + L.y, p, g);
+      const ScalT<double> sy = eval_jac<double>(M, s, L, s + L.y, p, g);
+      vset(jr + A.SY, s + L.S, M.nnz_S, g);
+      vset(jr + A.UY, s + L.u, m, g);
+      vset(jr + A.VY, s + L.v, m, g);
+      vset(jr + A.QY, s + L.q, M.R, g);
+      vset(jr + A.HY, s + L.hRT, M.n, g);
+      if (g.lane == 0) {
+        jr[A.SC] = sy.T; jr[A.SC + 1] = sy.rho; jr[A.SC + 2] = sy.cp; jr[A.SC + 3] = sy.irho;
+      }
       const StepOut so = ros_attempt(M, s, L, p, rec_h[(size_t)nn * N + cell], o.rtol, o.atol, g);
-      if (!so.good) return false;
+      if (!so.good) return false;   // also a singular factor (cannot happen for a step the forward pass accepted)
+      vset(jr + A.LUG, s + L.LU, M.nnz_LU + m, g);
       double* u4 = ust + (size_t)(nn - n0) * 4 * m;
       for (int i = g.lane; i < m; i += g.size) {
         u4[i] = s[L.U1 + i]; u4[m + i] = s[L.U2 + i]; u4[2 * m + i] = s[L.U3 + i]; u4[3 * m + i] = s[L.U4 + i];
@@ -337,9 +356,8 @@ __device__ __forceinline__ bool adjoint_cell(const MechView& M, double* s, doubl
     }
     for (int nn = n1 - 1; nn >= n0; --nn) {
       const double* u4 = ust + (size_t)(nn - n0) * 4 * m;
-      if (!adjoint_step(M, s, ws, A, dw, seg + (size_t)(nn - n0) * m, u4, u4 + m, u4 + 2 * m, u4 + 3 * m, p,
-                        rec_h[(size_t)nn * N + cell], GA, GE, g))
-        return false;
+      adjoint_step(M, s, ws, A, dw, ws + A.JREC + (size_t)(nn - n0) * A.jstride, seg + (size_t)(nn - n0) * m, u4,
+                   u4 + m, u4 + 2 * m, u4 + 3 * m, p, rec_h[(size_t)nn * N + cell], GA, GE, g);
     }
   }
   return true;

@@ -135,11 +135,15 @@ AdjLayout make_adj_layout(const HostMech& hm, int K) {
   auto take = [&](int cnt) { int at = o; o += (cnt + 31) / 32 * 32; return at; };
   A.Y3 = take(m); A.Y4 = take(m); A.W1 = take(m); A.W2 = take(m); A.W3 = take(m); A.W4 = take(m);
   A.MU1 = take(m); A.MU2 = take(m); A.MU3 = take(m); A.MU4 = take(m); A.LAM = take(m); A.G = take(m);
-  A.ZT = take(m); A.WS = take(m); A.UY = take(m); A.VY = take(m); A.HY = take(m);
-  A.SY = take(hm.nnz_S);
-  A.QY = take(std::max(hm.R, 1));
-  A.LUG = take(hm.nnz_LU + m);
-  A.SC = take(8);
+  A.ZT = take(m); A.WS = take(m);
+  {   // one step record: offsets within it
+    int r = 0;
+    auto rtake = [&](int cnt) { int at = r; r += (cnt + 31) / 32 * 32; return at; };
+    A.SY = rtake(hm.nnz_S); A.UY = rtake(m); A.VY = rtake(m); A.HY = rtake(hm.n); A.QY = rtake(std::max(hm.R, 1));
+    A.SC = rtake(8); A.LUG = rtake(hm.nnz_LU + m);
+    A.jstride = r;
+  }
+  A.JREC = take(K * A.jstride);
   A.UST = take(K * 4 * m);
   A.SEG = take(K * m);
   A.GA = take(std::max(hm.R, 1));

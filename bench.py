@@ -522,10 +522,12 @@ def main():
     ap.add_argument("--tabulate", type=float, default=0.0,
                     help="evaluate the costly temperature functions from tables of this relative tolerance "
                          "(an approximation; 0: exact)")
-    ap.add_argument("--specialized", action="store_true",
-                    help="headline on the mechanism-specialised kernels (run-time compiled, one warp per cell)")
+    ap.add_argument("--kernels", default="auto", choices=["auto", "library", "specialized"],
+                    help="integration kernels of the headline: the mechanism-specialised ones (run-time "
+                         "compiled, one warp per cell), the library's, or auto = specialised where the "
+                         "workload runs one cell per warp and the compile succeeds")
     ap.add_argument("--no-specialized-ab", action="store_true",
-                    help="skip timing the specialised kernels beside the library's (default line)")
+                    help="skip timing the other kernel build beside the headline's on the same steps")
     args = ap.parse_args()
     global RTOL
     RTOL = args.rtol
@@ -549,16 +551,18 @@ def main():
     evolving = WORKLOADS[args.workload]["evolving"]
     meth = METHODS[args.method]
     h = chem.create(m, local)
+    one_warp = (args.cells_per_warp or int(h.info["auto_cells_per_warp"])) == 1 and \
+        int(h.info["auto_warps_per_cell"]) == 1
     spec_info = None
-    if args.specialized or not args.no_specialized_ab:
+    if args.kernels == "specialized" or (one_warp and (args.kernels == "auto" or not args.no_specialized_ab)):
         try:   # compiled before any timing; the time is reported, not counted
             spec_info = {"compile_s": h.specialize()}
         except chem.ChemError as e:
-            if args.specialized:
+            if args.kernels == "specialized":
                 raise
             spec_info = {"unavailable": str(e)}
-    one_warp = (args.cells_per_warp or int(h.info["auto_cells_per_warp"])) == 1 and \
-        int(h.info["auto_warps_per_cell"]) == 1
+    args.specialized = args.kernels == "specialized" or (
+        args.kernels == "auto" and one_warp and spec_info is not None and "compile_s" in spec_info)
     oc = opcount.model(m, h.export_plan(0), h.export_plan(1), method=meth)
     N = F.n_cells
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
@@ -661,9 +665,10 @@ def main():
                        # throughput ratio, specialised over library, on the same flow steps
                        "specialized_over_library": (t_same / res_ab["t"]) if not args.specialized
                        else (res_ab["t"] / t_same), "mode": args.mode})
-        elif not one_warp:
-            sp["note"] = "not timed: the specialised kernels run one cell per warp, this workload's choice differs"
         line["specialized"] = sp
+    elif not one_warp:
+        line["specialized"] = {"note": "not used: the specialised kernels run one cell per warp, this workload's "
+                                       "choice differs"}
     if res["clocks"]:
         line["clocks"] = res["clocks"]
     if secondary is not None:

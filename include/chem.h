@@ -164,7 +164,9 @@ typedef struct {
                              most of a warp idle; needs warps_per_cell 0 or 1; block_cells is rounded to
                              an even count; in mode 1 the two halves of a warp take consecutive cells of the
                              sorted queue); 1 = one cell per warp (or per two warps); 0: automatic (see
-                             chem_info).  Results agree with one warp per cell to rounding. */
+                             chem_info: two for mechanisms of at most 16 species when half-warp blocks
+                             keep at least as many cells resident per SM, else one).  Results agree with
+                             one warp per cell to rounding. */
   int tabulate;           /* chem_integrate, chem_integrate_noalloc, chem_integrate_mapped: 1 = evaluate the
                              costly temperature functions from tables (an approximation; Sec. 2.5: SpeedCHEM
                              interpolates costly thermodynamic functions with polynomials of optimal

@@ -293,6 +293,9 @@ chem_status set_attrs(chem_handle h) {
   // automatic choice: two warps per cell when one-warp cells leave fewer than 6 warps per SM (a cell
   // larger than ~35 KB of shared memory) and two-warp cells fit as many cells
   h->auto_wpc = (h->resident_cells[0] < 6 && h->resident_cells[1] >= h->resident_cells[0]) ? 2 : 1;
+  // two cells per warp for mechanisms whose species loops fit half a warp, unless shared memory would
+  // then hold fewer cells per SM
+  h->auto_cpw = (h->hm.n <= 16 && h->resident_cells[2] >= h->resident_cells[0]) ? 2 : 1;
   h->attr_set = true;
   return CHEM_OK;
 }

@@ -157,3 +157,14 @@ def test_two_cells_per_warp_rejects_two_warps(small, dev):
         _run(h, F, dev, warps_per_cell=2, cells_per_warp=2)
     with pytest.raises(chem.ChemError):
         _run(h, F, dev, cells_per_warp=3)
+
+
+def test_automatic_cells_per_warp(small, mid, dev):
+    """The automatic choice shares warps for the 10-species mechanism (its half-warp blocks keep more
+    cells resident) and not for the 53-species one; the automatic call equals the explicit one."""
+    m, h = small
+    assert h.info["auto_cells_per_warp"] == 2
+    assert h.info["resident_cells"][2] >= h.info["resident_cells"][0]
+    assert mid[1].info["auto_cells_per_warp"] == 1
+    F = synth.field_uniform_random(m, 300, seed=4)
+    _same(_run(h, F, dev, mode=1), _run(h, F, dev, mode=1, cells_per_warp=2))

@@ -146,6 +146,17 @@ constexpr double R4_C51 = 7.496443313967647, R4_C52 = -10.24680431464352, R4_C53
                  R4_C54 = 11.70890893206160;
 constexpr double R4_C61 = 8.083246795921522, R4_C62 = -7.981132988064893, R4_C63 = -31.52159432874371,
                  R4_C64 = 16.31930543123136, R4_C65 = -6.058818238834054;
+// The same coefficients as tables for the stage loop (row k - 2 of stage k; constant memory, read
+// with warp-uniform indices).
+static __constant__ double kR4A[4][4] = {{R4_A21, 0.0, 0.0, 0.0},
+                                         {R4_A31, R4_A32, 0.0, 0.0},
+                                         {R4_A41, R4_A42, R4_A43, 0.0},
+                                         {R4_A51, R4_A52, R4_A53, R4_A54}};
+static __constant__ double kR4C[5][5] = {{R4_C21, 0.0, 0.0, 0.0, 0.0},
+                                         {R4_C31, R4_C32, 0.0, 0.0, 0.0},
+                                         {R4_C41, R4_C42, R4_C43, 0.0, 0.0},
+                                         {R4_C51, R4_C52, R4_C53, R4_C54, 0.0},
+                                         {R4_C61, R4_C62, R4_C63, R4_C64, R4_C65}};
 
 constexpr double kInvLn10 = 0.43429448190325182765;
 constexpr double kLn10 = 2.30258509299404568402;
@@ -892,48 +903,44 @@ __device__ __forceinline__ StepOut ros4_attempt(const MV& M, double* s, const LT
   vx *= iden;
   for (int i = g.lane; i < m; i += g.size) U1[i] = fma(z[i], vx, U1[i]);
   g.sync();
-  // stage 2
-  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(R4_A21, U1[i], y[i]);
-  g.sync();
-  eval_f<double>(M, s, L, yt, p, U2, g);
-  for (int i = g.lane; i < m; i += g.size) U2[i] = fma(R4_C21 * ih, U1[i], U2[i]);
-  g.sync();
-  sm_solve(M, s, L, U2, iden, g);
-  // stage 3
-  for (int i = g.lane; i < m; i += g.size) yt[i] = fma(R4_A32, U2[i], fma(R4_A31, U1[i], y[i]));
-  g.sync();
-  eval_f<double>(M, s, L, yt, p, U3, g);
-  for (int i = g.lane; i < m; i += g.size) U3[i] = fma(ih, fma(R4_C31, U1[i], R4_C32 * U2[i]), U3[i]);
-  g.sync();
-  sm_solve(M, s, L, U3, iden, g);
-  // stage 4
-  for (int i = g.lane; i < m; i += g.size)
-    yt[i] = fma(R4_A43, U3[i], fma(R4_A42, U2[i], fma(R4_A41, U1[i], y[i])));
-  g.sync();
-  eval_f<double>(M, s, L, yt, p, U4, g);
-  for (int i = g.lane; i < m; i += g.size)
-    U4[i] = fma(ih, fma(R4_C41, U1[i], fma(R4_C42, U2[i], R4_C43 * U3[i])), U4[i]);
-  g.sync();
-  sm_solve(M, s, L, U4, iden, g);
-  // stage 5
-  for (int i = g.lane; i < m; i += g.size)
-    yt[i] = fma(R4_A54, U4[i], fma(R4_A53, U3[i], fma(R4_A52, U2[i], fma(R4_A51, U1[i], y[i]))));
-  g.sync();
-  eval_f<double>(M, s, L, yt, p, U5, g);
-  for (int i = g.lane; i < m; i += g.size)
-    U5[i] = fma(ih, fma(R4_C51, U1[i], fma(R4_C52, U2[i], fma(R4_C53, U3[i], R4_C54 * U4[i]))), U5[i]);
-  g.sync();
-  sm_solve(M, s, L, U5, iden, g);
-  // stage 6: stage 5's point plus U5; the coefficient sum of U1..U5 goes into U1 (not read afterwards)
-  for (int i = g.lane; i < m; i += g.size) {
-    yt[i] += U5[i];
-    U1[i] = ih * fma(R4_C61, U1[i], fma(R4_C62, U2[i], fma(R4_C63, U3[i], fma(R4_C64, U4[i], R4_C65 * U5[i]))));
+  // stages 2..6 in one loop (one copy of the right-hand side and solve code: the six stages written out
+  // overflowed the instruction cache).  Stage k's point is y + sum_j a_kj U_j (stage 6: stage 5's point
+  // plus U5), its vector solves A U_k = f(point) + (1/h) sum_j c_kj U_j; the coefficient sums are formed
+  // in the order of the written-out stages, so the arithmetic is unchanged.
+  double* Us[5] = {U1, U2, U3, U4, U5};
+#pragma unroll 1
+  for (int k = 1; k < 6; ++k) {   // stage k + 1
+    double* out = k < 5 ? Us[k] : U2;   // stage 6's vector overwrites U2, dead by then
+    if (k < 5) {
+      for (int i = g.lane; i < m; i += g.size) {
+        double acc = y[i];
+        for (int j = 0; j < k; ++j) acc = fma(kR4A[k - 1][j], Us[j][i], acc);
+        yt[i] = acc;
+      }
+    } else {   // stage 6: the coefficient sum of U1..U5 goes into U1 (not read afterwards)
+      for (int i = g.lane; i < m; i += g.size) {
+        yt[i] += U5[i];
+        double acc = kR4C[4][4] * U5[i];
+        for (int j = 3; j >= 0; --j) acc = fma(kR4C[4][j], Us[j][i], acc);
+        U1[i] = ih * acc;
+      }
+    }
+    g.sync();
+    eval_f<double>(M, s, L, yt, p, out, g);
+    if (k == 1) {
+      for (int i = g.lane; i < m; i += g.size) out[i] = fma(R4_C21 * ih, U1[i], out[i]);
+    } else if (k < 5) {
+      for (int i = g.lane; i < m; i += g.size) {
+        double acc = kR4C[k - 1][k - 1] * Us[k - 1][i];
+        for (int j = k - 2; j >= 0; --j) acc = fma(kR4C[k - 1][j], Us[j][i], acc);
+        out[i] = fma(ih, acc, out[i]);
+      }
+    } else {
+      for (int i = g.lane; i < m; i += g.size) out[i] += U1[i];
+    }
+    g.sync();
+    sm_solve(M, s, L, out, iden, g);
   }
-  g.sync();
-  eval_f<double>(M, s, L, yt, p, U2, g);
-  for (int i = g.lane; i < m; i += g.size) U2[i] += U1[i];
-  g.sync();
-  sm_solve(M, s, L, U2, iden, g);
   // solution = stage 6's point + U6, error estimate U6, scaled RMS norm
   double e2 = 0.0;
   bool fin = true;

@@ -91,3 +91,24 @@ def test_rodas4_constants(setup):
     assert np.allclose(a[5, :4], a[4, :4], rtol=1e-13) and abs(a[5, 4] - 1.0) < 1e-13
     assert np.allclose(t["m"], [*a[4, :4], 1.0, 1.0], rtol=1e-13, atol=1e-13)
     assert np.allclose(t["e"], [0, 0, 0, 0, 0, 1.0], atol=1e-13)
+
+
+def _table(name):
+    """Entries of `static __constant__ double NAME[r][c] = {{...}, ...};` in device.cuh, as text."""
+    text = open(SRC).read()
+    body = re.search(name + r"\[(\d+)\]\[(\d+)\]\s*=\s*\{(.*?)\};", text, re.S)
+    assert body, name
+    rows = re.findall(r"\{([^{}]*)\}", body.group(3))
+    return [[x.strip() for x in r.split(",")] for r in rows], int(body.group(1)), int(body.group(2))
+
+
+def test_rodas4_stage_tables_hold_the_named_coefficients():
+    """The stage loop of the RODAS4 attempt reads a_kj and c_kj from two tables: row k - 2 is stage k,
+    column j - 1 multiplies U_j, below the diagonal only (a transposed or shifted entry fails here)."""
+    for name, letter, nrow in (("kR4A", "A", 4), ("kR4C", "C", 5)):
+        rows, r, c = _table(name)
+        assert r == nrow and c == nrow and len(rows) == nrow
+        for i, row in enumerate(rows):
+            assert len(row) == nrow
+            for j, x in enumerate(row):
+                assert x == (f"R4_{letter}{i + 2}{j + 1}" if j <= i else "0.0"), (name, i, j, x)

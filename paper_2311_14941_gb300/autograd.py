@@ -25,7 +25,9 @@ class ChemIntegrate(torch.autograd.Function):
         hio = torch.zeros(N, dtype=torch.float64, device=dev)
         ns = torch.zeros(N, dtype=torch.int32, device=dev)
         st = torch.zeros(N, dtype=torch.int32, device=dev)
-        mech.integrate(T, p, Y, dt, hio, ns, st, rtol=rtol, atol=atol)
+        # the map chem_adjoint differentiates: one warp per cell, plain launch (same arithmetic, so the
+        # returned state is bit for bit the one whose gradients backward gives)
+        mech.integrate(T, p, Y, dt, hio, ns, st, rtol=rtol, atol=atol, mode=0, warps_per_cell=1, cells_per_warp=1)
         mech.set_params()
         ctx.mech = mech
         ctx.opts = (rtol, atol, ckpt_every, tape_steps)

@@ -232,7 +232,6 @@ __device__ __forceinline__ void adjoint_step(const MechView& M, double* s, doubl
   double* LAM = ws + A.LAM; double* G = ws + A.G; double* Y3 = ws + A.Y3; double* Y4 = ws + A.Y4;
   const double* UY = jr + A.UY; const double* VY = jr + A.VY; double* ZT = ws + A.ZT;
   const double* LUg = jr + A.LUG;
-  const double* dinvg = LUg + M.nnz_LU;
   double* X = s + L.U3;      // shared scratch of the transposed solves
   double* a = s + L.ytmp;    // shared scratch of the parameter terms (n <= m)
   // ---- the step's factor (kept by the recompute) into shared memory for the first solves
@@ -247,57 +246,50 @@ __device__ __forceinline__ void adjoint_step(const MechView& M, double* s, doubl
   uz = gsum(g, uz);
   const double idenT = 1.0 / (1.0 - uz);
   vset(ZT, X, m, g);
-  // ---- reverse sweep over the stages
+  // ---- reverse sweep over the stages, one pass of the loop per stage, so that the kernel holds one copy
+  //      of the transposed solve and of the stage Jacobian code (written out, the stages overflowed the
+  //      instruction cache)
   for (int i = g.lane; i < m; i += g.size) {
     MU1[i] = M1 * LAM[i]; MU2[i] = 0.0; MU3[i] = M3 * LAM[i]; MU4[i] = M4 * LAM[i];
-  }
-  g.sync();
-  // stage 4: r4 = f(Y4) + (c41 U1 + c42 U2 + c43 U3)/h, Y4 = y + a41 U1 + a43 U3 (factor still in shared
-  // memory; copied out before the Jacobian at Y4 takes its region)
-  vset(X, MU4, m, g);
-  smT_solve(M, LUs, dinvs, UY, ZT, X, idenT, g);
-  vset(W4, X, m, g);
-  for (int i = g.lane; i < m; i += g.size) {
     Y4[i] = fma(A43, U3[i], fma(A41, U1[i], y[i]));
     Y3[i] = fma(A31, U1[i], y[i]);
   }
   g.sync();
-  {
-    const ScalT<double> sc = eval_jac<double>(M, s, L, Y4, p, g);
-    theta_terms(M, s + L.hRT, s + L.q, sc.T, sc.rho, sc.cp, sc.irho, W4, a, GA, GE, g);
-    vjp<double>(M, s + L.S, s + L.u, s + L.v, W4, G, s + L.part, g);
+  double* const Wv[4] = {W1, W2, W3, W4};
+  double* const MUv[4] = {MU1, MU2, MU3, MU4};
+#pragma unroll 1
+  for (int st = 3; st >= 0; --st) {   // stage st + 1
+    // the factor back into shared memory where a stage Jacobian took its region
+    if (st == 2 || st == 1) vset(s + L.LU, LUg, M.nnz_LU + m, g);
+    vset(X, MUv[st], m, g);
+    smT_solve(M, LUs, dinvs, UY, ZT, X, idenT, g);
+    double* W = Wv[st];
+    vset(W, X, m, g);
+    if (st >= 2) {
+      // stage 4: r4 = f(Y4) + (c41 U1 + c42 U2 + c43 U3)/h, Y4 = y + a41 U1 + a43 U3;
+      // stage 3: r3 = f(Y3) + (c31 U1 + c32 U2)/h,          Y3 = y + a31 U1
+      const ScalT<double> sc = eval_jac<double>(M, s, L, st == 3 ? Y4 : Y3, p, g);
+      theta_terms(M, s + L.hRT, s + L.q, sc.T, sc.rho, sc.cp, sc.irho, W, a, GA, GE, g);
+      vjp<double>(M, s + L.S, s + L.u, s + L.v, W, G, s + L.part, g);
+      if (st == 3) {
+        for (int i = g.lane; i < m; i += g.size) {
+          MU1[i] = fma(C41 * ih, W4[i], fma(A41, G[i], MU1[i]));
+          MU2[i] = fma(C42 * ih, W4[i], MU2[i]);
+          MU3[i] = fma(C43 * ih, W4[i], fma(A43, G[i], MU3[i]));
+          LAM[i] += G[i];
+        }
+      } else {
+        for (int i = g.lane; i < m; i += g.size) {
+          MU1[i] = fma(C31 * ih, W3[i], fma(A31, G[i], MU1[i]));
+          MU2[i] = fma(C32 * ih, W3[i], MU2[i]);
+          LAM[i] += G[i];
+        }
+      }
+    } else if (st == 1) {   // stage 2: r2 = f(y) + (c21/h) U1 (stage 1: r1 = f(y), nothing to propagate)
+      for (int i = g.lane; i < m; i += g.size) MU1[i] = fma(C21 * ih, W2[i], MU1[i]);
+    }
+    g.sync();
   }
-  for (int i = g.lane; i < m; i += g.size) {
-    MU1[i] = fma(C41 * ih, W4[i], fma(A41, G[i], MU1[i]));
-    MU2[i] = fma(C42 * ih, W4[i], MU2[i]);
-    MU3[i] = fma(C43 * ih, W4[i], fma(A43, G[i], MU3[i]));
-    LAM[i] += G[i];
-  }
-  g.sync();
-  // stage 3: r3 = f(Y3) + (c31 U1 + c32 U2)/h, Y3 = y + a31 U1
-  vset(X, MU3, m, g);
-  smT_solve(M, LUg, dinvg, UY, ZT, X, idenT, g);
-  vset(W3, X, m, g);
-  {
-    const ScalT<double> sc = eval_jac<double>(M, s, L, Y3, p, g);
-    theta_terms(M, s + L.hRT, s + L.q, sc.T, sc.rho, sc.cp, sc.irho, W3, a, GA, GE, g);
-    vjp<double>(M, s + L.S, s + L.u, s + L.v, W3, G, s + L.part, g);
-  }
-  for (int i = g.lane; i < m; i += g.size) {
-    MU1[i] = fma(C31 * ih, W3[i], fma(A31, G[i], MU1[i]));
-    MU2[i] = fma(C32 * ih, W3[i], MU2[i]);
-    LAM[i] += G[i];
-  }
-  g.sync();
-  // stage 2: r2 = f(y) + (c21/h) U1;  stage 1: r1 = f(y)
-  vset(X, MU2, m, g);
-  smT_solve(M, LUg, dinvg, UY, ZT, X, idenT, g);
-  vset(W2, X, m, g);
-  for (int i = g.lane; i < m; i += g.size) MU1[i] = fma(C21 * ih, W2[i], MU1[i]);
-  g.sync();
-  vset(X, MU1, m, g);
-  smT_solve(M, LUg, dinvg, UY, ZT, X, idenT, g);
-  vset(W1, X, m, g);
   double* WS = ws + A.WS;
   for (int i = g.lane; i < m; i += g.size) WS[i] = W1[i] + W2[i];
   g.sync();

@@ -1,7 +1,7 @@
 """Build the CUDA library ``_native/libchemgb.so`` in-tree (sm_103a only).
 
 Translation units compiled in parallel: the host mechanism compiler, the load-balance planner and the
-run-time specialisation driver (C++), the C ABI with its small kernels, the integration kernels of each
+run-time specialisation (C++), the C ABI with its small kernels, the integration kernels of each
 lane group and form (one warp, two warps, half a warp per cell), the rate and Jacobian kernels and the
 adjoint kernels (CUDA).  The device headers of the integration kernels are embedded as text
 (``_native/rtc_headers.inc``) for the run-time compiler.  Called by ``__graft_entry__.build()``; also

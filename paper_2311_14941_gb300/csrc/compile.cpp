@@ -500,33 +500,18 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
         for (int u : upd_to[slot[i][k]]) ops[u].succ.push_back(sc);
       }
     }
-    std::vector<std::vector<int>> upd_reading(hm.nnz_LU);   // UPDATE ops reading each U slot
     for (size_t v = 0; v < ops.size(); ++v) {
       if (ops[v].kind != K_UPDATE) continue;
       int a = ops[v].enc.a, b = ops[v].enc.b;
       ops[scale_of[a]].succ.push_back((int)v);
       for (int u : upd_to[b]) ops[u].succ.push_back((int)v);
-      upd_reading[b].push_back((int)v);
     }
-    // LDU form: once row k of U has served every update, scale it by the pivot's reciprocal, so that U
-    // is unit upper triangular and the substitutions need no scaling inside their triangular sweeps
-    for (int k = 0; k < m; ++k)
-      for (int j = k + 1; j < m; ++j) {
-        const int t = slot[k][j];
-        if (t < 0) continue;
-        const int id = (int)ops.size();
-        ops.push_back(DagOp{K_SCALE, t, ElimOp{(uint16_t)t, (uint16_t)k, 0, 0}, {}});
-        ops[recip[k]].succ.push_back(id);
-        for (int u : upd_to[t]) ops[u].succ.push_back(id);          // the entry is final
-        for (int u : upd_reading[t]) ops[u].succ.push_back(id);     // every update has read it unscaled
-      }
     for (HostProg& P : hm.prog) {
       std::vector<DagOp> work = ops;
       if (!schedule(work, P.lu_ops, P.lu_kind, err, P.width)) return CHEM_EINVAL;
     }
   }
-  // ---- substitution program (forward with unit L, scaling by 1/diag, backward with unit U: the LDU
-  //      form), state-order indices
+  // ---- substitution program (forward with unit L, backward with U and 1/diag), state-order indices
   {
     std::vector<DagOp> ops;
     std::vector<std::vector<int>> fw_w(m), fw_r(m), bw_w(m);
@@ -556,21 +541,21 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
       for (int w : fw_w[p]) for (int r : fw_r[p]) ops[w].succ.push_back(r);     // RAW forward
       for (int w : fw_w[p]) ops[w].succ.push_back(sc[p]);
       for (int r : fw_r[p]) ops[r].succ.push_back(sc[p]);                       // WAR before scaling
-      for (int w : bw_w[p]) ops[sc[p]].succ.push_back(w);                       // backward after scaling
+      for (int w : bw_w[p]) {
+        for (int f : fw_w[p]) ops[f].succ.push_back(w);                         // backward after forward
+        for (int r : fw_r[p]) ops[r].succ.push_back(w);                         // WAR
+        ops[w].succ.push_back(sc[p]);
+      }
     }
-    for (auto& pr : bw) {                                                       // RAW backward: x_q final
-      const int q = pr.second;
-      ops[sc[q]].succ.push_back(pr.first);
-      for (int w : bw_w[q]) ops[w].succ.push_back(pr.first);
-    }
+    for (auto& pr : bw) ops[sc[pr.second]].succ.push_back(pr.first);           // RAW backward
     for (HostProg& P : hm.prog) {
       std::vector<DagOp> work = ops;
       if (!schedule(work, P.sv_ops, P.sv_kind, err, P.width)) return CHEM_EINVAL;
     }
   }
-  // ---- transposed substitution (A^T x = b, A^T = U^T D L^T with unit U and L): forward with U^T, then
-  //      x_p *= 1/D_p, then backward with L^T.  In factor positions: x_p -= U_qp x_q (q < p); x_p *= 1/D_p;
-  //      x_p -= L_qp x_q (q > p).  Same op encoding, state-order vector indices.
+  // ---- transposed substitution (A^T x = b): forward with U^T (scaled by 1/diag), then backward with
+  //      the unit L^T.  In factor positions: x_p -= U_qp x_q (q < p), x_p *= 1/U_pp; then x_p -= L_qp x_q
+  //      (q > p).  Same op encoding, state-order vector indices.
   {
     std::vector<DagOp> ops;
     std::vector<std::vector<int>> f_w(m), f_r(m), b_w(m);
@@ -586,12 +571,9 @@ chem_status compile_mechanism(const chem_mech_desc& d, HostMech& hm, std::string
           ops.push_back(DagOp{K_UPDATE, hm.perm[p], ElimOp{(uint16_t)hm.perm[p], (uint16_t)slot[q][p], (uint16_t)hm.perm[q], 0}, {}});
           f_w[p].push_back(id);
           f_r[q].push_back(id);
+          ops[sc[q]].succ.push_back(id);    // reads x_q after its scaling
           ops[id].succ.push_back(sc[p]);    // x_p scaled after all its updates
         }
-    for (int p = 0; p < m; ++p) {
-      for (int w : f_w[p]) for (int r : f_r[p]) ops[w].succ.push_back(r);      // RAW forward: x_p final
-      for (int r : f_r[p]) ops[r].succ.push_back(sc[p]);                       // WAR before scaling
-    }
     std::vector<std::pair<int, int>> bl;    // (op id, q)
     for (int p = 0; p < m; ++p)
       for (int q = p + 1; q < m; ++q)

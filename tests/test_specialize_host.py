@@ -19,7 +19,7 @@ def _consts(src):
 
 
 def test_source_holds_the_mechanisms_sizes():
-    for mk in (synth.mechanism_small, synth.mechanism_methane_sized):
+    for mk in (synth.mechanism_small, synth.mechanism_methane_sized, synth.mechanism_large):
         h = chem.create(mk(), device=-1)
         src = h.specialized_source()
         c = _consts(src)
